@@ -1,0 +1,209 @@
+"""Pins of the FP64 oracle's BiCGStab (Algorithm 1) and p-BiCGStab (Algorithm 2).
+
+Chain of evidence: the rational transcriptions in ``ratref`` are checked
+against facts exact arithmetic fixes (Algorithm 2's invariants, equality of the
+two algorithms' iterates, finite termination); the FP64 oracle is then checked
+against them, and against closed-form and invariance properties.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2404_13216_gb300 import inputs
+from tests import ratref
+
+
+def tiny_system(seed, n):
+    """Integer, diagonally dominant, unsymmetric: well-conditioned and breakdown-free."""
+    rng = np.random.default_rng(seed)
+    A = rng.integers(-3, 4, (n, n)).astype(np.int64)
+    A += np.diag(np.abs(A).sum(axis=1) + rng.integers(1, 4, n))
+    b = rng.integers(-5, 6, n)
+    b[0] = 7
+    return A, b
+
+
+def dense_to_csr(A):
+    n = A.shape[0]
+    rp, ci, v = [0], [], []
+    for i in range(n):
+        for j in range(n):
+            if A[i, j] != 0:
+                ci.append(j)
+                v.append(float(A[i, j]))
+        rp.append(len(ci))
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(v)
+
+
+def frac_mat(A):
+    return [[Fraction(int(a)) for a in row] for row in A]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_rational_invariants_equivalence_termination(seed):
+    n = 3 + seed % 4
+    A, b = tiny_system(seed, n)
+    Af, bf = frac_mat(A), [Fraction(int(v)) for v in b]
+    x0 = [Fraction(0)] * n
+    bad = []
+
+    def check(name, lhs, rhs):
+        if lhs != rhs:
+            bad.append(name)
+
+    p = ratref.pbicgstab(Af, bf, x0, n + 2, check=check)
+    c = ratref.bicgstab(Af, bf, x0, n + 2)
+    assert not bad, f"Algorithm 2 invariant broken: {set(bad)}"
+    # identical iterates in exact arithmetic
+    assert len(p) == len(c)
+    for rp_, rc_ in zip(p, c):
+        for key in ("x", "r", "alpha", "omega", "beta"):
+            assert rp_[key] == rc_[key], key
+        # r_{i+1} = b - A x_{i+1}
+        assert rp_["r"] == ratref.sub(bf, ratref.matvec(Af, rp_["x"]))
+    # terminates with the exact solution within n steps
+    assert len(p) <= n
+    assert all(v == 0 for v in p[-1]["r"])
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("seed", range(4))
+def test_fp64_oracle_follows_rational(orc, alg, seed):
+    n = 6
+    A, b = tiny_system(100 + seed, n)
+    Af, bf = frac_mat(A), [Fraction(int(v)) for v in b]
+    runs = ratref.bicgstab(Af, bf, [Fraction(0)] * n, 4)
+    rp, ci, v = dense_to_csr(A)
+    res = orc.solve(rp, ci, v, b.astype(float), tol=1e-300, maxit=3, alg=alg, mode=orc.EXACT, trace=True)
+    normb = math.sqrt(float(ratref.dot(bf, bf)))
+    k = min(3, len(runs))
+    for i in range(k):
+        r = runs[i]["r"]
+        want = math.sqrt(float(ratref.dot(r, r))) / normb
+        got = res.history[i + 1]
+        if want == 0:
+            assert got < 1e-12
+        else:
+            assert abs(got - want) <= 1e-9 * want + 1e-15, (i, got, want)
+        assert abs(res.trace[i, 0] - float(runs[i]["alpha"])) <= 1e-9 * abs(float(runs[i]["alpha"]))
+        assert abs(res.trace[i, 1] - float(runs[i]["omega"])) <= 1e-9 * abs(float(runs[i]["omega"]))
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_scaled_identity_lucky_breakdown(orc, alg, mode):
+    """A = 4 I: one iteration gives x = b/4 exactly (q = 0, y = 0, omega = 0)."""
+    n = 50
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    v = np.full(n, 4.0)
+    b = np.random.default_rng(0).standard_normal(n)
+    res = orc.solve(rp, ci, v, b, tol=1e-14, maxit=10, alg=alg, mode=mode)
+    assert res.status == orc.CONVERGED and res.iters == 1
+    assert np.array_equal(res.x, b / 4.0)
+    assert res.history[1] == 0.0 and res.relres_true == 0.0
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_power_of_two_scaling_is_exact(orc, alg, mode):
+    A = inputs.convdiff2d(16, 5.0)
+    b = inputs.rhs_ones(A)
+    r1 = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=200, alg=alg, mode=mode)
+    r2 = orc.solve(A.row_ptr, A.col_idx, A.vals * 2.0 ** 40, b * 2.0 ** 40, tol=1e-10, maxit=200,
+                   alg=alg, mode=mode)
+    r3 = orc.solve(A.row_ptr, A.col_idx, A.vals, b * 2.0 ** -30, tol=1e-10, maxit=200, alg=alg, mode=mode)
+    assert r1.iters == r2.iters == r3.iters
+    assert np.array_equal(r1.history, r2.history) and np.array_equal(r1.history, r3.history)
+    assert np.array_equal(r1.x, r2.x)
+    assert np.array_equal(r1.x * 2.0 ** -30, r3.x)
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("N,Pe,tol", [(32, 10.0, 1e-8), (24, 60.0, 1e-10)])
+def test_true_residual_reaches_tol(orc, alg, mode, N, Pe, tol):
+    A = inputs.convdiff2d(N, Pe)
+    b = inputs.rhs_ones(A)
+    res = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=tol, maxit=3000, alg=alg, mode=mode)
+    assert res.status == orc.CONVERGED
+    assert res.relres_true <= tol
+    assert res.history.size == res.iters + 1
+    assert res.history[-1] <= tol
+    assert np.max(np.abs(res.x - 1.0)) < 1e3 * tol * N * N
+
+
+def test_bicgstab_and_pipelined_agree_early(orc):
+    """Equivalent in exact arithmetic: FP64 histories agree closely at first."""
+    A = inputs.convdiff2d(16, 1.0)
+    b = inputs.rhs_ones(A)
+    for mode in (0, 1):
+        h1 = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=5, alg=0, mode=mode).history
+        h2 = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=5, alg=1, mode=mode).history
+        assert h1.size == h2.size == 6
+        assert np.all(np.abs(h1 - h2) <= 1e-6 * np.abs(h1))
+
+
+def test_exact_start_converges_at_zero(orc):
+    A = inputs.convdiff2d(8, 3.0)
+    b = inputs.rhs_ones(A)
+    for alg in (0, 1):
+        res = orc.solve(A.row_ptr, A.col_idx, A.vals, b, x0=np.ones(A.n), tol=1e-12, maxit=10, alg=alg)
+        assert res.status == orc.CONVERGED and res.iters == 0 and res.history.tolist() == [0.0]
+
+
+def test_maxit_zero_and_nonfinite(orc):
+    A = inputs.convdiff2d(8, 3.0)
+    b = inputs.rhs_ones(A)
+    for alg in (0, 1):
+        res = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-12, maxit=0, alg=alg)
+        assert res.status == orc.MAXIT and res.iters == 0 and res.history.size == 1
+        bn = b.copy()
+        bn[3] = np.nan
+        res = orc.solve(A.row_ptr, A.col_idx, A.vals, bn, tol=1e-12, maxit=10, alg=alg)
+        assert res.status == orc.NONFINITE and res.iters == 0
+        vn = A.vals.copy()
+        vn[5] = np.inf
+        res = orc.solve(A.row_ptr, A.col_idx, vn, b, tol=1e-12, maxit=10, alg=alg)
+        assert res.status == orc.NONFINITE
+
+
+def test_breakdown_skew(orc):
+    """(r0, A r0) = 0 for skew-symmetric A: alpha_0 is infinite -> BREAKDOWN."""
+    rp = np.array([0, 1, 2], np.int32)
+    ci = np.array([1, 0], np.int32)
+    v = np.array([1.0, -1.0])
+    b = np.array([1.0, 0.0])
+    for alg in (0, 1):
+        for mode in (0, 1):
+            res = orc.solve(rp, ci, v, b, tol=1e-10, maxit=10, alg=alg, mode=mode)
+            assert res.status == orc.BREAKDOWN and res.iters == 0
+            assert np.array_equal(res.x, [0.0, 0.0])
+
+
+def test_invalid_inputs(orc):
+    rp = np.array([0, 1, 2], np.int32)
+    ci = np.array([1, 0], np.int32)
+    v = np.array([1.0, 1.0])
+    b = np.ones(2)
+    with pytest.raises(ValueError):
+        orc.solve(rp, ci, v, b, tol=0.0)
+    with pytest.raises(ValueError):
+        orc.solve(rp, np.array([1, 2], np.int32), v, b)
+    with pytest.raises(ValueError):
+        orc.solve(np.array([0, 2, 1], np.int32), ci, v, b)
+    with pytest.raises(ValueError):
+        orc.solve(rp, ci, v, b, maxit=-1)
+
+
+def test_exact_mode_history_is_partition_free(orc):
+    """Exact dots make the whole run independent of how dots are split across
+    threads (the single-node analogue of the process-count invariance of Tables 2-3)."""
+    A = inputs.convdiff3d(42, 50.0)
+    b = inputs.rhs_ones(A)
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=40, alg=1, mode=1, nthreads=1)
+    for t in (3, 8):
+        res = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=40, alg=1, mode=1, nthreads=t)
+        assert np.array_equal(res.history, ref.history) and np.array_equal(res.x, ref.x)
