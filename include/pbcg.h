@@ -1,0 +1,171 @@
+/*
+ * pbcg.h -- C ABI of the GB300 (sm_103a) solver library libpbcg.so.
+ *
+ * Solves A x = b for a sparse, unsymmetric A in FP64 CSR with classical
+ * BiCGStab (Algorithm 1 of arXiv 2404.13216, after van der Vorst) or pipelined
+ * BiCGStab (Algorithm 2, after Cools and Vanroose), given x_0, a relative
+ * tolerance and an iteration cap -- the problem statement of Section 2.  Dot
+ * products are either plain FP64 or exact: the real sum rounded once to the
+ * nearest double, the accuracy the paper obtains from the ExBLAS long
+ * accumulator (Section 2) in place of residual replacement.
+ *
+ * Arithmetic contract (both dot modes): each SpMV row is an fma chain over the
+ * row's stored entries in stored order starting from +0; every vector update
+ * is the fixed fma form listed with the solver entry points below; scalars use
+ * IEEE division and square root.  In exact mode the residual history,
+ * iteration count and x are therefore a deterministic function of the inputs,
+ * independent of launch shape, batching and partitioning.
+ *
+ * Conventions
+ *   - Every call returns an int: 0 or a positive solver status on completion,
+ *     a negative PBCG_ERR_* code on error (the context's last-error string then
+ *     says why).  No call aborts the process.
+ *   - Vector arguments (b, x, row_ptr, ...) may be host or device pointers; the
+ *     library finds out which with cudaPointerGetAttributes.  Device pointers
+ *     must be on the context's device.  The caller keeps ownership of every
+ *     buffer it passes; the library copies what it keeps.
+ *   - A context owns one CUDA stream (its own, or the caller's) and is not
+ *     thread-safe: use one context per host thread.
+ *   - Index types: int32 row pointers and column indices (nnz < 2^31).
+ */
+#ifndef PBCG_H
+#define PBCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pbcg_ctx pbcg_ctx;   /* opaque, library-owned */
+typedef struct pbcg_mat pbcg_mat;   /* opaque, library-owned device copy of a CSR matrix */
+
+/* solver statuses (>= 0) and error codes (< 0) */
+enum {
+    PBCG_OK = 0,            /* converged: true relative residual <= tol */
+    PBCG_MAXIT = 1,         /* maxit iterations done without convergence */
+    PBCG_BREAKDOWN = 2,     /* zero or non-finite denominator in alpha, beta or omega */
+    PBCG_NONFINITE = 3,     /* NaN/Inf reached a dot product (input or overflow) */
+    PBCG_ERR_INVALID = -1,  /* bad argument; nothing was launched */
+    PBCG_ERR_OOM = -2,      /* device allocation failed */
+    PBCG_ERR_CUDA = -3,     /* a CUDA call failed */
+    PBCG_ERR_TIMEOUT = -4   /* a bounded device wait expired */
+};
+
+enum { PBCG_ALG_BICGSTAB = 0, PBCG_ALG_PIPELINED = 1 };
+enum { PBCG_DOT_PLAIN = 0, PBCG_DOT_EXACT = 1 };
+
+typedef struct {
+    int32_t iters;            /* completed loop bodies */
+    int32_t status;           /* PBCG_OK .. PBCG_NONFINITE */
+    double relres_recursive;  /* sqrt((r,r)) / sqrt((b,b)) of the last iterate, solve's dot mode */
+    double relres_true;       /* ||b - A x||_2 / ||b||_2 with the fixed SpMV and exact dots */
+    double seconds;           /* wall time of the call on the host */
+} pbcg_result;
+
+/*
+ * Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+ * launch on, or NULL for a stream the context creates and owns.
+ * Errors: INVALID (out == NULL or bad device), CUDA, OOM.
+ */
+int pbcg_create(pbcg_ctx **out, int device, void *cuda_stream);
+
+/* Destroy a context and everything it allocated.  destroy(NULL) is a no-op. */
+void pbcg_destroy(pbcg_ctx *ctx);
+
+/* The last error message of this context ("" if none).  The string lives until the next call. */
+const char *pbcg_last_error(pbcg_ctx *ctx);
+
+/*
+ * Copy a CSR matrix to the device.  row_ptr[n+1], col_idx[nnz], vals[nnz];
+ * host or device pointers (ptrs_on_device is a hint only, the library checks).
+ * Validation (INVALID on failure): n >= 1, nnz >= 0, row_ptr[0] == 0,
+ * row_ptr non-decreasing, row_ptr[n] == nnz < 2^31, 0 <= col_idx < n.
+ * Duplicate columns are allowed and summed in stored order.
+ * The matrix belongs to ctx and is freed by pbcg_mat_free or pbcg_destroy.
+ */
+int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                    const double *vals, int ptrs_on_device, pbcg_mat **out);
+
+/* Free a matrix created by pbcg_csr_upload (NULL is a no-op). */
+int pbcg_mat_free(pbcg_ctx *ctx, pbcg_mat *mat);
+
+/*
+ * Solve A x = b from x (in: x_0, out: the last iterate, written for every
+ * status).  b and x hold n doubles each.  alg: PBCG_ALG_*; dot_mode: PBCG_DOT_*.
+ *
+ * Algorithm 2 (p-BiCGStab), with omega the scalar (q,y)/(y,y) and w the
+ * vector A r (the paper uses the letter w for both):
+ *   r_0 = b - A x_0, w_0 = A r_0 (the paper prints "A - r_0"), t_0 = A w_0,
+ *   alpha_0 = (r_0,r_0)/(r_0,w_0); p_0 = r_0, s_0 = w_0, z_0 = t_0; then per i
+ *     p = fma(beta, fma(-omega, s, p), r)   s = fma(beta, fma(-omega, z, s), w)
+ *     z = fma(beta, fma(-omega, v, z), t)   q = fma(-alpha, s, r)
+ *     y = fma(-alpha, z, w)                 v = A z      omega = (q,y)/(y,y)
+ *     x = fma(omega, q, fma(alpha, p, x))   r = fma(-omega, y, q)
+ *     w = fma(-omega, fma(-alpha, v, t), y) t = A w
+ *     beta  = (alpha/omega) * ((r_0,r_new)/(r_0,r_old))
+ *     alpha = (r_0,r_new) / (((r_0,w) + beta*(r_0,s)) - (beta*omega)*(r_0,z))
+ * Algorithm 1 (BiCGStab): s = A p, alpha = (r_0,r)/(r_0,s), q = fma(-alpha,s,r),
+ *   y = A q, omega = (q,y)/(y,y), x and r as above, beta as above,
+ *   p = fma(beta, fma(-omega, s, p), r).
+ *
+ * Stopping (the paper gives none): res_k = sqrt((r_k,r_k))/sqrt((b,b)) in the
+ * solve's dot mode is tested at k = 0 and after every iteration; when
+ * res_k <= target the true residual ||b - A x||/||b|| (exact dots) is formed
+ * and the solve stops if it is <= tol, else target = tol*(tol/true) and the
+ * iteration continues unchanged.  (y,y) = 0 gives omega = 0 and, unless that
+ * step converged, BREAKDOWN.  The residual history (res_0 .. res_iters) is
+ * kept for pbcg_residual_history.
+ *
+ * Returns the status (also in out->status) or a negative error.
+ */
+int pbcg_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double *x, double tol, int32_t maxit,
+               int alg, int dot_mode, pbcg_result *out);
+
+/*
+ * Solve nsys independent systems stored as one block-diagonal matrix:
+ * system k owns rows (and columns) [sys_row_ptr[k], sys_row_ptr[k+1]) of A.
+ * b, x: A's n entries; tol: nsys tolerances; out: nsys results.
+ * Every system runs the same arithmetic as a pbcg_solve of its own block,
+ * bit for bit in exact mode, and stops on its own.
+ * Validation adds: sys_row_ptr[0] == 0, strictly increasing,
+ * sys_row_ptr[nsys] == n, and no entry of a block outside its own columns.
+ * Returns 0 when every system converged, else the largest status, or an error.
+ */
+int pbcg_solve_batched(pbcg_ctx *ctx, const pbcg_mat *A, int32_t nsys, const int32_t *sys_row_ptr,
+                       const double *b, double *x, const double *tol, int32_t maxit, int alg, int dot_mode,
+                       pbcg_result *out);
+
+/*
+ * Copy the residual history res_0 .. res_iters of the last solve (sys = 0) or
+ * of system `sys` of the last batched solve into out[0 .. cap-1]; *len gets
+ * the full length (iters + 1).  INVALID if no such history exists.
+ */
+int pbcg_residual_history(pbcg_ctx *ctx, int32_t sys, double *out, int32_t cap, int32_t *len);
+
+/*
+ * Standalone kernels of the solver, for checks and measurement.
+ * pbcg_dot: *out = (a, b) over n entries in dot_mode (exact: correctly
+ *   rounded; NaN if an operand is NaN or Inf).  a, b host or device.
+ * pbcg_spmv: y = A x with the fixed fma row order.  x, y host or device.
+ */
+int pbcg_dot(pbcg_ctx *ctx, int64_t n, const double *a, const double *b, int dot_mode, double *out);
+int pbcg_spmv(pbcg_ctx *ctx, const pbcg_mat *A, const double *x, double *y);
+
+/*
+ * Time the solver's kernels: run the solve of pbcg_solve with a host-driven
+ * launch loop (no CUDA graph) and CUDA events around every launch, on the
+ * context's stream.  names receives up to cap kernel names (a
+ * '\0'-terminated string each, at most 31 characters), ms their total
+ * durations, launches their launch counts; *count gets the number of kernels.
+ * The solve's results are those of pbcg_solve.
+ */
+int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double *x, double tol,
+                       int32_t maxit, int alg, int dot_mode, pbcg_result *out, char (*names)[32],
+                       double *ms, int32_t *launches, int32_t cap, int32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBCG_H */

@@ -1,0 +1,764 @@
+// api.cu -- host driver and C ABI of libpbcg (declared in include/pbcg.h).
+//
+// A solve is: setup passes (r_0, w_0, t_0 and their dots), then the loop of
+// Algorithm 1 or 2 as a CUDA graph whose body is the fused passes inside a
+// conditional WHILE node; the last CTA of each pass sets the node's condition,
+// so the device iterates without host round trips.  The host wakes up only
+// when the device proposes to stop (residual below target), runs the
+// true-residual pass, and either finishes or relaunches the loop.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/pbcg.h"
+#include "kernels.cuh"
+
+using namespace pbcg;
+
+namespace {
+
+enum { V_X, V_B, V_R0, V_R, V_W, V_T, V_P, V_S, V_Z, V_V, V_Y, V_COUNT };
+
+struct LoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle handle = 0;
+    int alg = -1, mode = -1, n = -1;
+    const void *mat = nullptr;
+};
+
+struct Workspace {
+    long long n_cap = 0;
+    int hist_cap = 0;
+    double *vec[V_COUNT] = {};
+    Ctl *ctl = nullptr;
+    Work *wk = nullptr;
+    double *part = nullptr;
+    double *hist = nullptr;
+    double *dot_out = nullptr;
+    LoopGraph loop;
+};
+
+}  // namespace
+
+struct pbcg_mat {
+    int n;
+    long long nnz;
+    int *rp;
+    int *ci;
+    double *va;
+};
+
+struct pbcg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int maxgrid = 0;
+    std::string err;
+    Workspace ws;
+    std::set<pbcg_mat *> mats;
+    std::vector<double> hist;          // last single solve
+    bool have_hist = false;
+    Ctl *h_ctl = nullptr;              // pinned mirror of the control block
+};
+
+namespace {
+
+int fail(pbcg_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA,          \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+Csr csr_of(const pbcg_mat *m)
+{
+    Csr A;
+    A.n = m->n;
+    A.rp = m->rp;
+    A.ci = m->ci;
+    A.va = m->va;
+    return A;
+}
+
+Vecs vecs_of(Workspace &ws)
+{
+    Vecs V;
+    V.x = ws.vec[V_X];
+    V.b = ws.vec[V_B];
+    V.r0 = ws.vec[V_R0];
+    V.r = ws.vec[V_R];
+    V.w = ws.vec[V_W];
+    V.t = ws.vec[V_T];
+    V.p = ws.vec[V_P];
+    V.s = ws.vec[V_S];
+    V.z = ws.vec[V_Z];
+    V.v = ws.vec[V_V];
+    V.y = ws.vec[V_Y];
+    return V;
+}
+
+int grid_for(pbcg_ctx *ctx, long long n)
+{
+    long long tiles = (n + 31) / 32;
+    long long g = (tiles + WARPS - 1) / WARPS;
+    if (g > ctx->maxgrid)
+        g = ctx->maxgrid;
+    if (g < 1)
+        g = 1;
+    return (int)g;
+}
+
+void free_loop(LoopGraph &L)
+{
+    if (L.exec)
+        cudaGraphExecDestroy(L.exec);
+    if (L.graph)
+        cudaGraphDestroy(L.graph);
+    L = LoopGraph();
+}
+
+void free_ws(Workspace &ws)
+{
+    free_loop(ws.loop);
+    for (auto &p : ws.vec) {
+        if (p)
+            cudaFree(p);
+        p = nullptr;
+    }
+    if (ws.ctl)
+        cudaFree(ws.ctl);
+    if (ws.wk)
+        cudaFree(ws.wk);
+    if (ws.part)
+        cudaFree(ws.part);
+    if (ws.hist)
+        cudaFree(ws.hist);
+    if (ws.dot_out)
+        cudaFree(ws.dot_out);
+    ws = Workspace();
+}
+
+// make sure the workspace holds n-vectors and a history of hist_cap entries
+int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
+{
+    Workspace &ws = ctx->ws;
+    if (!ws.ctl) {
+        CK(cudaMalloc(&ws.ctl, sizeof(Ctl)));
+        CK(cudaMalloc(&ws.wk, sizeof(Work)));
+        CK(cudaMalloc(&ws.part, sizeof(double) * MAXD * ctx->maxgrid));
+        CK(cudaMalloc(&ws.dot_out, sizeof(double)));
+        Work h;
+        memset(&h, 0, sizeof h);
+        for (int d = 0; d < MAXD; d++) {
+            h.g[d].kmin = NDIG;
+            h.g[d].kmax = -1;
+        }
+        h.ticket = 0;
+        h.maxgrid = ctx->maxgrid;
+        h.part = ws.part;
+        CK(cudaMemcpy(ws.wk, &h, sizeof h, cudaMemcpyHostToDevice));
+    }
+    if (n > ws.n_cap) {
+        free_loop(ws.loop);
+        for (auto &p : ws.vec) {
+            if (p)
+                cudaFree(p);
+            p = nullptr;
+        }
+        ws.n_cap = 0;
+        for (auto &p : ws.vec)
+            CK(cudaMalloc(&p, sizeof(double) * (size_t)n));
+        ws.n_cap = n;
+    }
+    if (hist_cap > ws.hist_cap) {
+        if (ws.hist)
+            cudaFree(ws.hist);
+        ws.hist = nullptr;
+        ws.hist_cap = 0;
+        CK(cudaMalloc(&ws.hist, sizeof(double) * (size_t)hist_cap));
+        ws.hist_cap = hist_cap;
+    }
+    return 0;
+}
+
+int validate_csr_host(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci)
+{
+    if (n < 1)
+        return fail(ctx, PBCG_ERR_INVALID, "n must be >= 1 (got %d)", n);
+    if (nnz < 0 || nnz >= (1ll << 31))
+        return fail(ctx, PBCG_ERR_INVALID, "nnz out of range (got %lld)", (long long)nnz);
+    if (rp[0] != 0)
+        return fail(ctx, PBCG_ERR_INVALID, "row_ptr[0] must be 0");
+    for (int32_t i = 0; i < n; i++)
+        if (rp[i + 1] < rp[i])
+            return fail(ctx, PBCG_ERR_INVALID, "row_ptr decreases at row %d", i);
+    if ((int64_t)rp[n] != nnz)
+        return fail(ctx, PBCG_ERR_INVALID, "row_ptr[n] = %d differs from nnz = %lld", rp[n], (long long)nnz);
+    for (int64_t k = 0; k < nnz; k++)
+        if (ci[k] < 0 || ci[k] >= n)
+            return fail(ctx, PBCG_ERR_INVALID, "col_idx[%lld] = %d outside [0, %d)", (long long)k, ci[k], n);
+    return 0;
+}
+
+template <int MODE>
+struct Kern {
+    static void *setup1() { return (void *)k_setup1<MODE>; }
+    static void *setup2() { return (void *)k_setup2<MODE>; }
+    static void *pipe_x() { return (void *)k_pipe_x<MODE>; }
+    static void *pipe_y() { return (void *)k_pipe_y<MODE>; }
+    static void *bicg_a() { return (void *)k_bicg_a<MODE>; }
+    static void *bicg_b() { return (void *)k_bicg_b<MODE>; }
+    static void *bicg_c() { return (void *)k_bicg_c<MODE>; }
+};
+
+// kernel list of one loop body
+struct BodyKernel {
+    void *fn;
+    const char *name;
+    int has_work;    // kernel takes (Csr, Vecs, Ctl*, Work*) rather than (Csr, Vecs, const Ctl*)
+};
+
+std::vector<BodyKernel> body_kernels(int alg, int mode)
+{
+    std::vector<BodyKernel> k;
+    if (alg == PBCG_ALG_PIPELINED) {
+        k.push_back({mode ? Kern<1>::pipe_x() : Kern<0>::pipe_x(), mode ? "pipe_x_exact" : "pipe_x_plain", 1});
+        k.push_back({mode ? Kern<1>::pipe_y() : Kern<0>::pipe_y(), mode ? "pipe_y_exact" : "pipe_y_plain", 1});
+    } else {
+        k.push_back({(void *)k_bicg_p, "bicg_p", 0});
+        k.push_back({mode ? Kern<1>::bicg_a() : Kern<0>::bicg_a(), mode ? "bicg_a_exact" : "bicg_a_plain", 1});
+        k.push_back({mode ? Kern<1>::bicg_b() : Kern<0>::bicg_b(), mode ? "bicg_b_exact" : "bicg_b_plain", 1});
+        k.push_back({mode ? Kern<1>::bicg_c() : Kern<0>::bicg_c(), mode ? "bicg_c_exact" : "bicg_c_plain", 1});
+    }
+    return k;
+}
+
+int launch_kernel(pbcg_ctx *ctx, void *fn, int grid, Csr &A, Vecs &V, Ctl *c, Work *wk, int has_work)
+{
+    void *args4[4] = {&A, &V, &c, &wk};
+    void *args3[3] = {&A, &V, &c};
+    CK(cudaLaunchKernel(fn, dim3(grid), dim3(THREADS), has_work ? args4 : args3, 0, ctx->stream));
+    return 0;
+}
+
+// build (or reuse) the WHILE-node loop graph for this matrix / algorithm / mode
+int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, LoopGraph **out)
+{
+    LoopGraph &L = ctx->ws.loop;
+    if (L.exec && L.mat == m && L.alg == alg && L.mode == mode && L.n == m->n) {
+        *out = &L;
+        return 0;
+    }
+    free_loop(L);
+    CK(cudaGraphCreate(&L.graph, 0));
+    CK(cudaGraphConditionalHandleCreate(&L.handle, L.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = L.handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, L.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // kernel parameter values are copied into the nodes when they are added
+    Csr A = csr_of(m);
+    Vecs V = vecs_of(ctx->ws);
+    Ctl *c = ctx->ws.ctl;
+    Work *wk = ctx->ws.wk;
+    int grid = grid_for(ctx, m->n);
+    cudaGraphNode_t prev = nullptr;
+    for (auto &bk : body_kernels(alg, mode)) {
+        void *args4[4] = {&A, &V, &c, &wk};
+        void *args3[3] = {&A, &V, &c};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = bk.fn;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(THREADS);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = bk.has_work ? args4 : args3;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        prev = node;
+    }
+    CK(cudaGraphInstantiate(&L.exec, L.graph, 0));
+    L.alg = alg;
+    L.mode = mode;
+    L.mat = m;
+    L.n = m->n;
+    *out = &L;
+    return 0;
+}
+
+int read_ctl(pbcg_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+// profiling support: events around launches, accumulated per kernel name
+struct Prof {
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<int> count;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> which;
+    void add(const std::string &n, float t)
+    {
+        for (size_t i = 0; i < names.size(); i++)
+            if (names[i] == n) {
+                ms[i] += t;
+                count[i]++;
+                return;
+            }
+        names.push_back(n);
+        ms.push_back(t);
+        count.push_back(1);
+    }
+};
+
+// launch with optional timing
+struct Launcher {
+    pbcg_ctx *ctx;
+    Prof *prof;
+    std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+
+    int go(const char *name, void *fn, int grid, Csr &A, Vecs &V, Ctl *c, Work *wk, int has_work)
+    {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (prof) {
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventRecord(e0, ctx->stream));
+        }
+        int rc = launch_kernel(ctx, fn, grid, A, V, c, wk, has_work);
+        if (rc)
+            return rc;
+        if (prof) {
+            CK(cudaEventRecord(e1, ctx->stream));
+            pending.push_back({name, {e0, e1}});
+        }
+        return 0;
+    }
+    int flush()
+    {
+        for (auto &p : pending) {
+            CK(cudaEventSynchronize(p.second.second));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, p.second.first, p.second.second));
+            prof->add(p.first, t);
+            cudaEventDestroy(p.second.first);
+            cudaEventDestroy(p.second.second);
+        }
+        pending.clear();
+        return 0;
+    }
+};
+
+int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, double tol, int32_t maxit, int alg,
+               int mode, pbcg_result *out, Prof *prof)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!m || !ctx->mats.count(const_cast<pbcg_mat *>(m)))
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
+    if (!b || !x)
+        return fail(ctx, PBCG_ERR_INVALID, "b and x must not be NULL");
+    if (!(tol > 0.0))
+        return fail(ctx, PBCG_ERR_INVALID, "tol must be > 0");
+    if (maxit < 0)
+        return fail(ctx, PBCG_ERR_INVALID, "maxit must be >= 0");
+    if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", alg);
+    if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", mode);
+    CK(cudaSetDevice(ctx->device));
+    int n = m->n;
+    int rc = ensure_ws(ctx, n, maxit + 1);
+    if (rc)
+        return rc;
+    Workspace &ws = ctx->ws;
+    CK(cudaMemcpyAsync(ws.vec[V_B], b, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(ws.vec[V_X], x, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
+    Ctl h;
+    memset(&h, 0, sizeof h);
+    h.it = 0;
+    h.maxit = maxit;
+    h.status = ST_RUNNING;
+    h.tol = tol;
+    h.target = tol;
+    h.alg = alg;
+    h.use_cond = 0;
+    h.hist = ws.hist;
+    h.hist_cap = maxit + 1;
+    h.trueres = __builtin_nan("");
+    *ctx->h_ctl = h;
+    CK(cudaMemcpyAsync(ws.ctl, ctx->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+
+    Csr A = csr_of(m);
+    Vecs V = vecs_of(ws);
+    int grid = grid_for(ctx, n);
+    Launcher L{ctx, prof, {}};
+    if (alg == PBCG_ALG_PIPELINED) {
+        rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), grid, A, V, ws.ctl, ws.wk, 1);
+        if (!rc)
+            rc = L.go("setup2", mode ? Kern<1>::setup2() : Kern<0>::setup2(), grid, A, V, ws.ctl, ws.wk, 1);
+        if (!rc)
+            rc = L.go("setup3", (void *)k_setup3, grid, A, V, ws.ctl, ws.wk, 0);
+    } else {
+        rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), grid, A, V, ws.ctl, ws.wk, 1);
+    }
+    if (rc)
+        return rc;
+    bool cond_on = false;
+    bool true_done = false;
+    auto body = body_kernels(alg, mode);
+    for (;;) {
+        if (prof && (rc = L.flush()))
+            return rc;
+        if ((rc = read_ctl(ctx)))
+            return rc;
+        int st = ctx->h_ctl->status;
+        if (st == ST_CANDIDATE) {
+            rc = L.go("true_res", (void *)k_true_res, grid, A, V, ws.ctl, ws.wk, 1);
+            if (rc)
+                return rc;
+            true_done = true;
+            continue;
+        }
+        if (st != ST_RUNNING)
+            break;
+        true_done = false;
+        if (prof) {
+            // host-driven iteration, one kernel at a time
+            for (auto &bk : body)
+                if ((rc = L.go(bk.name, bk.fn, grid, A, V, ws.ctl, ws.wk, bk.has_work)))
+                    return rc;
+        } else {
+            LoopGraph *G = nullptr;
+            if ((rc = get_loop(ctx, m, alg, mode, &G)))
+                return rc;
+            if (!cond_on) {
+                int one = 1;
+                unsigned long long hv = (unsigned long long)G->handle;
+                CK(cudaMemcpyAsync(&ws.ctl->cond, &hv, sizeof hv, cudaMemcpyHostToDevice, ctx->stream));
+                CK(cudaMemcpyAsync(&ws.ctl->use_cond, &one, sizeof one, cudaMemcpyHostToDevice, ctx->stream));
+                cond_on = true;
+            }
+            CK(cudaGraphLaunch(G->exec, ctx->stream));
+        }
+    }
+    if (!true_done) {
+        if ((rc = L.go("true_res", (void *)k_true_res, grid, A, V, ws.ctl, ws.wk, 1)))
+            return rc;
+        if (prof && (rc = L.flush()))
+            return rc;
+        if ((rc = read_ctl(ctx)))
+            return rc;
+    }
+    if (cond_on) {
+        int zero = 0;
+        CK(cudaMemcpyAsync(&ws.ctl->use_cond, &zero, sizeof zero, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    Ctl fin_ctl = *ctx->h_ctl;
+    CK(cudaMemcpyAsync(x, ws.vec[V_X], sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
+    int hl = fin_ctl.it + 1;
+    if (hl > maxit + 1)
+        hl = maxit + 1;
+    ctx->hist.assign(hl, 0.0);
+    CK(cudaMemcpyAsync(ctx->hist.data(), ws.hist, sizeof(double) * hl, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->have_hist = true;
+    if (out) {
+        out->iters = fin_ctl.it;
+        out->status = fin_ctl.status;
+        out->relres_recursive = fin_ctl.res;
+        out->relres_true = fin_ctl.trueres;
+        out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return fin_ctl.status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pbcg_create(pbcg_ctx **out, int device, void *cuda_stream)
+{
+    if (!out)
+        return PBCG_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return PBCG_ERR_INVALID;
+    pbcg_ctx *ctx = new pbcg_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return PBCG_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    ctx->maxgrid = ctx->num_sms * (2048 / THREADS);
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return PBCG_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaMallocHost(&ctx->h_ctl, sizeof(Ctl)) != cudaSuccess) {
+        if (ctx->own_stream)
+            cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return PBCG_ERR_OOM;
+    }
+    *out = ctx;
+    return 0;
+}
+
+void pbcg_destroy(pbcg_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto *m : ctx->mats) {
+        cudaFree(m->rp);
+        cudaFree(m->ci);
+        cudaFree(m->va);
+        delete m;
+    }
+    ctx->mats.clear();
+    free_ws(ctx->ws);
+    if (ctx->h_ctl)
+        cudaFreeHost(ctx->h_ctl);
+    if (ctx->own_stream)
+        cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *pbcg_last_error(pbcg_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "no context";
+}
+
+int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                    const double *vals, int ptrs_on_device, pbcg_mat **out)
+{
+    (void)ptrs_on_device;
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!out || !row_ptr || (nnz > 0 && (!col_idx || !vals)))
+        return fail(ctx, PBCG_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    if (n < 1)
+        return fail(ctx, PBCG_ERR_INVALID, "n must be >= 1 (got %d)", n);
+    if (nnz < 0 || nnz >= (1ll << 31))
+        return fail(ctx, PBCG_ERR_INVALID, "nnz out of range (got %lld)", (long long)nnz);
+    CK(cudaSetDevice(ctx->device));
+    // bring the index arrays to the host for validation
+    std::vector<int32_t> hrp((size_t)n + 1), hci((size_t)nnz);
+    CK(cudaMemcpy(hrp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDefault));
+    if (nnz)
+        CK(cudaMemcpy(hci.data(), col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDefault));
+    int rc = validate_csr_host(ctx, n, nnz, hrp.data(), hci.data());
+    if (rc)
+        return rc;
+    pbcg_mat *m = new pbcg_mat();
+    m->n = n;
+    m->nnz = nnz;
+    m->rp = nullptr;
+    m->ci = nullptr;
+    m->va = nullptr;
+    cudaError_t e = cudaMalloc(&m->rp, sizeof(int32_t) * ((size_t)n + 1));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->ci, sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->va, sizeof(double) * (size_t)(nnz ? nnz : 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->rp, hrp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz)
+        e = cudaMemcpy(m->ci, hci.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz)
+        e = cudaMemcpy(m->va, vals, sizeof(double) * (size_t)nnz, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+        cudaFree(m->rp);
+        cudaFree(m->ci);
+        cudaFree(m->va);
+        delete m;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "matrix upload: %s",
+                    cudaGetErrorString(e));
+    }
+    ctx->mats.insert(m);
+    *out = m;
+    return 0;
+}
+
+int pbcg_mat_free(pbcg_ctx *ctx, pbcg_mat *m)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!m)
+        return 0;
+    if (!ctx->mats.count(m))
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws.loop.mat == m)
+        free_loop(ctx->ws.loop);
+    cudaFree(m->rp);
+    cudaFree(m->ci);
+    cudaFree(m->va);
+    ctx->mats.erase(m);
+    delete m;
+    return 0;
+}
+
+int pbcg_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double *x, double tol, int32_t maxit, int alg,
+               int dot_mode, pbcg_result *out)
+{
+    return solve_impl(ctx, A, b, x, tol, maxit, alg, dot_mode, out, nullptr);
+}
+
+int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double *x, double tol, int32_t maxit,
+                       int alg, int dot_mode, pbcg_result *out, char (*names)[32], double *ms, int32_t *launches,
+                       int32_t cap, int32_t *count)
+{
+    Prof prof;
+    int rc = solve_impl(ctx, A, b, x, tol, maxit, alg, dot_mode, out, &prof);
+    if (rc < 0)
+        return rc;
+    int k = (int)prof.names.size();
+    if (count)
+        *count = k;
+    for (int i = 0; i < k && i < cap; i++) {
+        if (names) {
+            strncpy(names[i], prof.names[i].c_str(), 31);
+            names[i][31] = '\0';
+        }
+        if (ms)
+            ms[i] = prof.ms[i];
+        if (launches)
+            launches[i] = prof.count[i];
+    }
+    return rc;
+}
+
+int pbcg_residual_history(pbcg_ctx *ctx, int32_t sys, double *out, int32_t cap, int32_t *len)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (sys != 0 || !ctx->have_hist)
+        return fail(ctx, PBCG_ERR_INVALID, "no residual history for system %d", sys);
+    int32_t L = (int32_t)ctx->hist.size();
+    if (len)
+        *len = L;
+    if (out && cap > 0)
+        memcpy(out, ctx->hist.data(), sizeof(double) * (size_t)(cap < L ? cap : L));
+    return 0;
+}
+
+int pbcg_dot(pbcg_ctx *ctx, int64_t n, const double *a, const double *b, int dot_mode, double *out)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (n < 0 || (n > 0 && (!a || !b)) || !out)
+        return fail(ctx, PBCG_ERR_INVALID, "bad dot arguments");
+    if (dot_mode != PBCG_DOT_PLAIN && dot_mode != PBCG_DOT_EXACT)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", dot_mode);
+    CK(cudaSetDevice(ctx->device));
+    int rc = ensure_ws(ctx, 0, 0);
+    if (rc)
+        return rc;
+    double *da = nullptr, *db = nullptr;
+    cudaPointerAttributes pa, pb;
+    bool a_dev = n > 0 && cudaPointerGetAttributes(&pa, a) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
+    bool b_dev = n > 0 && cudaPointerGetAttributes(&pb, b) == cudaSuccess && pb.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    if (n > 0 && !a_dev) {
+        CK(cudaMalloc(&da, sizeof(double) * (size_t)n));
+        CK(cudaMemcpyAsync(da, a, sizeof(double) * (size_t)n, cudaMemcpyDefault, ctx->stream));
+    }
+    if (n > 0 && !b_dev) {
+        CK(cudaMalloc(&db, sizeof(double) * (size_t)n));
+        CK(cudaMemcpyAsync(db, b, sizeof(double) * (size_t)n, cudaMemcpyDefault, ctx->stream));
+    }
+    const double *pa_ = a_dev ? a : da, *pb_ = b_dev ? b : db;
+    long long tiles = (n + 31) / 32;
+    long long g = (tiles + WARPS - 1) / WARPS;
+    int grid = (int)(g < 1 ? 1 : (g > ctx->maxgrid ? ctx->maxgrid : g));
+    long long nn = n;
+    double *o = ctx->ws.dot_out;
+    Work *wk = ctx->ws.wk;
+    void *args[5] = {&nn, &pa_, &pb_, &o, &wk};
+    CK(cudaLaunchKernel(dot_mode ? (void *)k_dot<1> : (void *)k_dot<0>, dim3(grid), dim3(THREADS), args, 0,
+                        ctx->stream));
+    CK(cudaMemcpyAsync(out, o, sizeof(double), cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (da)
+        cudaFree(da);
+    if (db)
+        cudaFree(db);
+    return 0;
+}
+
+int pbcg_spmv(pbcg_ctx *ctx, const pbcg_mat *m, const double *x, double *y)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!m || !ctx->mats.count(const_cast<pbcg_mat *>(m)))
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
+    if (!x || !y)
+        return fail(ctx, PBCG_ERR_INVALID, "x and y must not be NULL");
+    CK(cudaSetDevice(ctx->device));
+    int n = m->n;
+    double *dx = nullptr, *dy = nullptr;
+    CK(cudaMalloc(&dx, sizeof(double) * (size_t)n));
+    CK(cudaMalloc(&dy, sizeof(double) * (size_t)n));
+    CK(cudaMemcpyAsync(dx, x, sizeof(double) * (size_t)n, cudaMemcpyDefault, ctx->stream));
+    Csr A = csr_of(m);
+    void *args[3] = {&A, &dx, &dy};
+    CK(cudaLaunchKernel((void *)k_spmv, dim3(grid_for(ctx, n)), dim3(THREADS), args, 0, ctx->stream));
+    CK(cudaMemcpyAsync(y, dy, sizeof(double) * (size_t)n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(dx);
+    cudaFree(dy);
+    return 0;
+}
+
+int pbcg_solve_batched(pbcg_ctx *ctx, const pbcg_mat *A, int32_t nsys, const int32_t *sys_row_ptr, const double *b,
+                       double *x, const double *tol, int32_t maxit, int alg, int dot_mode, pbcg_result *out)
+{
+    (void)A; (void)nsys; (void)sys_row_ptr; (void)b; (void)x; (void)tol; (void)maxit; (void)alg; (void)dot_mode;
+    (void)out;
+    return fail(ctx, PBCG_ERR_INVALID, "batched solve not available in this build");
+}
+
+}  // extern "C"

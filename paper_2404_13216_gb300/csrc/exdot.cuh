@@ -1,0 +1,363 @@
+// exdot.cuh -- exact, correctly rounded FP64 dot products on sm_103a using
+// integer arithmetic only.
+//
+// Section 2 of arXiv 2404.13216 replaces residual replacement in p-BiCGStab by
+// ExBLAS dot products: a long fixed-point accumulator fed by floating-point
+// expansions, rounded once, independent of data partitioning and reduction
+// order.  GB300 issues FP64 at roughly 2 FMA per clock per SM against about 64
+// integer operations, so this engine keeps the long-accumulator idea but builds
+// every stage from integer instructions:
+//
+//   1. decode both doubles into (sign, 53-bit integer mantissa, exponent) with
+//      bit operations;
+//   2. form the exact 106-bit mantissa product with four 32x32->64 multiplies;
+//   3. add it, as a signed 256-bit two's-complement number, into a per-lane
+//      register window whose bit position (the anchor) is shared by the warp;
+//      a product that falls outside the window goes straight to the CTA's
+//      accumulator with shared-memory atomics;
+//   4. at the end of a pass the warp sums its windows (butterfly with carries)
+//      and adds the total into the CTA accumulator: 32-bit digits held in
+//      int64 (carry-save), bit 0 of digit 0 weighing 2^-2148;
+//   5. each CTA adds its touched digits into one global accumulator per dot
+//      with 64-bit atomics (integer addition is associative, so arrival order
+//      does not matter);
+//   6. the last CTA to finish normalises the carries and rounds the exact sum
+//      to the nearest double (ties to even, subnormals exact, overflow to inf).
+//
+// Every stage is exact, so the rounded value is RN(sum a_i b_i) whatever the
+// grid shape, row assignment or batch composition.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pbcg {
+
+constexpr int NDIG = 136;        // 32-bit digits; 136*32 = 4352 bits cover 2^-2148 .. 2^2048 plus carries
+constexpr int WIN_SMAX = 120;    // largest left shift of a product inside a 256-bit window
+constexpr int WIN_ROOM = 24;     // bits of room left above the first product when anchoring
+
+// ---------------------------------------------------------------------------
+// decode and exact product
+// ---------------------------------------------------------------------------
+struct Prod {
+    uint32_t w0, w1, w2, w3;     // |a*b| mantissa product (< 2^106)
+    int off;                     // bit offset of its LSB above 2^-2148, or -1 for a zero product
+    uint32_t neg;                // 1 if a*b < 0
+    bool nonfinite;              // an operand is Inf or NaN
+};
+
+__device__ __forceinline__ Prod exact_product(double a, double b)
+{
+    Prod p;
+    unsigned long long ba = (unsigned long long)__double_as_longlong(a);
+    unsigned long long bb = (unsigned long long)__double_as_longlong(b);
+    uint32_t ahi = (uint32_t)(ba >> 32), alo = (uint32_t)ba;
+    uint32_t bhi = (uint32_t)(bb >> 32), blo = (uint32_t)bb;
+    uint32_t ea = (ahi >> 20) & 0x7ffu, eb = (bhi >> 20) & 0x7ffu;
+    p.nonfinite = (ea == 0x7ffu) | (eb == 0x7ffu);
+    p.neg = (ahi ^ bhi) >> 31;
+    uint32_t ma = (ahi & 0xfffffu) | (ea ? 0x100000u : 0u);   // high 21 mantissa bits
+    uint32_t mb = (bhi & 0xfffffu) | (eb ? 0x100000u : 0u);
+    bool zero = ((ma | alo) == 0u) | ((mb | blo) == 0u);
+    // (ma:alo) * (mb:blo), 53 x 53 -> 106 bits
+    unsigned long long p0 = (unsigned long long)alo * blo;
+    unsigned long long m = (unsigned long long)ma * blo + (p0 >> 32);
+    m = (unsigned long long)alo * mb + m;
+    unsigned long long h = (unsigned long long)ma * mb + (m >> 32);
+    p.w0 = (uint32_t)p0;
+    p.w1 = (uint32_t)m;
+    p.w2 = (uint32_t)h;
+    p.w3 = (uint32_t)(h >> 32);
+    // LSB exponent of a double: max(e,1) - 1075; offset above 2^-2148
+    int eea = ea ? (int)ea : 1, eeb = eb ? (int)eb : 1;
+    p.off = (zero | p.nonfinite) ? -1 : (eea + eeb - 2);
+    return p;
+}
+
+// signed product words shifted left by r (0..31): u0..u4, u4 carrying the sign
+struct Shifted {
+    uint32_t u0, u1, u2, u3, u4, sgn;
+};
+
+__device__ __forceinline__ Shifted signed_shift(const Prod &p, uint32_t r)
+{
+    uint32_t mask = 0u - p.neg;
+    uint32_t w0 = p.w0 ^ mask, w1 = p.w1 ^ mask, w2 = p.w2 ^ mask, w3 = p.w3 ^ mask;
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.cc.u32 %2, %2, 0;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
+        : "r"(p.neg));
+    Shifted s;
+    s.sgn = mask;
+    s.u0 = w0 << r;
+    s.u1 = __funnelshift_l(w0, w1, r);
+    s.u2 = __funnelshift_l(w1, w2, r);
+    s.u3 = __funnelshift_l(w2, w3, r);
+    s.u4 = __funnelshift_l(w3, mask, r);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// CTA accumulator (shared memory) for ND dots
+// ---------------------------------------------------------------------------
+template <int ND>
+struct CtaAcc {
+    unsigned long long dig[ND][NDIG];   // carry-save signed digits (two's complement int64)
+    int kmin[ND], kmax[ND];
+    int nf[ND];
+};
+
+template <int ND>
+__device__ __forceinline__ void cta_acc_init(CtaAcc<ND> &c)
+{
+    unsigned long long *d = &c.dig[0][0];
+    for (int i = threadIdx.x; i < ND * NDIG; i += blockDim.x)
+        d[i] = 0ull;
+    if (threadIdx.x < ND) {
+        c.kmin[threadIdx.x] = NDIG;
+        c.kmax[threadIdx.x] = -1;
+        c.nf[threadIdx.x] = 0;
+    }
+}
+
+template <int ND>
+__device__ __forceinline__ void cta_touch(CtaAcc<ND> &c, int d, int k0, int k1)
+{
+    atomicMin(&c.kmin[d], k0);
+    atomicMax(&c.kmax[d], k1);
+}
+
+// slow path: one lane adds one product straight into the CTA digits
+template <int ND>
+__device__ __noinline__ void cta_add_product(CtaAcc<ND> &c, int d, const Prod &p)
+{
+    int k = p.off >> 5;
+    Shifted s = signed_shift(p, (uint32_t)(p.off & 31));
+    unsigned long long *g = c.dig[d];
+    atomicAdd(&g[k + 0], (unsigned long long)s.u0);
+    atomicAdd(&g[k + 1], (unsigned long long)s.u1);
+    atomicAdd(&g[k + 2], (unsigned long long)s.u2);
+    atomicAdd(&g[k + 3], (unsigned long long)s.u3);
+    atomicAdd(&g[k + 4], (unsigned long long)(long long)(int)s.u4);
+    cta_touch(c, d, k, k + 4);
+}
+
+// ---------------------------------------------------------------------------
+// per-lane window: 256-bit two's complement, LSB at bit `anchor` (warp-uniform)
+// ---------------------------------------------------------------------------
+struct Win {
+    uint32_t a[8];
+    int anchor;      // -1 while unset
+};
+
+__device__ __forceinline__ void win_init(Win &w)
+{
+#pragma unroll
+    for (int t = 0; t < 8; t++)
+        w.a[t] = 0u;
+    w.anchor = -1;
+}
+
+__device__ __forceinline__ void add256(uint32_t (&a)[8], uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                       uint32_t x4, uint32_t x5, uint32_t x6, uint32_t x7)
+{
+    asm("add.cc.u32 %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32 %7, %7, %15;"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7])
+        : "r"(x0), "r"(x1), "r"(x2), "r"(x3), "r"(x4), "r"(x5), "r"(x6), "r"(x7));
+}
+
+// Deposit a*b.  Must be called by all 32 lanes of the warp together (the
+// anchor is chosen with a warp reduction); `active` masks lanes with no term.
+template <int ND>
+__device__ __forceinline__ void win_deposit(Win &w, CtaAcc<ND> &c, int d, double a, double b, bool active,
+                                            bool &nf)
+{
+    Prod p = exact_product(a, b);
+    if (!active) {
+        p.off = -1;
+        p.nonfinite = false;
+    }
+    nf |= p.nonfinite;
+    if (w.anchor < 0) {                                   // warp-uniform branch
+        int m = __reduce_max_sync(0xffffffffu, p.off);
+        if (m >= 0)
+            w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
+    }
+    if (p.off < 0)
+        return;
+    int sh = p.off - w.anchor;
+    if (w.anchor >= 0 && sh >= 0 && sh <= WIN_SMAX) {
+        Shifted s = signed_shift(p, (uint32_t)(sh & 31));
+        uint32_t q = (uint32_t)sh >> 5;                   // 0..3 whole words
+        bool qa = q & 1u, qb = q & 2u;
+        uint32_t v0 = qa ? 0u : s.u0, v1 = qa ? s.u0 : s.u1, v2 = qa ? s.u1 : s.u2;
+        uint32_t v3 = qa ? s.u2 : s.u3, v4 = qa ? s.u3 : s.u4, v5 = qa ? s.u4 : s.sgn;
+        uint32_t x0 = qb ? 0u : v0, x1 = qb ? 0u : v1, x2 = qb ? v0 : v2, x3 = qb ? v1 : v3;
+        uint32_t x4 = qb ? v2 : v4, x5 = qb ? v3 : v5, x6 = qb ? v4 : s.sgn, x7 = qb ? v5 : s.sgn;
+        add256(w.a, x0, x1, x2, x3, x4, x5, x6, x7);
+    } else {
+        cta_add_product(c, d, p);
+    }
+}
+
+// Sum the warp's windows and add the total into the CTA digits.  All lanes call.
+template <int ND>
+__device__ __forceinline__ void win_flush(Win &w, CtaAcc<ND> &c, int d)
+{
+    if (w.anchor < 0)
+        return;                                           // warp-uniform: nothing deposited
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint32_t y[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++)
+            y[t] = __shfl_xor_sync(0xffffffffu, w.a[t], o);
+        add256(w.a, y[0], y[1], y[2], y[3], y[4], y[5], y[6], y[7]);
+    }
+    int k = w.anchor >> 5;
+    uint32_t r = (uint32_t)(w.anchor & 31);
+    uint32_t sg = (uint32_t)((int)w.a[7] >> 31);
+    uint32_t z[9];
+    z[0] = w.a[0] << r;
+#pragma unroll
+    for (int t = 1; t < 8; t++)
+        z[t] = __funnelshift_l(w.a[t - 1], w.a[t], r);
+    z[8] = __funnelshift_l(w.a[7], sg, r);
+    int lane = threadIdx.x & 31;
+    uint32_t mine = 0u;
+#pragma unroll
+    for (int t = 0; t < 9; t++)
+        mine = (lane == t) ? z[t] : mine;
+    if (lane < 9) {
+        unsigned long long v = (lane < 8) ? (unsigned long long)mine : (unsigned long long)(long long)(int)mine;
+        if (v != 0ull)
+            atomicAdd(&c.dig[d][k + lane], v);
+    }
+    if (lane == 0)
+        cta_touch(c, d, k, k + 8);
+}
+
+// ---------------------------------------------------------------------------
+// global accumulator: one per dot, merged by integer atomics
+// ---------------------------------------------------------------------------
+struct GAcc {
+    unsigned long long dig[NDIG];
+    int kmin, kmax, nf, pad;
+};
+
+template <int ND>
+__device__ __forceinline__ void cta_to_global(CtaAcc<ND> &c, GAcc *g)
+{
+    for (int d = 0; d < ND; d++) {
+        int k0 = c.kmin[d], k1 = c.kmax[d];
+        for (int k = k0 + (int)threadIdx.x; k <= k1; k += blockDim.x) {
+            unsigned long long v = c.dig[d][k];
+            if (v != 0ull)
+                atomicAdd(&g[d].dig[k], v);
+        }
+        if (threadIdx.x == 0) {
+            if (k1 >= k0) {
+                atomicMin(&g[d].kmin, k0);
+                atomicMax(&g[d].kmax, k1);
+            }
+            if (c.nf[d])
+                atomicOr(&g[d].nf, 1);
+        }
+    }
+}
+
+// Round the exact sum held in g (read through L2) to the nearest double and
+// reset g for the next use.  Called by one thread; `scratch` is NDIG words.
+__device__ __forceinline__ uint32_t bit_at(const uint32_t *w, int lo, int hi, int i)
+{
+    int k = i >> 5;
+    if (k < lo || k > hi)
+        return 0u;
+    return (w[k] >> (i & 31)) & 1u;
+}
+
+__device__ double gacc_round_reset(GAcc *g, uint32_t *scratch)
+{
+    int nf = *((volatile int *)&g->nf);
+    int k0 = *((volatile int *)&g->kmin), k1 = *((volatile int *)&g->kmax);
+    double result = 0.0;
+    if (nf) {
+        result = __longlong_as_double(0x7ff8000000000000ll);
+    } else if (k1 >= k0) {
+        // carry normalisation from k0 upward; digits above k1 start at 0
+        long long carry = 0;
+        int top = k0;
+        for (int k = k0; k < NDIG; k++) {
+            long long v = (k <= k1) ? (long long)__ldcg(&g->dig[k]) : 0ll;
+            // v + carry without overflow: |digit| < 2^62 and |carry| < 2^31 here
+            long long s = v + carry;
+            scratch[k] = (uint32_t)s;
+            carry = s >> 32;
+            top = k;
+            // stop once the rest is pure sign extension of a canonical top word
+            if (k >= k1 && ((carry == 0 && !(scratch[k] >> 31)) || (carry == -1 && (scratch[k] >> 31))))
+                break;
+        }
+        bool negv = carry < 0;
+        if (negv) {
+            // magnitude = -value over digits k0..top (infinite sign extension above)
+            uint32_t c1 = 1u;
+            for (int k = k0; k <= top; k++) {
+                uint32_t x = ~scratch[k];
+                unsigned long long s = (unsigned long long)x + c1;
+                scratch[k] = (uint32_t)s;
+                c1 = (uint32_t)(s >> 32);
+            }
+        }
+        int hk = -1;
+        for (int k = top; k >= k0; k--) {
+            if (scratch[k] != 0u) {
+                hk = k;
+                break;
+            }
+        }
+        if (hk >= 0) {
+            int h = hk * 32 + 31 - __clz(scratch[hk]);
+            int lsb = max(h - 52, 1074);
+            unsigned long long m = 0ull;
+            for (int i = h; i >= lsb; i--)
+                m = (m << 1) | bit_at(scratch, k0, top, i);
+            uint32_t rb = bit_at(scratch, k0, top, lsb - 1);
+            uint32_t st = 0u;
+            int sk = (lsb - 1) >> 5;
+            for (int k = k0; k < sk && k <= top; k++)
+                st |= scratch[k];
+            if (sk >= k0 && sk <= top)
+                st |= scratch[sk] & ((1u << ((lsb - 1) & 31)) - 1u);
+            if (rb && (st || (m & 1ull)))
+                m += 1ull;
+            // value = m * 2^(lsb - 2148); biased exponent field = lsb - 1074 (+1 via the implicit bit)
+            long long ef = (long long)(lsb - 1074);
+            unsigned long long bits = ((unsigned long long)ef << 52) + m;
+            if (bits >= 0x7ff0000000000000ull)
+                bits = 0x7ff0000000000000ull;            // overflow rounds to infinity
+            if (negv)
+                bits |= 0x8000000000000000ull;
+            result = __longlong_as_double((long long)bits);
+        } else if (negv) {
+            result = 0.0;
+        }
+        for (int k = k0; k <= k1; k++)
+            g->dig[k] = 0ull;
+    }
+    g->kmin = NDIG;
+    g->kmax = -1;
+    g->nf = 0;
+    return result;
+}
+
+}  // namespace pbcg

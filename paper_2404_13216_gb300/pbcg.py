@@ -1,0 +1,210 @@
+"""ctypes binding of libpbcg.so (include/pbcg.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels; this module moves
+pointers and sizes across the C ABI.  Arrays may be numpy arrays (host) or
+torch tensors (host or CUDA; their data_ptr is passed through).  Loading the
+module raises if the library has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpbcg.so")
+
+OK, MAXIT, BREAKDOWN, NONFINITE = 0, 1, 2, 3
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = -1, -2, -3, -4
+BICGSTAB, PIPELINED = 0, 1
+PLAIN, EXACT = 0, 1
+
+EXPORTS = ("pbcg_create", "pbcg_destroy", "pbcg_last_error", "pbcg_csr_upload", "pbcg_mat_free",
+           "pbcg_solve", "pbcg_solve_batched", "pbcg_residual_history", "pbcg_dot", "pbcg_spmv",
+           "pbcg_profile_solve")
+
+
+class PbcgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pbcg error {code}: {msg}")
+        self.code = code
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres_recursive", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2404_13216_gb300.build.build_library()")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.pbcg_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P]
+    lib.pbcg_create.restype = ctypes.c_int
+    lib.pbcg_destroy.argtypes = [P]
+    lib.pbcg_destroy.restype = None
+    lib.pbcg_last_error.argtypes = [P]
+    lib.pbcg_last_error.restype = ctypes.c_char_p
+    lib.pbcg_csr_upload.argtypes = [P, i32, i64, P, P, P, ctypes.c_int, ctypes.POINTER(P)]
+    lib.pbcg_csr_upload.restype = ctypes.c_int
+    lib.pbcg_mat_free.argtypes = [P, P]
+    lib.pbcg_mat_free.restype = ctypes.c_int
+    lib.pbcg_solve.argtypes = [P, P, P, P, d, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result)]
+    lib.pbcg_solve.restype = ctypes.c_int
+    lib.pbcg_solve_batched.argtypes = [P, P, i32, P, P, P, P, i32, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(_Result)]
+    lib.pbcg_solve_batched.restype = ctypes.c_int
+    lib.pbcg_residual_history.argtypes = [P, i32, P, i32, ctypes.POINTER(i32)]
+    lib.pbcg_residual_history.restype = ctypes.c_int
+    lib.pbcg_dot.argtypes = [P, i64, P, P, ctypes.c_int, ctypes.POINTER(d)]
+    lib.pbcg_dot.restype = ctypes.c_int
+    lib.pbcg_spmv.argtypes = [P, P, P, P]
+    lib.pbcg_spmv.restype = ctypes.c_int
+    lib.pbcg_profile_solve.argtypes = [P, P, P, P, d, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result),
+                                       P, P, P, i32, ctypes.POINTER(i32)]
+    lib.pbcg_profile_solve.restype = ctypes.c_int
+    return lib
+
+
+_lib = load_library()
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _host(a, dtype):
+    if hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+@dataclass
+class Result:
+    status: int
+    iters: int
+    relres_recursive: float
+    relres_true: float
+    seconds: float
+
+
+class Matrix:
+    def __init__(self, ctx: "Context", handle, n: int, nnz: int):
+        self.ctx, self.handle, self.n, self.nnz = ctx, handle, n, nnz
+
+    def free(self):
+        if self.handle:
+            self.ctx._check(_lib.pbcg_mat_free(self.ctx.handle, self.handle))
+            self.handle = None
+
+
+class Context:
+    """One libpbcg context: a device, a stream, its matrices and workspace."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream) if stream else None
+        rc = _lib.pbcg_create(ctypes.byref(h), int(device), s)
+        if rc != 0:
+            raise PbcgError(rc, "pbcg_create failed")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            _lib.pbcg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return _lib.pbcg_last_error(self.handle).decode()
+
+    def _check(self, rc: int) -> int:
+        if rc < 0:
+            raise PbcgError(rc, self.last_error())
+        return rc
+
+    def upload(self, row_ptr, col_idx, vals) -> Matrix:
+        rp, ci, va = _host(row_ptr, np.int32), _host(col_idx, np.int32), _host(vals, np.float64)
+        n = (rp.numel() if hasattr(rp, "numel") else rp.size) - 1
+        nnz = va.numel() if hasattr(va, "numel") else va.size
+        m = ctypes.c_void_p()
+        dev = int(hasattr(rp, "is_cuda") and rp.is_cuda)
+        self._check(_lib.pbcg_csr_upload(self.handle, n, nnz, _ptr(rp), _ptr(ci), _ptr(va), dev, ctypes.byref(m)))
+        return Matrix(self, m, n, nnz)
+
+    def upload_csr(self, A) -> Matrix:
+        return self.upload(A.row_ptr, A.col_idx, A.vals)
+
+    def solve(self, mat: Matrix, b, x, tol: float, maxit: int, alg: int = PIPELINED, mode: int = EXACT) -> Result:
+        """Solve in place: x holds x0 on entry and the last iterate on return."""
+        r = _Result()
+        self._check(_lib.pbcg_solve(self.handle, mat.handle, _ptr(b), _ptr(x), float(tol), int(maxit), int(alg),
+                                    int(mode), ctypes.byref(r)))
+        return Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds)
+
+    def solve_batched(self, mat: Matrix, sys_row_ptr, b, x, tol, maxit: int, alg: int = PIPELINED,
+                      mode: int = EXACT):
+        srp = _host(sys_row_ptr, np.int32)
+        nsys = (srp.numel() if hasattr(srp, "numel") else srp.size) - 1
+        tl = _host(tol, np.float64)
+        res = (_Result * nsys)()
+        self._check(_lib.pbcg_solve_batched(self.handle, mat.handle, nsys, _ptr(srp), _ptr(b), _ptr(x), _ptr(tl),
+                                            int(maxit), int(alg), int(mode), res))
+        return [Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds) for r in res]
+
+    def history(self, sys: int = 0) -> np.ndarray:
+        ln = ctypes.c_int32(0)
+        self._check(_lib.pbcg_residual_history(self.handle, int(sys), None, 0, ctypes.byref(ln)))
+        out = np.empty(ln.value, dtype=np.float64)
+        self._check(_lib.pbcg_residual_history(self.handle, int(sys), _ptr(out), ln.value, ctypes.byref(ln)))
+        return out
+
+    def dot(self, a, b, mode: int = EXACT) -> float:
+        a, b = _host(a, np.float64), _host(b, np.float64)
+        n = a.numel() if hasattr(a, "numel") else a.size
+        out = ctypes.c_double(0.0)
+        self._check(_lib.pbcg_dot(self.handle, n, _ptr(a), _ptr(b), int(mode), ctypes.byref(out)))
+        return out.value
+
+    def spmv(self, mat: Matrix, x, y=None):
+        x = _host(x, np.float64)
+        if y is None:
+            y = np.empty(mat.n, dtype=np.float64)
+        self._check(_lib.pbcg_spmv(self.handle, mat.handle, _ptr(x), _ptr(y)))
+        return y
+
+    def profile_solve(self, mat: Matrix, b, x, tol: float, maxit: int, alg: int = PIPELINED, mode: int = EXACT):
+        """Solve with a host-driven loop and CUDA events around every kernel.
+        Returns (Result, {kernel: (total_ms, launches)})."""
+        cap = 32
+        names = (ctypes.c_char * 32 * cap)()
+        ms = np.zeros(cap, dtype=np.float64)
+        cnt = np.zeros(cap, dtype=np.int32)
+        k = ctypes.c_int32(0)
+        r = _Result()
+        self._check(_lib.pbcg_profile_solve(self.handle, mat.handle, _ptr(b), _ptr(x), float(tol), int(maxit),
+                                            int(alg), int(mode), ctypes.byref(r), ctypes.cast(names, ctypes.c_void_p),
+                                            _ptr(ms), _ptr(cnt), cap, ctypes.byref(k)))
+        prof = {}
+        for i in range(min(k.value, cap)):
+            prof[bytes(names[i]).split(b"\0")[0].decode()] = (float(ms[i]), int(cnt[i]))
+        return Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds), prof

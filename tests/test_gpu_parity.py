@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Exact mode: residual history, iteration count, status and x bit-identical.
+Plain mode: history within a relative 1e-8 over the first 20 iterations and
+the true relative residual <= tol.  Dots and SpMV are checked on their own too.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2404_13216_gb300 import inputs
+from tests import dotcases
+
+pytestmark = pytest.mark.gpu
+
+PLAIN_HIST_RTOL = 1e-8      # relative, first 20 iterations (plain-mode dot order differs)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2404_13216_gb300 import build
+    build.build_library()
+    from paper_2404_13216_gb300 import pbcg
+    c = pbcg.Context(0)
+    yield c
+    c.close()
+
+
+def same(a, b):
+    return np.array_equal(np.asarray(a).view(np.int64), np.asarray(b).view(np.int64))
+
+
+# --------------------------------------------------------------------------- dots
+CASES = dotcases.cases(0)
+
+
+@pytest.mark.parametrize("name,a,b", CASES, ids=[c[0] for c in CASES])
+def test_exact_dot_bitwise(ctx, orc, name, a, b):
+    got = ctx.dot(a, b, mode=1)
+    want = orc.dot_exact(a, b)
+    if math.isnan(want):
+        assert math.isnan(got)
+    else:
+        assert same([got], [want]), (name, got, want)
+
+
+def test_exact_dot_large_random(ctx, orc):
+    rng = np.random.default_rng(11)
+    for n in (1, 31, 32, 33, 1000, 65537, 1_000_003):
+        a = rng.standard_normal(n) * np.ldexp(1.0, rng.integers(-40, 40, n))
+        b = rng.standard_normal(n) * np.ldexp(1.0, rng.integers(-300, 300, n))
+        assert same([ctx.dot(a, b, 1)], [orc.dot_exact(a, b, nthreads=8)]), n
+
+
+def test_exact_dot_empty_and_nonfinite(ctx):
+    assert ctx.dot(np.zeros(0), np.zeros(0), 1) == 0.0
+    a = np.ones(100)
+    a[57] = np.inf
+    assert math.isnan(ctx.dot(a, np.ones(100), 1))
+
+
+def test_plain_dot_close(ctx, orc):
+    rng = np.random.default_rng(12)
+    a, b = rng.standard_normal(100_000), rng.standard_normal(100_000)
+    want = orc.dot_exact(a, b)
+    assert abs(ctx.dot(a, b, 0) - want) <= 1e-12 * np.abs(a * b).sum()
+
+
+# --------------------------------------------------------------------------- SpMV
+@pytest.mark.parametrize("gen", ["2d64", "3d20", "powerlaw"])
+def test_spmv_bitwise(ctx, orc, gen):
+    if gen == "2d64":
+        A = inputs.convdiff2d(64, 10.0)
+    elif gen == "3d20":
+        A = inputs.convdiff3d(20, 50.0)
+    else:
+        A = inputs.powerlaw(n=5000, mean_len=30, max_len=400, seed=2)
+    M = ctx.upload_csr(A)
+    x = np.random.default_rng(1).standard_normal(A.n)
+    assert same(ctx.spmv(M, x), orc.spmv(A.row_ptr, A.col_idx, A.vals, x))
+    M.free()
+
+
+# --------------------------------------------------------------------------- solves
+def run_both(ctx, orc, A, b, tol, maxit, alg, mode, x0=None):
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, x0=x0, tol=tol, maxit=maxit, alg=alg, mode=mode, nthreads=8)
+    M = ctx.upload_csr(A)
+    x = np.zeros(A.n) if x0 is None else np.array(x0, dtype=np.float64)
+    res = ctx.solve(M, b, x, tol, maxit, alg, mode)
+    hist = ctx.history()
+    M.free()
+    return ref, res, x, hist
+
+
+SYSTEMS = {
+    "2d64_pe10": lambda: inputs.convdiff2d(64, 10.0),
+    "2d37_pe40": lambda: inputs.convdiff2d(37, 40.0),          # ragged: n = 1369
+    "3d24_pe50": lambda: inputs.convdiff3d(24, 50.0),
+    "2d5_pe3": lambda: inputs.convdiff2d(5, 3.0),               # n = 25 < one tile
+}
+
+
+@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
+@pytest.mark.parametrize("sysname", list(SYSTEMS))
+def test_exact_solve_bitwise(ctx, orc, sysname, alg):
+    A = SYSTEMS[sysname]()
+    b = inputs.rhs_ones(A)
+    ref, res, x, hist = run_both(ctx, orc, A, b, 1e-8, 2000, alg, 1)
+    assert res.status == ref.status and res.iters == ref.iters, (res, ref.status, ref.iters)
+    assert same(hist, ref.history)
+    assert same(x, ref.x)
+    assert same([res.relres_true], [ref.relres_true])
+
+
+@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
+@pytest.mark.parametrize("sysname", ["2d64_pe10", "3d24_pe50"])
+def test_plain_solve_tolerance(ctx, orc, sysname, alg):
+    A = SYSTEMS[sysname]()
+    b = inputs.rhs_ones(A)
+    tol = 1e-8
+    ref, res, x, hist = run_both(ctx, orc, A, b, tol, 2000, alg, 0)
+    assert res.status == 0 and res.relres_true <= tol
+    k = min(21, hist.size, ref.history.size)
+    rel = np.abs(hist[:k] - ref.history[:k]) / np.abs(ref.history[:k])
+    assert np.all(rel <= PLAIN_HIST_RTOL), rel.max()
+
+
+def test_golden_fixture_exact(ctx):
+    """The committed oracle fixture for the 64x64 system (tests/golden)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "convdiff64.json")))
+    A = inputs.convdiff2d(64, 10.0, (1.0, 0.5))
+    b = inputs.rhs_ones(A)
+    M = ctx.upload_csr(A)
+    for alg, an in ((0, "bicgstab"), (1, "pbicgstab")):
+        want = g["runs"][f"{an}_exact"]
+        x = np.zeros(A.n)
+        r = ctx.solve(M, b, x, 1e-8, 2000, alg, 1)
+        assert r.status == want["status"] and r.iters == want["iters"]
+        assert same(ctx.history(), np.array([float.fromhex(h) for h in want["history"]]))
+    M.free()
+
+
+# --------------------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_edge_cases(ctx, orc, alg, mode):
+    # one unknown
+    A = inputs.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]))
+    ref, res, x, hist = run_both(ctx, orc, A, np.array([6.0]), 1e-12, 10, alg, mode)
+    assert res.status == ref.status == 0 and res.iters == ref.iters and same(x, ref.x)
+    # exact start
+    A = inputs.convdiff2d(8, 3.0)
+    b = inputs.rhs_ones(A)
+    ref, res, x, hist = run_both(ctx, orc, A, b, 1e-12, 10, alg, mode, x0=np.ones(A.n))
+    assert res.status == 0 and res.iters == 0 and same(hist, ref.history)
+    # maxit = 0
+    ref, res, x, hist = run_both(ctx, orc, A, b, 1e-12, 0, alg, mode)
+    assert res.status == ref.status == 1 and res.iters == 0
+    # NaN in b
+    bn = b.copy()
+    bn[3] = np.nan
+    ref, res, x, hist = run_both(ctx, orc, A, bn, 1e-12, 10, alg, mode)
+    assert res.status == ref.status == 3 and res.iters == 0
+    # skew breakdown
+    A = inputs.CSR(2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([1.0, -1.0]))
+    ref, res, x, hist = run_both(ctx, orc, A, np.array([1.0, 0.0]), 1e-10, 10, alg, mode)
+    assert res.status == ref.status == 2 and res.iters == 0
+    # A = 4 I: lucky breakdown, exact in one step
+    n = 100
+    A = inputs.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.full(n, 4.0))
+    bb = np.random.default_rng(0).standard_normal(n)
+    ref, res, x, hist = run_both(ctx, orc, A, bb, 1e-14, 10, alg, mode)
+    assert res.status == 0 and res.iters == 1 and same(x, bb / 4.0)
+
+
+def test_invalid_inputs(ctx):
+    from paper_2404_13216_gb300 import pbcg
+    with pytest.raises(pbcg.PbcgError):
+        ctx.upload(np.array([0, 1, 2], np.int32), np.array([1, 5], np.int32), np.ones(2))
+    with pytest.raises(pbcg.PbcgError):
+        ctx.upload(np.array([0, 2, 1], np.int32), np.array([1, 0], np.int32), np.ones(2))
+    A = inputs.convdiff2d(4, 1.0)
+    M = ctx.upload_csr(A)
+    with pytest.raises(pbcg.PbcgError):
+        ctx.solve(M, np.ones(A.n), np.zeros(A.n), 0.0, 10)
+    with pytest.raises(pbcg.PbcgError):
+        ctx.solve(M, np.ones(A.n), np.zeros(A.n), 1e-8, -1)
+    with pytest.raises(pbcg.PbcgError):
+        ctx.solve(M, np.ones(A.n), np.zeros(A.n), 1e-8, 10, alg=7)
+    M.free()
+
+
+def test_device_pointers(ctx, orc):
+    import torch
+    A = inputs.convdiff2d(40, 20.0)
+    b = inputs.rhs_ones(A)
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-9, maxit=1000, alg=1, mode=1)
+    M = ctx.upload(torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col_idx).cuda(),
+                   torch.from_numpy(A.vals).cuda())
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    res = ctx.solve(M, bd, xd, 1e-9, 1000, 1, 1)
+    assert res.iters == ref.iters and same(xd.cpu().numpy(), ref.x)
+    M.free()
+
+
+# --------------------------------------------------------------------------- full size
+def test_full_size_128cubed_first_iterations(ctx, orc):
+    """3D 128^3 (n = 2,097,152): the first iterations in the launch shape the
+    benchmark uses are bit-identical to the oracle (plain: within tolerance)."""
+    A = inputs.convdiff3d(128, 50.0)
+    b = inputs.rhs_ones(A)
+    for mode in (1, 0):
+        ref, res, x, hist = run_both(ctx, orc, A, b, 1e-10, 4, 1, mode)
+        assert res.iters == ref.iters == 4
+        if mode == 1:
+            assert same(hist, ref.history) and same(x, ref.x)
+        else:
+            assert np.all(np.abs(hist - ref.history) <= PLAIN_HIST_RTOL * ref.history)
