@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark: exact-dot p-BiCGStab (Algorithm 2 of arXiv 2404.13216) on GB300.
+
+Workload: 3D convection-diffusion, 7-point upwind, 128^3 grid (n = 2,097,152,
+nnz = 14,581,760), wind (1, 0.5, 0.25), Peclet 50, FP64 CSR, b = A*ones,
+x0 = 0, relative tolerance 1e-10.  One step = one full solve (setup, the
+iteration loop, the true-residual check) with exact dot products; the same
+solves with plain FP64 dots are timed beside them.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is exact-mode iterations per second summed over
+ranks (each rank solves its own copy: replicas, weak scaling), inputs resident
+in HBM.  `e2e` repeats the measurement through the C ABI with pinned host
+buffers (host<->device copies inside the timed region).  `roofline` gives the
+dominant kernel's achieved HBM bandwidth (algorithmic bytes / CUDA-event time)
+against the measured copy bandwidth.  `cpu_baseline` times the CPU oracle on a
+bounded sample.  `--impl reference` times the CPU oracle alone (the reference
+arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "p-BiCGStab iters/s & HBM GB/s, exact vs plain dots; batched solves/s & p99"
+N_SIDE, PECLET, WIND, TOL, MAXIT = 128, 50.0, (1.0, 0.5, 0.25), 1e-10, 5000
+WORKLOAD = ("3D convection-diffusion 7-point upwind 128^3 (n=2097152, nnz=14581760), wind (1,0.5,0.25), "
+            "Peclet 50, FP64 CSR, b=A*ones, x0=0, rel tol 1e-10, p-BiCGStab")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        import tempfile
+        self.path = tempfile.mktemp(suffix=".csv")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        maxp = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * maxp] or rows
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[3]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": maxp, "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(A, b, nthreads: int, mode: int, iters: int):
+    """Time `iters` iterations of the CPU oracle's p-BiCGStab (setup excluded by
+    differencing a 1-iteration run)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=1, alg=oracle.PIPELINED, mode=mode,
+                 nthreads=nthreads)
+    t1 = time.perf_counter()
+    oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=1 + iters, alg=oracle.PIPELINED, mode=mode,
+                 nthreads=nthreads)
+    t2 = time.perf_counter()
+    dt = (t2 - t1) - (t1 - t0)
+    return iters / max(dt, 1e-9), dt
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2404_13216_gb300 import inputs
+    import oracle
+    oracle.build()
+    A = inputs.convdiff3d(N_SIDE, PECLET, WIND)
+    b = inputs.rhs_ones(A)
+    cores = os.cpu_count() or 1
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=per_step, alg=1, mode=1, nthreads=cores)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        r = oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=per_step, alg=1, mode=1,
+                         nthreads=cores)
+        its += r.iters
+    dt = time.perf_counter() - t0
+    v = its / dt
+    sample = (f"{per_step} exact p-BiCGStab iterations (setup included) per step on the 128^3 system, "
+              f"{cores} threads for exact dots, CPU {cpu_model()}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dots": "exact", "impl": "CPU oracle (oracle/oracle.c)"},
+        "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2404_13216_gb300 import build, inputs
+    build.build_library()
+    from paper_2404_13216_gb300 import pbcg
+
+    A = inputs.convdiff3d(N_SIDE, PECLET, WIND)
+    b = inputs.rhs_ones(A)
+    n, nnz = A.n, A.nnz
+    M_bytes, V_bytes = A.matrix_bytes(), 8 * n
+    stream = torch.cuda.current_stream(dev)
+    ctx = pbcg.Context(local, stream.cuda_stream)
+    M = ctx.upload_csr(A)
+    b_d = torch.from_numpy(b).to(dev)
+    x_d = torch.zeros(n, dtype=torch.float64, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(mode, steps, host=False):
+        """Run `steps` solves; CUDA-event time on the context's (torch's current) stream."""
+        if host:
+            bh = torch.from_numpy(b).pin_memory()
+            xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        its, launches, res = 0, 0, None
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            if host:
+                xh.zero_()
+                res = ctx.solve(M, bh, xh, TOL, MAXIT, pbcg.PIPELINED, mode)
+            else:
+                x_d.zero_()
+                res = ctx.solve(M, b_d, x_d, TOL, MAXIT, pbcg.PIPELINED, mode)
+            its += res.iters
+            launches += res.launches
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        hist = ctx.history() if not host else None
+        return ms, its, launches, res, hist
+
+    for mode in (pbcg.EXACT, pbcg.PLAIN):
+        for _ in range(args.warmup):
+            x_d.zero_()
+            ctx.solve(M, b_d, x_d, TOL, MAXIT, pbcg.PIPELINED, mode)
+
+    clk = Clocks(local)
+    clk.start()
+    ms_e, its_e, launches_e, res_e, hist_e = timed(pbcg.EXACT, args.steps)
+    clocks = clk.stop()
+    ms_p, its_p, launches_p, res_p, _ = timed(pbcg.PLAIN, args.steps)
+    ms_h, its_h, _, res_h, _ = timed(pbcg.EXACT, max(1, args.steps // 2), host=True)
+
+    def reduce(ms, its):
+        if dist is None:
+            return ms, its
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([its], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        return float(t.item()), int(c.item())
+
+    ms_e, its_e_all = reduce(ms_e, its_e)
+    ms_p, its_p_all = reduce(ms_p, its_p)
+    ms_h, its_h_all = reduce(ms_h, its_h)
+
+    # per-kernel durations with CUDA events around each launch (host-driven loop, same kernels and grid)
+    x_d.zero_()
+    _, prof_e = ctx.profile_solve(M, b_d, x_d, TOL, MAXIT, pbcg.PIPELINED, pbcg.EXACT)
+    x_d.zero_()
+    _, prof_p = ctx.profile_solve(M, b_d, x_d, TOL, MAXIT, pbcg.PIPELINED, pbcg.PLAIN)
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = peaks()
+    iter_bytes = 2 * M_bytes + 23 * V_bytes
+    kern_bytes = {"pipe_x": M_bytes + 11 * V_bytes, "pipe_y": M_bytes + 12 * V_bytes}
+
+    def kernel_table(prof):
+        out, total = {}, sum(v[0] for v in prof.values())
+        for k, (ms, cnt) in prof.items():
+            base = k.rsplit("_", 1)[0]
+            e = {"launches": cnt, "avg_us": 1e3 * ms / cnt, "share": ms / total if total else 0.0}
+            if base in kern_bytes:
+                gbs = kern_bytes[base] / (1e-3 * ms / cnt) / 1e9
+                e["gbs"] = gbs
+                e["frac_of_" + peak_kind] = gbs / peak
+            out[k] = e
+        return out
+
+    kt_e, kt_p = kernel_table(prof_e), kernel_table(prof_p)
+    dom = max(kt_e, key=lambda k: kt_e[k]["share"])
+    dom_base = dom.rsplit("_", 1)[0]
+    ach = kt_e[dom].get("gbs", 0.0)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            t = json.load(open(tfile))
+            if t.get("kernel") == dom and t.get("source_sha") == source_sha():
+                traffic = t.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    ips_e = its_e_all / (ms_e * 1e-3)
+    ips_p = its_p_all / (ms_p * 1e-3)
+    us_it_e = 1e3 * ms_e / max(its_e, 1)
+    us_it_p = 1e3 * ms_p / max(its_p, 1)
+
+    cpu = None
+    if ws == 1:
+        cores = os.cpu_count() or 1
+        v_e, dt_e = oracle_sample(A, b, cores, 1, 4)
+        v_p1, dt_p = oracle_sample(A, b, 1, 0, 2)
+        cpu = {"value": v_e, "unit": "iter/s", "cores": cores, "kind": "oracle",
+               "sample": (f"4 exact p-BiCGStab iterations on the 128^3 system ({dt_e:.2f} s, {cores} threads for "
+                          f"exact dots; setup subtracted); plain FP64 oracle 1 core: {v_p1:.3f} iter/s "
+                          f"({dt_p:.2f} s for 2 iterations); CPU {cpu_model()}"),
+               "plain_1core_iter_per_s": v_p1}
+
+    steps_h = max(1, args.steps // 2)
+    line = {
+        "metric": METRIC, "value": ips_e, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_e / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "dots": "exact", "tol": TOL,
+                   "step": "one full solve (setup + iterations + true-residual check)",
+                   "l2": f"working set {(M_bytes + 11 * V_bytes) / 1e6:.0f} MB > 129 MB L2, no flush",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "iters_per_solve": res_e.iters, "status": res_e.status, "relres_true": res_e.relres_true,
+        "exact": {"iter_per_s": ips_e, "us_per_iter": us_it_e, "hbm_gbs": iter_bytes / (us_it_e * 1e-6) / 1e9,
+                  "iters": res_e.iters},
+        "plain": {"iter_per_s": ips_p, "us_per_iter": us_it_p, "hbm_gbs": iter_bytes / (us_it_p * 1e-6) / 1e9,
+                  "iters": res_p.iters, "relres_true": res_p.relres_true},
+        "exact_over_plain_time_per_iter": us_it_e / us_it_p,
+        "iteration_roofline": {"bytes_per_iter": iter_bytes, "frac_exact": iter_bytes / (us_it_e * 1e-6) / 1e9 / peak,
+                               "frac_plain": iter_bytes / (us_it_p * 1e-6) / 1e9 / peak, "peak_gbs": peak,
+                               "peak_kind": peak_kind},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "traffic": traffic, "algorithmic_bytes_per_launch": kern_bytes.get(dom_base),
+                     "peak_kind": peak_kind},
+        "kernels_exact": kt_e, "kernels_plain": kt_p,
+        "cpu_baseline": cpu,
+        "e2e": {"value": its_h_all / (ms_h * 1e-3), "unit": "iter/s", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 8 * n + 8 * (res_h.iters + 1), "steps": steps_h},
+        "clocks": clocks,
+        "gpu_launches": launches_e,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def source_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2404_13216_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -344,6 +344,7 @@ struct Prof {
 struct Launcher {
     pbcg_ctx *ctx;
     Prof *prof;
+    long long launches = 0;
     std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
 
     int go(const char *name, void *fn, int grid, Csr &A, Vecs &V, Ctl *c, Work *wk, int has_work)
@@ -357,6 +358,7 @@ struct Launcher {
         int rc = launch_kernel(ctx, fn, grid, A, V, c, wk, has_work);
         if (rc)
             return rc;
+        launches++;
         if (prof) {
             CK(cudaEventRecord(e1, ctx->stream));
             pending.push_back({name, {e0, e1}});
@@ -422,7 +424,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     Csr A = csr_of(m);
     Vecs V = vecs_of(ws);
     int grid = grid_for(ctx, n);
-    Launcher L{ctx, prof, {}};
+    Launcher L{ctx, prof, 0, {}};
     if (alg == PBCG_ALG_PIPELINED) {
         rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), grid, A, V, ws.ctl, ws.wk, 1);
         if (!rc)
@@ -437,11 +439,13 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     bool cond_on = false;
     bool true_done = false;
     auto body = body_kernels(alg, mode);
+    bool fresh = false;      // h_ctl already mirrors the device after a graph launch
     for (;;) {
         if (prof && (rc = L.flush()))
             return rc;
-        if ((rc = read_ctl(ctx)))
+        if (!fresh && (rc = read_ctl(ctx)))
             return rc;
+        fresh = false;
         int st = ctx->h_ctl->status;
         if (st == ST_CANDIDATE) {
             rc = L.go("true_res", (void *)k_true_res, grid, A, V, ws.ctl, ws.wk, 1);
@@ -469,7 +473,19 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
                 CK(cudaMemcpyAsync(&ws.ctl->use_cond, &one, sizeof one, cudaMemcpyHostToDevice, ctx->stream));
                 cond_on = true;
             }
+            int it_before = ctx->h_ctl->it;
             CK(cudaGraphLaunch(G->exec, ctx->stream));
+            if ((rc = read_ctl(ctx)))
+                return rc;
+            // every body execution launches all body kernels; a stop inside an
+            // iteration (non-finite dot, breakdown) still ran that iteration's body
+            long long bodies = ctx->h_ctl->it - it_before;
+            int s2 = ctx->h_ctl->status;
+            if (s2 == 2 || s2 == 3)
+                bodies += 1;
+            L.launches += bodies * (long long)body.size();
+            fresh = true;
+            continue;
         }
     }
     if (!true_done) {
@@ -499,6 +515,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         out->relres_recursive = fin_ctl.res;
         out->relres_true = fin_ctl.trueres;
         out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        out->launches = (int32_t)L.launches;
+        out->reserved = 0;
     }
     return fin_ctl.status;
 }

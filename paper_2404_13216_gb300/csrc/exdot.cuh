@@ -351,9 +351,10 @@ __device__ double gacc_round_reset(GAcc *g, uint32_t *scratch)
         } else if (negv) {
             result = 0.0;
         }
-        for (int k = k0; k <= k1; k++)
-            g->dig[k] = 0ull;
     }
+    // clear every touched digit, also when a non-finite operand made the result NaN
+    for (int k = k0; k <= k1; k++)
+        g->dig[k] = 0ull;
     g->kmin = NDIG;
     g->kmax = -1;
     g->nf = 0;

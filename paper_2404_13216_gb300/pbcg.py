@@ -34,7 +34,8 @@ class PbcgError(RuntimeError):
 
 class _Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres_recursive", ctypes.c_double),
-                ("relres_true", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("relres_true", ctypes.c_double), ("seconds", ctypes.c_double), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 def load_library(path: str = LIB_PATH):
@@ -94,6 +95,7 @@ class Result:
     relres_recursive: float
     relres_true: float
     seconds: float
+    launches: int = 0
 
 
 class Matrix:
@@ -159,7 +161,7 @@ class Context:
         r = _Result()
         self._check(_lib.pbcg_solve(self.handle, mat.handle, _ptr(b), _ptr(x), float(tol), int(maxit), int(alg),
                                     int(mode), ctypes.byref(r)))
-        return Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds)
+        return Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds, r.launches)
 
     def solve_batched(self, mat: Matrix, sys_row_ptr, b, x, tol, maxit: int, alg: int = PIPELINED,
                       mode: int = EXACT):
@@ -169,7 +171,7 @@ class Context:
         res = (_Result * nsys)()
         self._check(_lib.pbcg_solve_batched(self.handle, mat.handle, nsys, _ptr(srp), _ptr(b), _ptr(x), _ptr(tl),
                                             int(maxit), int(alg), int(mode), res))
-        return [Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds) for r in res]
+        return [Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds, r.launches) for r in res]
 
     def history(self, sys: int = 0) -> np.ndarray:
         ln = ctypes.c_int32(0)
@@ -207,4 +209,4 @@ class Context:
         prof = {}
         for i in range(min(k.value, cap)):
             prof[bytes(names[i]).split(b"\0")[0].decode()] = (float(ms[i]), int(cnt[i]))
-        return Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds), prof
+        return Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds, r.launches), prof

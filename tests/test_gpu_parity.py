@@ -61,6 +61,8 @@ def test_exact_dot_empty_and_nonfinite(ctx):
     a = np.ones(100)
     a[57] = np.inf
     assert math.isnan(ctx.dot(a, np.ones(100), 1))
+    # the accumulator is clean afterwards: the next dot sees none of the finite terms above
+    assert ctx.dot(np.ones(10), np.ones(10), 1) == 10.0
 
 
 def test_plain_dot_close(ctx, orc):
