@@ -346,13 +346,38 @@ def source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def run_ncu_case(args):
+    """Small fixed run for profilers: the 128^3 system, host-driven launches (no
+    CUDA graph), a fixed number of iterations; prints the per-kernel event times."""
+    import numpy as np
+    from paper_2404_13216_gb300 import build, inputs
+    build.build_library()
+    from paper_2404_13216_gb300 import pbcg
+    A = inputs.convdiff3d(args.ncu_side, PECLET, WIND)
+    b = inputs.rhs_ones(A)
+    mode = pbcg.EXACT if args.ncu_case == "exact" else pbcg.PLAIN
+    with pbcg.Context(0) as ctx:
+        M = ctx.upload_csr(A)
+        x = np.zeros(A.n)
+        res, prof = ctx.profile_solve(M, b, x, 1e-300, args.ncu_iters, pbcg.PIPELINED, mode)
+        print(json.dumps({"case": args.ncu_case, "n": A.n, "iters": res.iters,
+                          "kernels": {k: {"launches": c, "avg_us": 1e3 * t / c} for k, (t, c) in prof.items()}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--ncu-case", choices=["exact", "plain"], default=None,
+                    help="run a short fixed solve for a profiler and exit")
+    ap.add_argument("--ncu-side", type=int, default=N_SIDE)
+    ap.add_argument("--ncu-iters", type=int, default=12)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
+    if args.ncu_case:
+        return run_ncu_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
