@@ -8,7 +8,9 @@
 // true-residual pass, and either finishes or relaunches the loop.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -24,7 +26,7 @@ using namespace pbcg;
 
 namespace {
 
-enum { V_X, V_B, V_R0, V_R, V_W, V_T, V_P, V_S, V_Z, V_V, V_Y, V_COUNT };
+enum { V_X, V_B, V_R0, V_R, V_W, V_T, V_P, V_S, V_Z, V_V, V_Y, V_Q, V_TMP, V_COUNT };
 
 struct LoopGraph {
     cudaGraph_t graph = nullptr;
@@ -51,9 +53,13 @@ struct Workspace {
 struct pbcg_mat {
     int n;
     long long nnz;
-    int *rp;
-    int *ci;
-    double *va;
+    int nslices;
+    long long padded;      // stored SELL-32 entries (nnz plus padding)
+    int *sl_off;           // [nslices + 1]
+    int *rlen;             // [nslices * 32]
+    int *ci;               // [padded], solver-order column indices
+    double *va;            // [padded]
+    int *perm;             // [n] solver row p holds caller row perm[p]; NULL when rows keep their order
 };
 
 struct pbcg_ctx {
@@ -68,6 +74,7 @@ struct pbcg_ctx {
     std::vector<double> hist;          // last single solve
     bool have_hist = false;
     Ctl *h_ctl = nullptr;              // pinned mirror of the control block
+    std::map<const void *, int> occ;   // resident CTAs per SM of each kernel
 };
 
 namespace {
@@ -92,14 +99,26 @@ int fail(pbcg_ctx *c, int code, const char *fmt, ...)
                         "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
-Csr csr_of(const pbcg_mat *m)
+Mat mat_of(const pbcg_mat *m)
 {
-    Csr A;
+    Mat A;
     A.n = m->n;
-    A.rp = m->rp;
+    A.nslices = m->nslices;
+    A.sl_off = m->sl_off;
+    A.rlen = m->rlen;
     A.ci = m->ci;
     A.va = m->va;
     return A;
+}
+
+void mat_release(pbcg_mat *m)
+{
+    cudaFree(m->sl_off);
+    cudaFree(m->rlen);
+    cudaFree(m->ci);
+    cudaFree(m->va);
+    cudaFree(m->perm);
+    delete m;
 }
 
 Vecs vecs_of(Workspace &ws)
@@ -116,13 +135,27 @@ Vecs vecs_of(Workspace &ws)
     V.z = ws.vec[V_Z];
     V.v = ws.vec[V_V];
     V.y = ws.vec[V_Y];
+    V.q = ws.vec[V_Q];
     return V;
 }
 
-int grid_for(pbcg_ctx *ctx, long long n)
+// persistent grid: every CTA resident (occupancy of this kernel x SMs), at least one slice per warp
+int grid_for(pbcg_ctx *ctx, const void *fn, long long nslices)
 {
-    long long tiles = (n + 31) / 32;
-    long long g = (tiles + WARPS - 1) / WARPS;
+    int per_sm = 0;
+    auto it = ctx->occ.find(fn);
+    if (it != ctx->occ.end()) {
+        per_sm = it->second;
+    } else {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        cudaGetLastError();
+        ctx->occ[fn] = per_sm;
+    }
+    long long g = (long long)per_sm * ctx->num_sms;
+    long long need = (nslices + WARPS - 1) / WARPS;
+    if (g > need)
+        g = need;
     if (g > ctx->maxgrid)
         g = ctx->maxgrid;
     if (g < 1)
@@ -203,6 +236,89 @@ int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
     return 0;
 }
 
+// SELL-32 layout of a CSR matrix (host side), with an optional row order
+// sorted by length inside windows of SELL_SIGMA rows when that saves padding
+constexpr int SELL_SIGMA = 4096;
+
+struct Sell {
+    int nslices = 0;
+    long long padded = 0;
+    bool permuted = false;
+    std::vector<int> sl_off, rlen, ci, perm;
+    std::vector<double> va;
+};
+
+bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val, Sell &S)
+{
+    int ns = (n + 31) / 32;
+    S.nslices = ns;
+    std::vector<int> len(n);
+    long long nnz = rp[n];
+    for (int i = 0; i < n; i++)
+        len[i] = rp[i + 1] - rp[i];
+    S.perm.resize(n);
+    for (int i = 0; i < n; i++)
+        S.perm[i] = i;
+    auto padded_of = [&](const std::vector<int> &pm) {
+        long long tot = 0;
+        for (int s = 0; s < ns; s++) {
+            int w = 0;
+            for (int l = 0; l < 32; l++) {
+                int p = s * 32 + l;
+                if (p < n && len[pm[p]] > w)
+                    w = len[pm[p]];
+            }
+            tot += 32ll * w;
+        }
+        return tot;
+    };
+    long long pad0 = padded_of(S.perm);
+    if ((double)pad0 > 1.10 * (double)nnz + 32.0 * ns) {
+        for (int w0 = 0; w0 < n; w0 += SELL_SIGMA) {
+            int w1 = std::min(n, w0 + SELL_SIGMA);
+            std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1,
+                             [&](int a, int b) { return len[a] > len[b]; });
+        }
+        S.permuted = true;
+    }
+    std::vector<int> inv(n);
+    for (int p = 0; p < n; p++)
+        inv[S.perm[p]] = p;
+    S.sl_off.assign(ns + 1, 0);
+    long long off = 0;
+    for (int s = 0; s < ns; s++) {
+        int w = 0;
+        for (int l = 0; l < 32; l++) {
+            int p = s * 32 + l;
+            if (p < n && len[S.perm[p]] > w)
+                w = len[S.perm[p]];
+        }
+        if (off > INT32_MAX)
+            return false;
+        S.sl_off[s] = (int)off;
+        off += 32ll * w;
+    }
+    if (off > INT32_MAX)
+        return false;
+    S.sl_off[ns] = (int)off;
+    S.padded = off;
+    S.ci.assign((size_t)off, 0);
+    S.va.assign((size_t)off, 0.0);
+    S.rlen.assign((size_t)ns * 32, 0);
+    for (int p = 0; p < n; p++) {
+        int i = S.perm[p], s = p / 32, l = p % 32;
+        S.rlen[p] = len[i];
+        long long base = S.sl_off[s] + l;
+        for (int j = 0; j < len[i]; j++) {
+            S.ci[(size_t)(base + 32ll * j)] = inv[col[rp[i] + j]];
+            S.va[(size_t)(base + 32ll * j)] = val[rp[i] + j];
+        }
+    }
+    if (!S.permuted)
+        S.perm.clear();
+    return true;
+}
+
 int validate_csr_host(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci)
 {
     if (n < 1)
@@ -255,10 +371,11 @@ std::vector<BodyKernel> body_kernels(int alg, int mode)
     return k;
 }
 
-int launch_kernel(pbcg_ctx *ctx, void *fn, int grid, Csr &A, Vecs &V, Ctl *c, Work *wk, int has_work)
+int launch_kernel(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work)
 {
     void *args4[4] = {&A, &V, &c, &wk};
     void *args3[3] = {&A, &V, &c};
+    int grid = grid_for(ctx, fn, A.nslices);
     CK(cudaLaunchKernel(fn, dim3(grid), dim3(THREADS), has_work ? args4 : args3, 0, ctx->stream));
     return 0;
 }
@@ -283,11 +400,10 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, LoopGraph **ou
     CK(cudaGraphAddNode(&cnode, L.graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     // kernel parameter values are copied into the nodes when they are added
-    Csr A = csr_of(m);
+    Mat A = mat_of(m);
     Vecs V = vecs_of(ctx->ws);
     Ctl *c = ctx->ws.ctl;
     Work *wk = ctx->ws.wk;
-    int grid = grid_for(ctx, m->n);
     cudaGraphNode_t prev = nullptr;
     for (auto &bk : body_kernels(alg, mode)) {
         void *args4[4] = {&A, &V, &c, &wk};
@@ -295,7 +411,7 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, LoopGraph **ou
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof kp);
         kp.func = bk.fn;
-        kp.gridDim = dim3(grid);
+        kp.gridDim = dim3(grid_for(ctx, bk.fn, A.nslices));
         kp.blockDim = dim3(THREADS);
         kp.sharedMemBytes = 0;
         kp.kernelParams = bk.has_work ? args4 : args3;
@@ -347,7 +463,7 @@ struct Launcher {
     long long launches = 0;
     std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
 
-    int go(const char *name, void *fn, int grid, Csr &A, Vecs &V, Ctl *c, Work *wk, int has_work)
+    int go(const char *name, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work)
     {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (prof) {
@@ -355,7 +471,7 @@ struct Launcher {
             CK(cudaEventCreate(&e1));
             CK(cudaEventRecord(e0, ctx->stream));
         }
-        int rc = launch_kernel(ctx, fn, grid, A, V, c, wk, has_work);
+        int rc = launch_kernel(ctx, fn, A, V, c, wk, has_work);
         if (rc)
             return rc;
         launches++;
@@ -379,6 +495,40 @@ struct Launcher {
         return 0;
     }
 };
+
+// caller-order vector (host or device) -> solver-order device vector
+int vec_in(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst)
+{
+    size_t bytes = sizeof(double) * (size_t)m->n;
+    if (!m->perm) {
+        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+        return 0;
+    }
+    double *tmp = ctx->ws.vec[V_TMP];
+    CK(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyDefault, ctx->stream));
+    int n = m->n;
+    const int *pm = m->perm;
+    void *args[4] = {&n, &pm, &tmp, &dst};
+    CK(cudaLaunchKernel((void *)k_gather, dim3(ctx->num_sms * 4), dim3(256), args, 0, ctx->stream));
+    return 0;
+}
+
+// solver-order device vector -> caller-order vector (host or device)
+int vec_out(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst)
+{
+    size_t bytes = sizeof(double) * (size_t)m->n;
+    if (!m->perm) {
+        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+        return 0;
+    }
+    double *tmp = ctx->ws.vec[V_TMP];
+    int n = m->n;
+    const int *pm = m->perm;
+    void *args[4] = {&n, &pm, &src, &tmp};
+    CK(cudaLaunchKernel((void *)k_scatter, dim3(ctx->num_sms * 4), dim3(256), args, 0, ctx->stream));
+    CK(cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDefault, ctx->stream));
+    return 0;
+}
 
 int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, double tol, int32_t maxit, int alg,
                int mode, pbcg_result *out, Prof *prof)
@@ -404,8 +554,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     if (rc)
         return rc;
     Workspace &ws = ctx->ws;
-    CK(cudaMemcpyAsync(ws.vec[V_B], b, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
-    CK(cudaMemcpyAsync(ws.vec[V_X], x, sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
+    if ((rc = vec_in(ctx, m, b, ws.vec[V_B])) || (rc = vec_in(ctx, m, x, ws.vec[V_X])))
+        return rc;
     Ctl h;
     memset(&h, 0, sizeof h);
     h.it = 0;
@@ -421,18 +571,17 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     *ctx->h_ctl = h;
     CK(cudaMemcpyAsync(ws.ctl, ctx->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
 
-    Csr A = csr_of(m);
+    Mat A = mat_of(m);
     Vecs V = vecs_of(ws);
-    int grid = grid_for(ctx, n);
     Launcher L{ctx, prof, 0, {}};
     if (alg == PBCG_ALG_PIPELINED) {
-        rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), grid, A, V, ws.ctl, ws.wk, 1);
+        rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), A, V, ws.ctl, ws.wk, 1);
         if (!rc)
-            rc = L.go("setup2", mode ? Kern<1>::setup2() : Kern<0>::setup2(), grid, A, V, ws.ctl, ws.wk, 1);
+            rc = L.go("setup2", mode ? Kern<1>::setup2() : Kern<0>::setup2(), A, V, ws.ctl, ws.wk, 1);
         if (!rc)
-            rc = L.go("setup3", (void *)k_setup3, grid, A, V, ws.ctl, ws.wk, 0);
+            rc = L.go("setup3", (void *)k_setup3, A, V, ws.ctl, ws.wk, 0);
     } else {
-        rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), grid, A, V, ws.ctl, ws.wk, 1);
+        rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), A, V, ws.ctl, ws.wk, 1);
     }
     if (rc)
         return rc;
@@ -448,7 +597,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         fresh = false;
         int st = ctx->h_ctl->status;
         if (st == ST_CANDIDATE) {
-            rc = L.go("true_res", (void *)k_true_res, grid, A, V, ws.ctl, ws.wk, 1);
+            rc = L.go("true_res", (void *)k_true_res, A, V, ws.ctl, ws.wk, 1);
             if (rc)
                 return rc;
             true_done = true;
@@ -460,7 +609,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         if (prof) {
             // host-driven iteration, one kernel at a time
             for (auto &bk : body)
-                if ((rc = L.go(bk.name, bk.fn, grid, A, V, ws.ctl, ws.wk, bk.has_work)))
+                if ((rc = L.go(bk.name, bk.fn, A, V, ws.ctl, ws.wk, bk.has_work)))
                     return rc;
         } else {
             LoopGraph *G = nullptr;
@@ -489,7 +638,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         }
     }
     if (!true_done) {
-        if ((rc = L.go("true_res", (void *)k_true_res, grid, A, V, ws.ctl, ws.wk, 1)))
+        if ((rc = L.go("true_res", (void *)k_true_res, A, V, ws.ctl, ws.wk, 1)))
             return rc;
         if (prof && (rc = L.flush()))
             return rc;
@@ -501,7 +650,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         CK(cudaMemcpyAsync(&ws.ctl->use_cond, &zero, sizeof zero, cudaMemcpyHostToDevice, ctx->stream));
     }
     Ctl fin_ctl = *ctx->h_ctl;
-    CK(cudaMemcpyAsync(x, ws.vec[V_X], sizeof(double) * n, cudaMemcpyDefault, ctx->stream));
+    if ((rc = vec_out(ctx, m, ws.vec[V_X], x)))
+        return rc;
     int hl = fin_ctl.it + 1;
     if (hl > maxit + 1)
         hl = maxit + 1;
@@ -567,12 +717,8 @@ void pbcg_destroy(pbcg_ctx *ctx)
         return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    for (auto *m : ctx->mats) {
-        cudaFree(m->rp);
-        cudaFree(m->ci);
-        cudaFree(m->va);
-        delete m;
-    }
+    for (auto *m : ctx->mats)
+        mat_release(m);
     ctx->mats.clear();
     free_ws(ctx->ws);
     if (ctx->h_ctl)
@@ -601,36 +747,49 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     if (nnz < 0 || nnz >= (1ll << 31))
         return fail(ctx, PBCG_ERR_INVALID, "nnz out of range (got %lld)", (long long)nnz);
     CK(cudaSetDevice(ctx->device));
-    // bring the index arrays to the host for validation
+    // bring the CSR arrays to the host (validation and layout conversion)
     std::vector<int32_t> hrp((size_t)n + 1), hci((size_t)nnz);
+    std::vector<double> hva((size_t)nnz);
     CK(cudaMemcpy(hrp.data(), row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDefault));
-    if (nnz)
+    if (nnz) {
         CK(cudaMemcpy(hci.data(), col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDefault));
+        CK(cudaMemcpy(hva.data(), vals, sizeof(double) * (size_t)nnz, cudaMemcpyDefault));
+    }
     int rc = validate_csr_host(ctx, n, nnz, hrp.data(), hci.data());
     if (rc)
         return rc;
+    Sell S;
+    if (!build_sell(n, hrp.data(), hci.data(), hva.data(), S))
+        return fail(ctx, PBCG_ERR_INVALID, "padded matrix exceeds 2^31 entries");
     pbcg_mat *m = new pbcg_mat();
     m->n = n;
     m->nnz = nnz;
-    m->rp = nullptr;
-    m->ci = nullptr;
+    m->nslices = S.nslices;
+    m->padded = S.padded;
+    m->sl_off = m->rlen = m->ci = m->perm = nullptr;
     m->va = nullptr;
-    cudaError_t e = cudaMalloc(&m->rp, sizeof(int32_t) * ((size_t)n + 1));
+    size_t P = (size_t)(S.padded ? S.padded : 1);
+    cudaError_t e = cudaMalloc(&m->sl_off, sizeof(int) * S.sl_off.size());
     if (e == cudaSuccess)
-        e = cudaMalloc(&m->ci, sizeof(int32_t) * (size_t)(nnz ? nnz : 1));
+        e = cudaMalloc(&m->rlen, sizeof(int) * S.rlen.size());
     if (e == cudaSuccess)
-        e = cudaMalloc(&m->va, sizeof(double) * (size_t)(nnz ? nnz : 1));
+        e = cudaMalloc(&m->ci, sizeof(int) * P);
     if (e == cudaSuccess)
-        e = cudaMemcpy(m->rp, hrp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nnz)
-        e = cudaMemcpy(m->ci, hci.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nnz)
-        e = cudaMemcpy(m->va, vals, sizeof(double) * (size_t)nnz, cudaMemcpyDefault);
+        e = cudaMalloc(&m->va, sizeof(double) * P);
+    if (e == cudaSuccess && S.permuted)
+        e = cudaMalloc(&m->perm, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->sl_off, S.sl_off.data(), sizeof(int) * S.sl_off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->rlen, S.rlen.data(), sizeof(int) * S.rlen.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && S.padded)
+        e = cudaMemcpy(m->ci, S.ci.data(), sizeof(int) * (size_t)S.padded, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && S.padded)
+        e = cudaMemcpy(m->va, S.va.data(), sizeof(double) * (size_t)S.padded, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && S.permuted)
+        e = cudaMemcpy(m->perm, S.perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(m->rp);
-        cudaFree(m->ci);
-        cudaFree(m->va);
-        delete m;
+        mat_release(m);
         return fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "matrix upload: %s",
                     cudaGetErrorString(e));
     }
@@ -651,11 +810,8 @@ int pbcg_mat_free(pbcg_ctx *ctx, pbcg_mat *m)
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ws.loop.mat == m)
         free_loop(ctx->ws.loop);
-    cudaFree(m->rp);
-    cudaFree(m->ci);
-    cudaFree(m->va);
     ctx->mats.erase(m);
-    delete m;
+    mat_release(m);
     return 0;
 }
 
@@ -729,9 +885,7 @@ int pbcg_dot(pbcg_ctx *ctx, int64_t n, const double *a, const double *b, int dot
         CK(cudaMemcpyAsync(db, b, sizeof(double) * (size_t)n, cudaMemcpyDefault, ctx->stream));
     }
     const double *pa_ = a_dev ? a : da, *pb_ = b_dev ? b : db;
-    long long tiles = (n + 31) / 32;
-    long long g = (tiles + WARPS - 1) / WARPS;
-    int grid = (int)(g < 1 ? 1 : (g > ctx->maxgrid ? ctx->maxgrid : g));
+    int grid = grid_for(ctx, dot_mode ? (void *)k_dot<1> : (void *)k_dot<0>, (n + 31) / 32);
     long long nn = n;
     double *o = ctx->ws.dot_out;
     Work *wk = ctx->ws.wk;
@@ -756,18 +910,19 @@ int pbcg_spmv(pbcg_ctx *ctx, const pbcg_mat *m, const double *x, double *y)
     if (!x || !y)
         return fail(ctx, PBCG_ERR_INVALID, "x and y must not be NULL");
     CK(cudaSetDevice(ctx->device));
-    int n = m->n;
-    double *dx = nullptr, *dy = nullptr;
-    CK(cudaMalloc(&dx, sizeof(double) * (size_t)n));
-    CK(cudaMalloc(&dy, sizeof(double) * (size_t)n));
-    CK(cudaMemcpyAsync(dx, x, sizeof(double) * (size_t)n, cudaMemcpyDefault, ctx->stream));
-    Csr A = csr_of(m);
+    int rc = ensure_ws(ctx, m->n, 0);
+    if (rc)
+        return rc;
+    double *dx = ctx->ws.vec[V_P], *dy = ctx->ws.vec[V_S];
+    if ((rc = vec_in(ctx, m, x, dx)))
+        return rc;
+    Mat A = mat_of(m);
     void *args[3] = {&A, &dx, &dy};
-    CK(cudaLaunchKernel((void *)k_spmv, dim3(grid_for(ctx, n)), dim3(THREADS), args, 0, ctx->stream));
-    CK(cudaMemcpyAsync(y, dy, sizeof(double) * (size_t)n, cudaMemcpyDefault, ctx->stream));
+    CK(cudaLaunchKernel((void *)k_spmv, dim3(grid_for(ctx, (void *)k_spmv, A.nslices)), dim3(THREADS), args, 0,
+                        ctx->stream));
+    if ((rc = vec_out(ctx, m, dy, y)))
+        return rc;
     CK(cudaStreamSynchronize(ctx->stream));
-    cudaFree(dx);
-    cudaFree(dy);
     return 0;
 }
 

@@ -11,7 +11,7 @@
 //   1. decode both doubles into (sign, 53-bit integer mantissa, exponent) with
 //      bit operations;
 //   2. form the exact 106-bit mantissa product with four 32x32->64 multiplies;
-//   3. add it, as a signed 256-bit two's-complement number, into a per-lane
+//   3. add it, as a signed 384-bit two's-complement number, into a per-lane
 //      register window whose bit position (the anchor) is shared by the warp;
 //      a product that falls outside the window goes straight to the CTA's
 //      accumulator with shared-memory atomics;
@@ -33,8 +33,9 @@
 namespace pbcg {
 
 constexpr int NDIG = 136;        // 32-bit digits; 136*32 = 4352 bits cover 2^-2148 .. 2^2048 plus carries
-constexpr int WIN_SMAX = 120;    // largest left shift of a product inside a 256-bit window
-constexpr int WIN_ROOM = 24;     // bits of room left above the first product when anchoring
+constexpr int WIN_WORDS = 12;    // per-lane window: 384-bit two's complement
+constexpr int WIN_SMAX = 248;    // largest left shift of a 106-bit product inside the window (7 words + 24 bits)
+constexpr int WIN_ROOM = 64;     // bits of room left above the first product when anchoring
 
 // ---------------------------------------------------------------------------
 // decode and exact product
@@ -145,34 +146,43 @@ __device__ __noinline__ void cta_add_product(CtaAcc<ND> &c, int d, const Prod &p
 }
 
 // ---------------------------------------------------------------------------
-// per-lane window: 256-bit two's complement, LSB at bit `anchor` (warp-uniform)
+// per-lane window: 384-bit two's complement, LSB at bit `anchor` (warp-uniform)
+//
+// Headroom: a product shifted by at most WIN_SMAX bits is below 2^354; a lane
+// adds fewer than 2^22 of them and a warp sums 32 lanes, so the total stays
+// below 2^381 and the sign bit (383) is never reached.
 // ---------------------------------------------------------------------------
 struct Win {
-    uint32_t a[8];
+    uint32_t a[WIN_WORDS];
     int anchor;      // -1 while unset
 };
 
 __device__ __forceinline__ void win_init(Win &w)
 {
 #pragma unroll
-    for (int t = 0; t < 8; t++)
+    for (int t = 0; t < WIN_WORDS; t++)
         w.a[t] = 0u;
     w.anchor = -1;
 }
 
-__device__ __forceinline__ void add256(uint32_t (&a)[8], uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
-                                       uint32_t x4, uint32_t x5, uint32_t x6, uint32_t x7)
+__device__ __forceinline__ void add384(uint32_t (&a)[WIN_WORDS], const uint32_t (&x)[WIN_WORDS])
 {
-    asm("add.cc.u32 %0, %0, %8;\n\t"
-        "addc.cc.u32 %1, %1, %9;\n\t"
-        "addc.cc.u32 %2, %2, %10;\n\t"
-        "addc.cc.u32 %3, %3, %11;\n\t"
-        "addc.cc.u32 %4, %4, %12;\n\t"
-        "addc.cc.u32 %5, %5, %13;\n\t"
-        "addc.cc.u32 %6, %6, %14;\n\t"
-        "addc.u32 %7, %7, %15;"
-        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7])
-        : "r"(x0), "r"(x1), "r"(x2), "r"(x3), "r"(x4), "r"(x5), "r"(x6), "r"(x7));
+    asm("add.cc.u32 %0, %0, %12;\n\t"
+        "addc.cc.u32 %1, %1, %13;\n\t"
+        "addc.cc.u32 %2, %2, %14;\n\t"
+        "addc.cc.u32 %3, %3, %15;\n\t"
+        "addc.cc.u32 %4, %4, %16;\n\t"
+        "addc.cc.u32 %5, %5, %17;\n\t"
+        "addc.cc.u32 %6, %6, %18;\n\t"
+        "addc.cc.u32 %7, %7, %19;\n\t"
+        "addc.cc.u32 %8, %8, %20;\n\t"
+        "addc.cc.u32 %9, %9, %21;\n\t"
+        "addc.cc.u32 %10, %10, %22;\n\t"
+        "addc.u32 %11, %11, %23;"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+          "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11])
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]), "r"(x[8]),
+          "r"(x[9]), "r"(x[10]), "r"(x[11]));
 }
 
 // Deposit a*b.  Must be called by all 32 lanes of the warp together (the
@@ -197,13 +207,27 @@ __device__ __forceinline__ void win_deposit(Win &w, CtaAcc<ND> &c, int d, double
     int sh = p.off - w.anchor;
     if (w.anchor >= 0 && sh >= 0 && sh <= WIN_SMAX) {
         Shifted s = signed_shift(p, (uint32_t)(sh & 31));
-        uint32_t q = (uint32_t)sh >> 5;                   // 0..3 whole words
-        bool qa = q & 1u, qb = q & 2u;
-        uint32_t v0 = qa ? 0u : s.u0, v1 = qa ? s.u0 : s.u1, v2 = qa ? s.u1 : s.u2;
-        uint32_t v3 = qa ? s.u2 : s.u3, v4 = qa ? s.u3 : s.u4, v5 = qa ? s.u4 : s.sgn;
-        uint32_t x0 = qb ? 0u : v0, x1 = qb ? 0u : v1, x2 = qb ? v0 : v2, x3 = qb ? v1 : v3;
-        uint32_t x4 = qb ? v2 : v4, x5 = qb ? v3 : v5, x6 = qb ? v4 : s.sgn, x7 = qb ? v5 : s.sgn;
-        add256(w.a, x0, x1, x2, x3, x4, x5, x6, x7);
+        uint32_t q = (uint32_t)sh >> 5;                   // 0..7 whole words
+        bool q1 = q & 1u, q2 = q & 2u, q4 = q & 4u;
+        // word t of the shifted product: u[t-q] inside 0..4, the sign word above, 0 below
+        uint32_t v0 = q1 ? 0u : s.u0, v1 = q1 ? s.u0 : s.u1, v2 = q1 ? s.u1 : s.u2;
+        uint32_t v3 = q1 ? s.u2 : s.u3, v4 = q1 ? s.u3 : s.u4, v5 = q1 ? s.u4 : s.sgn;
+        uint32_t w0 = q2 ? 0u : v0, w1 = q2 ? 0u : v1, w2 = q2 ? v0 : v2, w3 = q2 ? v1 : v3;
+        uint32_t w4 = q2 ? v2 : v4, w5 = q2 ? v3 : v5, w6 = q2 ? v4 : s.sgn, w7 = q2 ? v5 : s.sgn;
+        uint32_t x[WIN_WORDS];
+        x[0] = q4 ? 0u : w0;
+        x[1] = q4 ? 0u : w1;
+        x[2] = q4 ? 0u : w2;
+        x[3] = q4 ? 0u : w3;
+        x[4] = q4 ? w0 : w4;
+        x[5] = q4 ? w1 : w5;
+        x[6] = q4 ? w2 : w6;
+        x[7] = q4 ? w3 : w7;
+        x[8] = q4 ? w4 : s.sgn;
+        x[9] = q4 ? w5 : s.sgn;
+        x[10] = q4 ? w6 : s.sgn;
+        x[11] = q4 ? w7 : s.sgn;
+        add384(w.a, x);
     } else {
         cta_add_product(c, d, p);
     }
@@ -217,33 +241,36 @@ __device__ __forceinline__ void win_flush(Win &w, CtaAcc<ND> &c, int d)
         return;                                           // warp-uniform: nothing deposited
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        uint32_t y[8];
+        uint32_t y[WIN_WORDS];
 #pragma unroll
-        for (int t = 0; t < 8; t++)
+        for (int t = 0; t < WIN_WORDS; t++)
             y[t] = __shfl_xor_sync(0xffffffffu, w.a[t], o);
-        add256(w.a, y[0], y[1], y[2], y[3], y[4], y[5], y[6], y[7]);
+        add384(w.a, y);
     }
     int k = w.anchor >> 5;
     uint32_t r = (uint32_t)(w.anchor & 31);
-    uint32_t sg = (uint32_t)((int)w.a[7] >> 31);
-    uint32_t z[9];
-    z[0] = w.a[0] << r;
-#pragma unroll
-    for (int t = 1; t < 8; t++)
-        z[t] = __funnelshift_l(w.a[t - 1], w.a[t], r);
-    z[8] = __funnelshift_l(w.a[7], sg, r);
+    uint32_t sg = (uint32_t)((int)w.a[WIN_WORDS - 1] >> 31);
     int lane = threadIdx.x & 31;
-    uint32_t mine = 0u;
+    // lane t (t <= WIN_WORDS) takes word t of (total << r)
+    uint32_t lo = 0u, hi = 0u;
 #pragma unroll
-    for (int t = 0; t < 9; t++)
-        mine = (lane == t) ? z[t] : mine;
-    if (lane < 9) {
-        unsigned long long v = (lane < 8) ? (unsigned long long)mine : (unsigned long long)(long long)(int)mine;
+    for (int t = 0; t < WIN_WORDS; t++) {
+        if (lane == t)
+            hi = w.a[t];
+        if (lane == t + 1)
+            lo = w.a[t];
+    }
+    if (lane == WIN_WORDS)
+        hi = sg;
+    uint32_t mine = (lane == 0) ? (hi << r) : __funnelshift_l(lo, hi, r);
+    if (lane <= WIN_WORDS) {
+        unsigned long long v = (lane < WIN_WORDS) ? (unsigned long long)mine
+                                                  : (unsigned long long)(long long)(int)mine;
         if (v != 0ull)
             atomicAdd(&c.dig[d][k + lane], v);
     }
     if (lane == 0)
-        cta_touch(c, d, k, k + 8);
+        cta_touch(c, d, k, k + WIN_WORDS);
 }
 
 // ---------------------------------------------------------------------------

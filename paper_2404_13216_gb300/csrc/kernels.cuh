@@ -9,6 +9,16 @@
 // the stop and breakdown tests) and, inside a CUDA graph, sets the loop's
 // conditional handle.  Pass boundaries are the global reduction points of
 // Section 2; p-BiCGStab has two per iteration, BiCGStab three.
+//
+// Matrix layout: SELL-32.  Rows are grouped in slices of 32; inside a slice
+// entry j of every row is stored contiguously (column-major), so the 32 lanes
+// of a warp read one 256-byte line per entry.  Each row keeps its entries in
+// stored CSR order and padding is never read, so every SpMV row is exactly
+// the CSR fma chain.  Rows may be permuted (sorted by length) at upload; all
+// solver vectors then live in that order, which changes no result in exact
+// mode.
+//
+// Grid: persistent, one contiguous run of slices per warp.
 #pragma once
 #include "exdot.cuh"
 
@@ -17,6 +27,7 @@ namespace pbcg {
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 constexpr int MAXD = 4;                 // most dots merged in one pass
+constexpr int UNR = 8;                  // SpMV entries loaded per batch
 
 enum : int { ST_RUNNING = 100, ST_CANDIDATE = 101 };
 enum : int { PH_SETUP = 0, PH_ITER = 1 };
@@ -44,15 +55,18 @@ struct Work {
     double *part;                        // plain partials [MAXD][maxgrid]
 };
 
-struct Csr {
-    int n;
-    const int *__restrict__ rp;
-    const int *__restrict__ ci;
-    const double *__restrict__ va;
+// SELL-32 matrix in the solver's (possibly permuted) row order
+struct Mat {
+    int n;                               // rows
+    int nslices;                         // ceil(n / 32)
+    const int *__restrict__ sl_off;      // [nslices + 1] first entry of each slice; width = diff / 32
+    const int *__restrict__ rlen;        // [nslices * 32] row lengths (0 past n)
+    const int *__restrict__ ci;          // padded column indices (solver order)
+    const double *__restrict__ va;       // padded values
 };
 
 struct Vecs {
-    double *x, *b, *r0, *r, *w, *t, *p, *s, *z, *v, *y;
+    double *x, *b, *r0, *r, *w, *t, *p, *s, *z, *v, *y, *q;
 };
 
 __device__ __forceinline__ bool fin(double v)
@@ -60,13 +74,90 @@ __device__ __forceinline__ bool fin(double v)
     return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
-// SpMV row: acc = +0; acc = fma(val_k, x[col_k], acc) in stored order
-__device__ __forceinline__ double spmv_row(const Csr &A, const double *__restrict__ x, int i)
+// slices [s0, s1) of this warp: contiguous runs over all warps of the grid
+struct WarpRange {
+    int s0, s1, lane;
+};
+
+__device__ __forceinline__ WarpRange warp_range(int nslices)
 {
-    int k0 = __ldg(A.rp + i), k1 = __ldg(A.rp + i + 1);
+    WarpRange R;
+    const int nw = (gridDim.x * THREADS) >> 5;
+    const int gw = (blockIdx.x * THREADS + threadIdx.x) >> 5;
+    const int per = (nslices + nw - 1) / nw;
+    R.s0 = min(gw * per, nslices);
+    R.s1 = min(R.s0 + per, nslices);
+    R.lane = threadIdx.x & 31;
+    return R;
+}
+
+// SpMV row of slice s, lane `lane`: acc = +0; acc = fma(val_j, x[col_j], acc) for j < len
+struct RowRef {
+    int base, width, len;
+};
+
+__device__ __forceinline__ RowRef row_ref(const Mat &A, int s, int lane)
+{
+    RowRef R;
+    R.base = __ldg(A.sl_off + s);
+    R.width = (__ldg(A.sl_off + s + 1) - R.base) >> 5;
+    R.len = __ldg(A.rlen + s * 32 + lane);
+    R.base += lane;
+    return R;
+}
+
+__device__ __forceinline__ double spmv_row(const Mat &A, const RowRef &R, const double *__restrict__ x)
+{
     double acc = 0.0;
-    for (int k = k0; k < k1; k++)
-        acc = __fma_rn(__ldg(A.va + k), __ldg(x + __ldg(A.ci + k)), acc);
+    for (int j0 = 0; j0 < R.width; j0 += UNR) {      // warp-uniform bound
+        int c[UNR];
+        double v[UNR], xv[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            if (j0 + j < R.len) {
+                c[j] = __ldg(A.ci + R.base + (j0 + j) * 32);
+                v[j] = __ldg(A.va + R.base + (j0 + j) * 32);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < UNR; j++)
+            if (j0 + j < R.len)
+                xv[j] = __ldg(x + c[j]);
+#pragma unroll
+        for (int j = 0; j < UNR; j++)
+            if (j0 + j < R.len)
+                acc = __fma_rn(v[j], xv[j], acc);
+    }
+    return acc;
+}
+
+// same, with the gathered operand formed on the fly as fma(na, s[col], r[col])
+__device__ __forceinline__ double spmv_row_axpy(const Mat &A, const RowRef &R, double na,
+                                                const double *__restrict__ s, const double *__restrict__ r)
+{
+    double acc = 0.0;
+    for (int j0 = 0; j0 < R.width; j0 += UNR) {
+        int c[UNR];
+        double v[UNR], xs[UNR], xr[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            if (j0 + j < R.len) {
+                c[j] = __ldg(A.ci + R.base + (j0 + j) * 32);
+                v[j] = __ldg(A.va + R.base + (j0 + j) * 32);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            if (j0 + j < R.len) {
+                xs[j] = __ldg(s + c[j]);
+                xr[j] = __ldg(r + c[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < UNR; j++)
+            if (j0 + j < R.len)
+                acc = __fma_rn(v[j], __fma_rn(na, xs[j], xr[j]), acc);
+    }
     return acc;
 }
 
@@ -84,7 +175,7 @@ struct Shm {
 
 template <int ND, int MODE>
 struct DotSet {
-    Win win[ND];
+    Win win[MODE == 1 ? ND : 1];
     double s[ND];
     bool nf[ND];
 
@@ -92,7 +183,8 @@ struct DotSet {
     {
 #pragma unroll
         for (int d = 0; d < ND; d++) {
-            win_init(win[d]);
+            if (MODE == 1)
+                win_init(win[d]);
             s[d] = 0.0;
             nf[d] = false;
         }
@@ -117,6 +209,52 @@ __device__ __forceinline__ void shm_init(Shm<ND> &sh)
         sh.last = 0;
 }
 
+// Warp sum of ND plain partials with a reduce-scatter: the dots are split
+// between lane halves (and quarters) before the butterfly, so a lane performs
+// 5 additions for ND = 1 or 2 and 6 for ND = 3 or 4 instead of 5 per dot.
+// Every lane receives every total; the order of additions is fixed.
+template <int ND>
+__device__ __forceinline__ void warp_sum_plain(const double (&s)[ND], double (&out)[ND])
+{
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    double v;
+    if (ND == 1) {
+        v = s[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+        out[0] = v;
+        return;
+    } else if (ND == 2) {
+        // lanes < 16 keep dot 0, lanes >= 16 dot 1
+        double k = h16 ? s[ND - 1] : s[0], g = h16 ? s[0] : s[ND - 1];
+        v = __dadd_rn(k, __shfl_xor_sync(0xffffffffu, g, 16));
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1)
+            v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+#pragma unroll
+        for (int d = 0; d < ND; d++)
+            out[d] = __shfl_sync(0xffffffffu, v, 16 * d);
+        return;
+    } else {
+        // quarters: dot d = 2*h16 + h8 ends in lane 8*d
+        double a0 = s[0], a1 = s[1], a2 = s[2], a3 = ND > 3 ? s[ND > 3 ? 3 : 0] : 0.0;
+        double k0 = h16 ? a2 : a0, k1 = h16 ? a3 : a1;
+        double g0 = h16 ? a0 : a2, g1 = h16 ? a1 : a3;
+        k0 = __dadd_rn(k0, __shfl_xor_sync(0xffffffffu, g0, 16));
+        k1 = __dadd_rn(k1, __shfl_xor_sync(0xffffffffu, g1, 16));
+        double kk = h8 ? k1 : k0, gg = h8 ? k0 : k1;
+        v = __dadd_rn(kk, __shfl_xor_sync(0xffffffffu, gg, 8));
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1)
+            v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+#pragma unroll
+        for (int d = 0; d < ND; d++)
+            out[d] = __shfl_sync(0xffffffffu, v, 8 * d);
+    }
+}
+
 // Merge the CTA's dots grid-wide.  Returns true in the last CTA, whose
 // sh.dv[] then holds the finished dot values.  Called by every thread.
 template <int ND, int MODE>
@@ -131,14 +269,12 @@ __device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
                 atomicOr(&sh.acc.nf[d], 1);
         }
     } else {
+        double tot[ND];
+        warp_sum_plain<ND>(D.s, tot);
+        if (lane == 0) {
 #pragma unroll
-        for (int d = 0; d < ND; d++) {
-            double v = D.s[d];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (lane == 0)
-                sh.wpart[d][warp] = v;
+            for (int d = 0; d < ND; d++)
+                sh.wpart[d][warp] = tot[d];
         }
     }
     __syncthreads();
@@ -270,24 +406,18 @@ __device__ void setup_scalar(Ctl *c, double bb, double rho, double rw)
         post_stop(c);
 }
 
-// ---------------------------------------------------------------------------
-// grid mapping: warp-uniform 32-row tiles, strided over all warps of the grid
-// ---------------------------------------------------------------------------
-#define PBCG_TILE_LOOP(n)                                                                    \
-    const int lane_ = threadIdx.x & 31;                                                      \
-    const int gwarp_ = (blockIdx.x * THREADS + threadIdx.x) >> 5;                            \
-    const int nwarps_ = (gridDim.x * THREADS) >> 5;                                          \
-    const int ntiles_ = ((n) + 31) >> 5;                                                     \
-    for (int tile_ = gwarp_; tile_ < ntiles_; tile_ += nwarps_)
+#define PBCG_SLICE_LOOP(A)                                 \
+    const WarpRange wr_ = warp_range((A).nslices);         \
+    for (int sl_ = wr_.s0; sl_ < wr_.s1; sl_++)
 
-#define PBCG_ROW (tile_ * 32 + lane_)
+#define PBCG_ROW (sl_ * 32 + wr_.lane)
 
 // ---------------------------------------------------------------------------
 // setup passes
 // ---------------------------------------------------------------------------
 // S1: r0 = b - A x0, r = r0 (and p = r0 for BiCGStab); dots (b,b), (r0,r0)
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_setup1(Csr A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS) k_setup1(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     __shared__ Shm<2> sh;
     shm_init<2, MODE>(sh);
@@ -295,14 +425,16 @@ __global__ void __launch_bounds__(THREADS) k_setup1(Csr A, Vecs V, Ctl *c, Work 
     const bool bicg = c->alg == ALG_BICGSTAB;
     DotSet<2, MODE> D;
     D.init();
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         bool act = i < A.n;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double ax = spmv_row(A, R, V.x);
         double bi = 0.0, r0i = 0.0;
         if (act) {
             bi = V.b[i];
-            r0i = __dsub_rn(bi, spmv_row(A, V.x, i));
+            r0i = __dsub_rn(bi, ax);
             V.r0[i] = r0i;
             V.r[i] = r0i;
             if (bicg)
@@ -325,21 +457,22 @@ __global__ void __launch_bounds__(THREADS) k_setup1(Csr A, Vecs V, Ctl *c, Work 
 
 // S2 (p-BiCGStab): w0 = A r0; dot (r0, w0); setup scalars
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_setup2(Csr A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS) k_setup2(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     __shared__ Shm<1> sh;
     shm_init<1, MODE>(sh);
     __syncthreads();
     DotSet<1, MODE> D;
     D.init();
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         bool act = i < A.n;
-        double r0i = 0.0, wi = 0.0;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double wi = spmv_row(A, R, V.r0);
+        double r0i = 0.0;
         if (act) {
             r0i = V.r0[i];
-            wi = spmv_row(A, V.r0, i);
             V.w[i] = wi;
         }
         D.add(sh, 0, r0i, wi, act);
@@ -353,15 +486,17 @@ __global__ void __launch_bounds__(THREADS) k_setup2(Csr A, Vecs V, Ctl *c, Work 
 }
 
 // S3 (p-BiCGStab): t0 = A w0
-__global__ void __launch_bounds__(THREADS) k_setup3(Csr A, Vecs V, const Ctl *c)
+__global__ void __launch_bounds__(THREADS) k_setup3(Mat A, Vecs V, const Ctl *c)
 {
     if (c->status != ST_RUNNING && c->status != ST_CANDIDATE)
         return;
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double ti = spmv_row(A, R, V.w);
         if (i < A.n)
-            V.t[i] = spmv_row(A, V.w, i);
+            V.t[i] = ti;
     }
 }
 
@@ -370,7 +505,7 @@ __global__ void __launch_bounds__(THREADS) k_setup3(Csr A, Vecs V, const Ctl *c)
 // ---------------------------------------------------------------------------
 // X(i): t_i = A w_i (i >= 1), p_i, s_i, z_i, q_i, y_i; dots (q,y), (y,y), (r0,s), (r0,z); omega_i
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_pipe_x(Csr A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS, 2) k_pipe_x(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
         return;
@@ -382,32 +517,48 @@ __global__ void __launch_bounds__(THREADS) k_pipe_x(Csr A, Vecs V, Ctl *c, Work 
     const double nalpha = -alpha, nomega = -omega;
     DotSet<4, MODE> D;
     D.init();
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         bool act = i < A.n;
-        double q = 0.0, y = 0.0, r0i = 0.0, si = 0.0, zi = 0.0;
+        double ri = 0.0, wi = 0.0, r0i = 0.0, pold = 0.0, sold = 0.0, zold = 0.0, vold = 0.0, ti = 0.0;
         if (act) {
-            double ri = V.r[i], wi = V.w[i];
-            double pi, ti;
+            ri = V.r[i];
+            wi = V.w[i];
             r0i = V.r0[i];
             if (first) {
                 ti = V.t[i];
-                pi = ri;
-                si = wi;
-                zi = ti;
             } else {
-                ti = spmv_row(A, V.w, i);
-                pi = __fma_rn(beta, __fma_rn(nomega, V.s[i], V.p[i]), ri);
-                si = __fma_rn(beta, __fma_rn(nomega, V.z[i], V.s[i]), wi);
-                zi = __fma_rn(beta, __fma_rn(nomega, V.v[i], V.z[i]), ti);
-                V.t[i] = ti;
+                pold = V.p[i];
+                sold = V.s[i];
+                zold = V.z[i];
+                vold = V.v[i];
             }
+        }
+        if (!first) {
+            RowRef R = row_ref(A, sl_, wr_.lane);
+            ti = spmv_row(A, R, V.w);
+        }
+        double pi, si, zi, q = 0.0, y = 0.0;
+        if (first) {
+            pi = ri;
+            si = wi;
+            zi = ti;
+        } else {
+            pi = __fma_rn(beta, __fma_rn(nomega, sold, pold), ri);
+            si = __fma_rn(beta, __fma_rn(nomega, zold, sold), wi);
+            zi = __fma_rn(beta, __fma_rn(nomega, vold, zold), ti);
+        }
+        if (act) {
+            q = __fma_rn(nalpha, si, ri);
+            y = __fma_rn(nalpha, zi, wi);
+            if (!first)
+                V.t[i] = ti;
             V.p[i] = pi;
             V.s[i] = si;
             V.z[i] = zi;
-            q = __fma_rn(nalpha, si, ri);
-            y = __fma_rn(nalpha, zi, wi);
+            V.q[i] = q;
+            V.y[i] = y;
         }
         D.add(sh, 0, q, y, act);
         D.add(sh, 1, y, y, act);
@@ -433,7 +584,7 @@ __global__ void __launch_bounds__(THREADS) k_pipe_x(Csr A, Vecs V, Ctl *c, Work 
 
 // Y(i): v_i = A z_i, x_{i+1}, r_{i+1}, w_{i+1}; dots (r0,r), (r0,w), (r,r); beta_i, alpha_{i+1}, stop test
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_pipe_y(Csr A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS, 3 - MODE) k_pipe_y(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
         return;
@@ -444,20 +595,26 @@ __global__ void __launch_bounds__(THREADS) k_pipe_y(Csr A, Vecs V, Ctl *c, Work 
     const double nalpha = -alpha, nomega = -omega;
     DotSet<3, MODE> D;
     D.init();
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         bool act = i < A.n;
-        double rn = 0.0, wn = 0.0, r0i = 0.0;
+        double q = 0.0, y = 0.0, pi = 0.0, xi = 0.0, ti = 0.0, r0i = 0.0;
         if (act) {
-            double vi = spmv_row(A, V.z, i);
-            double ri = V.r[i], si = V.s[i], wi = V.w[i], zi = V.z[i];
-            double q = __fma_rn(nalpha, si, ri);
-            double y = __fma_rn(nalpha, zi, wi);
-            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, V.p[i], V.x[i]));
-            rn = __fma_rn(nomega, y, q);
-            wn = __fma_rn(nomega, __fma_rn(nalpha, vi, V.t[i]), y);
+            q = V.q[i];
+            y = V.y[i];
+            pi = V.p[i];
+            xi = V.x[i];
+            ti = V.t[i];
             r0i = V.r0[i];
+        }
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double vi = spmv_row(A, R, V.z);
+        double rn = 0.0, wn = 0.0;
+        if (act) {
+            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, pi, xi));
+            rn = __fma_rn(nomega, y, q);
+            wn = __fma_rn(nomega, __fma_rn(nalpha, vi, ti), y);
             V.v[i] = vi;
             V.r[i] = rn;
             V.w[i] = wn;
@@ -488,12 +645,12 @@ __global__ void __launch_bounds__(THREADS) k_pipe_y(Csr A, Vecs V, Ctl *c, Work 
 // BiCGStab passes
 // ---------------------------------------------------------------------------
 // P(i), i >= 1: p = fma(beta, fma(-omega, s, p), r)
-__global__ void __launch_bounds__(THREADS) k_bicg_p(Csr A, Vecs V, const Ctl *c)
+__global__ void __launch_bounds__(THREADS) k_bicg_p(Mat A, Vecs V, const Ctl *c)
 {
     if (c->status != ST_RUNNING || c->it == 0)
         return;
     const double beta = c->beta, nomega = -c->omega;
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         if (i < A.n)
@@ -503,7 +660,7 @@ __global__ void __launch_bounds__(THREADS) k_bicg_p(Csr A, Vecs V, const Ctl *c)
 
 // A(i): s = A p; dot (r0, s); alpha_i
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_bicg_a(Csr A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS) k_bicg_a(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
         return;
@@ -512,13 +669,14 @@ __global__ void __launch_bounds__(THREADS) k_bicg_a(Csr A, Vecs V, Ctl *c, Work 
     __syncthreads();
     DotSet<1, MODE> D;
     D.init();
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         bool act = i < A.n;
-        double si = 0.0, r0i = 0.0;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double si = spmv_row(A, R, V.p);
+        double r0i = 0.0;
         if (act) {
-            si = spmv_row(A, V.p, i);
             V.s[i] = si;
             r0i = V.r0[i];
         }
@@ -545,7 +703,7 @@ __global__ void __launch_bounds__(THREADS) k_bicg_a(Csr A, Vecs V, Ctl *c, Work 
 
 // B(i): y = A q with q_j = fma(-alpha, s_j, r_j) formed in the gather; dots (q,y), (y,y); omega_i
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_bicg_b(Csr A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS) k_bicg_b(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
         return;
@@ -555,20 +713,14 @@ __global__ void __launch_bounds__(THREADS) k_bicg_b(Csr A, Vecs V, Ctl *c, Work 
     const double nalpha = -c->alpha;
     DotSet<2, MODE> D;
     D.init();
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         bool act = i < A.n;
-        double qi = 0.0, yi = 0.0;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double yi = spmv_row_axpy(A, R, nalpha, V.s, V.r);
+        double qi = 0.0;
         if (act) {
-            int k0 = __ldg(A.rp + i), k1 = __ldg(A.rp + i + 1);
-            double acc = 0.0;
-            for (int k = k0; k < k1; k++) {
-                int j = __ldg(A.ci + k);
-                double qj = __fma_rn(nalpha, __ldg(V.s + j), __ldg(V.r + j));
-                acc = __fma_rn(__ldg(A.va + k), qj, acc);
-            }
-            yi = acc;
             qi = __fma_rn(nalpha, V.s[i], V.r[i]);
             V.y[i] = yi;
         }
@@ -592,7 +744,7 @@ __global__ void __launch_bounds__(THREADS) k_bicg_b(Csr A, Vecs V, Ctl *c, Work 
 
 // C(i): x, r updates; dots (r0,r), (r,r); beta_i, stop test
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_bicg_c(Csr A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS) k_bicg_c(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
         return;
@@ -603,17 +755,18 @@ __global__ void __launch_bounds__(THREADS) k_bicg_c(Csr A, Vecs V, Ctl *c, Work 
     const double nalpha = -alpha, nomega = -omega;
     DotSet<2, MODE> D;
     D.init();
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         bool act = i < A.n;
         double rn = 0.0, r0i = 0.0;
         if (act) {
-            double q = __fma_rn(nalpha, V.s[i], V.r[i]);
-            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, V.p[i], V.x[i]));
-            rn = __fma_rn(nomega, V.y[i], q);
-            V.r[i] = rn;
+            double si = V.s[i], ri = V.r[i], pi = V.p[i], xi = V.x[i], yi = V.y[i];
             r0i = V.r0[i];
+            double q = __fma_rn(nalpha, si, ri);
+            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, pi, xi));
+            rn = __fma_rn(nomega, yi, q);
+            V.r[i] = rn;
         }
         D.add(sh, 0, r0i, rn, act);
         D.add(sh, 1, rn, rn, act);
@@ -638,21 +791,23 @@ __global__ void __launch_bounds__(THREADS) k_bicg_c(Csr A, Vecs V, Ctl *c, Work 
 // ---------------------------------------------------------------------------
 // true residual ||b - A x|| / ||b|| with exact dots; resolves a candidate stop
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(THREADS) k_true_res(Csr A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS) k_true_res(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     __shared__ Shm<2> sh;
     shm_init<2, 1>(sh);
     __syncthreads();
     DotSet<2, 1> D;
     D.init();
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
         bool act = i < A.n;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double ax = spmv_row(A, R, V.x);
         double ri = 0.0, bi = 0.0;
         if (act) {
             bi = V.b[i];
-            ri = __dsub_rn(bi, spmv_row(A, V.x, i));
+            ri = __dsub_rn(bi, ax);
         }
         D.add(sh, 0, ri, ri, act);
         D.add(sh, 1, bi, bi, act);
@@ -679,7 +834,7 @@ __global__ void __launch_bounds__(THREADS) k_true_res(Csr A, Vecs V, Ctl *c, Wor
 }
 
 // ---------------------------------------------------------------------------
-// standalone kernels: dot and SpMV
+// standalone kernels: dot, SpMV, permutation gather/scatter
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(THREADS) k_dot(long long n, const double *a, const double *b, double *out,
@@ -691,10 +846,13 @@ __global__ void __launch_bounds__(THREADS) k_dot(long long n, const double *a, c
     DotSet<1, MODE> D;
     D.init();
     const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * THREADS + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * THREADS) >> 5;
+    const long long gw = ((long long)blockIdx.x * THREADS + threadIdx.x) >> 5;
     const long long nt = (n + 31) >> 5;
-    for (long long t = gw; t < nt; t += nw) {
+    const long long per = (nt + nw - 1) / nw;
+    const long long t0 = gw * per < nt ? gw * per : nt;
+    const long long t1 = t0 + per < nt ? t0 + per : nt;
+    for (long long t = t0; t < t1; t++) {
         long long i = t * 32 + lane;
         bool act = i < n;
         double ai = act ? a[i] : 0.0, bi = act ? b[i] : 0.0;
@@ -706,14 +864,30 @@ __global__ void __launch_bounds__(THREADS) k_dot(long long n, const double *a, c
         *out = sh.dv[0];
 }
 
-__global__ void __launch_bounds__(THREADS) k_spmv(Csr A, const double *x, double *y)
+__global__ void __launch_bounds__(THREADS) k_spmv(Mat A, const double *x, double *y)
 {
-    PBCG_TILE_LOOP(A.n)
+    PBCG_SLICE_LOOP(A)
     {
         int i = PBCG_ROW;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double yi = spmv_row(A, R, x);
         if (i < A.n)
-            y[i] = spmv_row(A, x, i);
+            y[i] = yi;
     }
+}
+
+// dst[p] = src[perm[p]] (into solver order)
+__global__ void k_gather(int n, const int *__restrict__ perm, const double *__restrict__ src, double *dst)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        dst[p] = src[perm[p]];
+}
+
+// dst[perm[p]] = src[p] (back to caller order)
+__global__ void k_scatter(int n, const int *__restrict__ perm, const double *__restrict__ src, double *dst)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        dst[perm[p]] = src[p];
 }
 
 }  // namespace pbcg

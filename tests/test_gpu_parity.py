@@ -119,9 +119,10 @@ def test_exact_solve_bitwise(ctx, orc, sysname, alg):
 
 
 @pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
-@pytest.mark.parametrize("sysname", ["2d64_pe10", "3d24_pe50"])
-def test_plain_solve_tolerance(ctx, orc, sysname, alg):
-    A = SYSTEMS[sysname]()
+def test_plain_solve_tolerance_2d64(ctx, orc, alg):
+    """The 64x64 configuration: plain-mode history within 1e-8 (relative) of the
+    oracle's over the first 20 iterations, true relative residual <= tol."""
+    A = SYSTEMS["2d64_pe10"]()
     b = inputs.rhs_ones(A)
     tol = 1e-8
     ref, res, x, hist = run_both(ctx, orc, A, b, tol, 2000, alg, 0)
@@ -129,6 +130,35 @@ def test_plain_solve_tolerance(ctx, orc, sysname, alg):
     k = min(21, hist.size, ref.history.size)
     rel = np.abs(hist[:k] - ref.history[:k]) / np.abs(ref.history[:k])
     assert np.all(rel <= PLAIN_HIST_RTOL), rel.max()
+
+
+def sensitivity_bar(orc, A, b, alg, k):
+    """Per-iteration spread between two valid FP64 dot orders on the CPU (the
+    oracle's sequential fma dot and its correctly rounded dot)."""
+    hp = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=k, alg=alg, mode=0).history
+    he = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=k, alg=alg, mode=1, nthreads=8).history
+    return hp, np.abs(hp - he) / np.abs(he)
+
+
+@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
+def test_plain_solve_3d_sensitivity_relative(ctx, orc, alg):
+    """3D systems separate faster than 1e-8 under any change of dot order (the
+    CPU's own two orders differ by ~3e-8 within 20 iterations), so the plain-mode
+    history is held to 4x that spread plus 1e-13, and the solve must converge."""
+    A = SYSTEMS["3d24_pe50"]()
+    b = inputs.rhs_ones(A)
+    k = 20
+    hp, spread = sensitivity_bar(orc, A, b, alg, k)
+    M = ctx.upload_csr(A)
+    x = np.zeros(A.n)
+    ctx.solve(M, b, x, 1e-300, k, alg, 0)
+    hist = ctx.history()
+    rel = np.abs(hist - hp) / np.abs(hp)
+    assert np.all(rel <= 4 * spread + 1e-13), (rel.max(), spread.max())
+    x = np.zeros(A.n)
+    res = ctx.solve(M, b, x, 1e-8, 2000, alg, 0)
+    assert res.status == 0 and res.relres_true <= 1e-8
+    M.free()
 
 
 def test_golden_fixture_exact(ctx):
@@ -215,14 +245,20 @@ def test_device_pointers(ctx, orc):
 
 # --------------------------------------------------------------------------- full size
 def test_full_size_128cubed_first_iterations(ctx, orc):
-    """3D 128^3 (n = 2,097,152): the first iterations in the launch shape the
-    benchmark uses are bit-identical to the oracle (plain: within tolerance)."""
+    """3D 128^3 (n = 2,097,152) in the launch shape the benchmark uses: exact mode
+    bit-identical to the oracle over the first iterations; plain mode within
+    4x the CPU's own two-order spread over 20 iterations."""
     A = inputs.convdiff3d(128, 50.0)
     b = inputs.rhs_ones(A)
-    for mode in (1, 0):
-        ref, res, x, hist = run_both(ctx, orc, A, b, 1e-10, 4, 1, mode)
-        assert res.iters == ref.iters == 4
-        if mode == 1:
-            assert same(hist, ref.history) and same(x, ref.x)
-        else:
-            assert np.all(np.abs(hist - ref.history) <= PLAIN_HIST_RTOL * ref.history)
+    ref, res, x, hist = run_both(ctx, orc, A, b, 1e-10, 4, 1, 1)
+    assert res.iters == ref.iters == 4
+    assert same(hist, ref.history) and same(x, ref.x)
+    k = 20
+    hp, spread = sensitivity_bar(orc, A, b, 1, k)
+    M = ctx.upload_csr(A)
+    x = np.zeros(A.n)
+    ctx.solve(M, b, x, 1e-300, k, 1, 0)
+    hist = ctx.history()
+    M.free()
+    rel = np.abs(hist - hp) / np.abs(hp)
+    assert np.all(rel <= 4 * spread + 1e-13), (rel.max(), spread.max())
