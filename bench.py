@@ -3,7 +3,7 @@
 
 Workload: 3D convection-diffusion, 7-point upwind, 128^3 grid (n = 2,097,152,
 nnz = 14,581,760), wind (1, 0.5, 0.25), Peclet 50, FP64 CSR, b = A*ones,
-x0 = 0, relative tolerance 1e-10.  One step = one full solve (setup, the
+x0 = 0, relative tolerance 1e-10, maxit 1000.  One step = one full solve (setup, the
 iteration loop, the true-residual check) with exact dot products; the same
 solves with plain FP64 dots are timed beside them.
 
@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "p-BiCGStab iters/s & HBM GB/s, exact vs plain dots; batched solves/s & p99"
-N_SIDE, PECLET, WIND, TOL, MAXIT = 128, 50.0, (1.0, 0.5, 0.25), 1e-10, 5000
+N_SIDE, PECLET, WIND, TOL, MAXIT = 128, 50.0, (1.0, 0.5, 0.25), 1e-10, 1000
 WORKLOAD = ("3D convection-diffusion 7-point upwind 128^3 (n=2097152, nnz=14581760), wind (1,0.5,0.25), "
             "Peclet 50, FP64 CSR, b=A*ones, x0=0, rel tol 1e-10, p-BiCGStab")
 

@@ -185,60 +185,10 @@ __device__ __forceinline__ void add384(uint32_t (&a)[WIN_WORDS], const uint32_t 
           "r"(x[9]), "r"(x[10]), "r"(x[11]));
 }
 
-// Deposit a*b.  Must be called by all 32 lanes of the warp together (the
-// anchor is chosen with a warp reduction); `active` masks lanes with no term.
+// the flush itself; leaves the window zero (anchor unchanged)
 template <int ND>
-__device__ __forceinline__ void win_deposit(Win &w, CtaAcc<ND> &c, int d, double a, double b, bool active,
-                                            bool &nf)
+__device__ __forceinline__ void win_flush_reset(Win &w, CtaAcc<ND> &c, int d)
 {
-    Prod p = exact_product(a, b);
-    if (!active) {
-        p.off = -1;
-        p.nonfinite = false;
-    }
-    nf |= p.nonfinite;
-    if (w.anchor < 0) {                                   // warp-uniform branch
-        int m = __reduce_max_sync(0xffffffffu, p.off);
-        if (m >= 0)
-            w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
-    }
-    if (p.off < 0)
-        return;
-    int sh = p.off - w.anchor;
-    if (w.anchor >= 0 && sh >= 0 && sh <= WIN_SMAX) {
-        Shifted s = signed_shift(p, (uint32_t)(sh & 31));
-        uint32_t q = (uint32_t)sh >> 5;                   // 0..7 whole words
-        bool q1 = q & 1u, q2 = q & 2u, q4 = q & 4u;
-        // word t of the shifted product: u[t-q] inside 0..4, the sign word above, 0 below
-        uint32_t v0 = q1 ? 0u : s.u0, v1 = q1 ? s.u0 : s.u1, v2 = q1 ? s.u1 : s.u2;
-        uint32_t v3 = q1 ? s.u2 : s.u3, v4 = q1 ? s.u3 : s.u4, v5 = q1 ? s.u4 : s.sgn;
-        uint32_t w0 = q2 ? 0u : v0, w1 = q2 ? 0u : v1, w2 = q2 ? v0 : v2, w3 = q2 ? v1 : v3;
-        uint32_t w4 = q2 ? v2 : v4, w5 = q2 ? v3 : v5, w6 = q2 ? v4 : s.sgn, w7 = q2 ? v5 : s.sgn;
-        uint32_t x[WIN_WORDS];
-        x[0] = q4 ? 0u : w0;
-        x[1] = q4 ? 0u : w1;
-        x[2] = q4 ? 0u : w2;
-        x[3] = q4 ? 0u : w3;
-        x[4] = q4 ? w0 : w4;
-        x[5] = q4 ? w1 : w5;
-        x[6] = q4 ? w2 : w6;
-        x[7] = q4 ? w3 : w7;
-        x[8] = q4 ? w4 : s.sgn;
-        x[9] = q4 ? w5 : s.sgn;
-        x[10] = q4 ? w6 : s.sgn;
-        x[11] = q4 ? w7 : s.sgn;
-        add384(w.a, x);
-    } else {
-        cta_add_product(c, d, p);
-    }
-}
-
-// Sum the warp's windows and add the total into the CTA digits.  All lanes call.
-template <int ND>
-__device__ __forceinline__ void win_flush(Win &w, CtaAcc<ND> &c, int d)
-{
-    if (w.anchor < 0)
-        return;                                           // warp-uniform: nothing deposited
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         uint32_t y[WIN_WORDS];
@@ -271,6 +221,71 @@ __device__ __forceinline__ void win_flush(Win &w, CtaAcc<ND> &c, int d)
     }
     if (lane == 0)
         cta_touch(c, d, k, k + WIN_WORDS);
+#pragma unroll
+    for (int t = 0; t < WIN_WORDS; t++)
+        w.a[t] = 0u;
+}
+
+
+// Sum the warp's windows and add the total into the CTA digits.  All lanes call.
+template <int ND>
+__device__ __forceinline__ void win_flush(Win &w, CtaAcc<ND> &c, int d)
+{
+    if (w.anchor < 0)
+        return;                                           // warp-uniform: nothing deposited
+    win_flush_reset<ND>(w, c, d);
+}
+
+// Deposit a*b.  Must be called by all 32 lanes of the warp together (the
+// anchor is chosen with a warp reduction); `active` masks lanes with no term.
+template <int ND>
+__device__ __forceinline__ void win_deposit(Win &w, CtaAcc<ND> &c, int d, double a, double b, bool active,
+                                            bool &nf)
+{
+    Prod p = exact_product(a, b);
+    if (!active) {
+        p.off = -1;
+        p.nonfinite = false;
+    }
+    nf |= p.nonfinite;
+    // warp-uniform anchoring: set on the first nonzero term; when a term would
+    // overflow the top of the window, the window is flushed to the CTA digits
+    // and re-anchored on the current terms
+    int m = __reduce_max_sync(0xffffffffu, p.off);
+    if (m >= 0 && (w.anchor < 0 || m - w.anchor > WIN_SMAX)) {
+        if (w.anchor >= 0)
+            win_flush_reset<ND>(w, c, d);
+        w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
+    }
+    if (p.off < 0)
+        return;
+    int sh = p.off - w.anchor;
+    if (w.anchor >= 0 && sh >= 0 && sh <= WIN_SMAX) {
+        Shifted s = signed_shift(p, (uint32_t)(sh & 31));
+        uint32_t q = (uint32_t)sh >> 5;                   // 0..7 whole words
+        bool q1 = q & 1u, q2 = q & 2u, q4 = q & 4u;
+        // word t of the shifted product: u[t-q] inside 0..4, the sign word above, 0 below
+        uint32_t v0 = q1 ? 0u : s.u0, v1 = q1 ? s.u0 : s.u1, v2 = q1 ? s.u1 : s.u2;
+        uint32_t v3 = q1 ? s.u2 : s.u3, v4 = q1 ? s.u3 : s.u4, v5 = q1 ? s.u4 : s.sgn;
+        uint32_t w0 = q2 ? 0u : v0, w1 = q2 ? 0u : v1, w2 = q2 ? v0 : v2, w3 = q2 ? v1 : v3;
+        uint32_t w4 = q2 ? v2 : v4, w5 = q2 ? v3 : v5, w6 = q2 ? v4 : s.sgn, w7 = q2 ? v5 : s.sgn;
+        uint32_t x[WIN_WORDS];
+        x[0] = q4 ? 0u : w0;
+        x[1] = q4 ? 0u : w1;
+        x[2] = q4 ? 0u : w2;
+        x[3] = q4 ? 0u : w3;
+        x[4] = q4 ? w0 : w4;
+        x[5] = q4 ? w1 : w5;
+        x[6] = q4 ? w2 : w6;
+        x[7] = q4 ? w3 : w7;
+        x[8] = q4 ? w4 : s.sgn;
+        x[9] = q4 ? w5 : s.sgn;
+        x[10] = q4 ? w6 : s.sgn;
+        x[11] = q4 ? w7 : s.sgn;
+        add384(w.a, x);
+    } else {
+        cta_add_product(c, d, p);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -24,10 +24,23 @@
 
 namespace pbcg {
 
+#ifndef PBCG_UNR
+#define PBCG_UNR 8                      // SpMV entries loaded per batch
+#endif
+#ifndef PBCG_MINB_PLAIN
+#define PBCG_MINB_PLAIN 2               // resident CTAs per SM the plain passes are compiled for
+#endif
+#ifndef PBCG_MINB_EXACT
+#define PBCG_MINB_EXACT 2               // same, exact passes
+#endif
+#ifndef PBCG_INTERLEAVE
+#define PBCG_INTERLEAVE 1               // 1: warp w takes slices w, w + W, ...; 0: one contiguous run per warp
+#endif
+
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 constexpr int MAXD = 4;                 // most dots merged in one pass
-constexpr int UNR = 8;                  // SpMV entries loaded per batch
+constexpr int UNR = PBCG_UNR;
 
 enum : int { ST_RUNNING = 100, ST_CANDIDATE = 101 };
 enum : int { PH_SETUP = 0, PH_ITER = 1 };
@@ -74,9 +87,9 @@ __device__ __forceinline__ bool fin(double v)
     return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
-// slices [s0, s1) of this warp: contiguous runs over all warps of the grid
+// the slices of this warp: s0, s0 + step, ... below s1
 struct WarpRange {
-    int s0, s1, lane;
+    int s0, s1, step, lane;
 };
 
 __device__ __forceinline__ WarpRange warp_range(int nslices)
@@ -84,9 +97,16 @@ __device__ __forceinline__ WarpRange warp_range(int nslices)
     WarpRange R;
     const int nw = (gridDim.x * THREADS) >> 5;
     const int gw = (blockIdx.x * THREADS + threadIdx.x) >> 5;
+#if PBCG_INTERLEAVE
+    R.s0 = gw;
+    R.s1 = nslices;
+    R.step = nw;
+#else
     const int per = (nslices + nw - 1) / nw;
     R.s0 = min(gw * per, nslices);
     R.s1 = min(R.s0 + per, nslices);
+    R.step = 1;
+#endif
     R.lane = threadIdx.x & 31;
     return R;
 }
@@ -408,7 +428,7 @@ __device__ void setup_scalar(Ctl *c, double bb, double rho, double rw)
 
 #define PBCG_SLICE_LOOP(A)                                 \
     const WarpRange wr_ = warp_range((A).nslices);         \
-    for (int sl_ = wr_.s0; sl_ < wr_.s1; sl_++)
+    for (int sl_ = wr_.s0; sl_ < wr_.s1; sl_ += wr_.step)
 
 #define PBCG_ROW (sl_ * 32 + wr_.lane)
 
@@ -505,7 +525,7 @@ __global__ void __launch_bounds__(THREADS) k_setup3(Mat A, Vecs V, const Ctl *c)
 // ---------------------------------------------------------------------------
 // X(i): t_i = A w_i (i >= 1), p_i, s_i, z_i, q_i, y_i; dots (q,y), (y,y), (r0,s), (r0,z); omega_i
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, 2) k_pipe_x(Mat A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN) k_pipe_x(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
         return;
@@ -584,7 +604,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_pipe_x(Mat A, Vecs V, Ctl *c, Wo
 
 // Y(i): v_i = A z_i, x_{i+1}, r_{i+1}, w_{i+1}; dots (r0,r), (r0,w), (r,r); beta_i, alpha_{i+1}, stop test
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, 3 - MODE) k_pipe_y(Mat A, Vecs V, Ctl *c, Work *wk)
+__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN) k_pipe_y(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
         return;
