@@ -166,6 +166,34 @@ int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double
                        int32_t maxit, int alg, int dot_mode, pbcg_result *out, char (*names)[32],
                        double *ms, int32_t *launches, int32_t cap, int32_t *count);
 
+/*
+ * pbcg_dot_noalloc: the dot product of pbcg_dot for callers that cannot
+ * allocate device memory (code inside another allocator's arena, a fixed or
+ * capped memory budget, or a loop that must not enter the allocator, since
+ * cudaMalloc and cudaFree can synchronise the device).  It needs no context
+ * and calls no cudaMalloc, cudaFree or other allocating routine.  The paper
+ * has no counterpart: it is a packaging of the exact dot for such callers.
+ *
+ * a, b: n doubles each, device pointers on the current device; out: one
+ * double in device memory, written with the result ((a,b) in dot_mode; exact
+ * mode: correctly rounded, NaN if an operand is NaN or Inf).  cuda_stream: the
+ * stream to launch on (NULL: the legacy default stream).  The call is
+ * asynchronous; the result is ready when the stream reaches it.
+ *
+ * Scratch: the grid-wide merge state lives in one file-scope device array of
+ * 70,144 bytes that every GPU loading this library holds until the process
+ * exits.  Every call on a device shares it and clears it first; calls that
+ * overlap on the GPU (other streams, other host threads) race on it and give
+ * wrong results, so serialise them.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and the occupancy of its
+ * kernels, with that device current; make that first call before any stream
+ * capture.
+ *
+ * Limits: 0 <= n <= 2^31 - 1 (INVALID beyond); at most 2048 CTAs per call.
+ * Errors: INVALID (bad size, NULL pointer, unknown dot_mode), CUDA.
+ */
+int pbcg_dot_noalloc(int64_t n, const double *a, const double *b, int dot_mode, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

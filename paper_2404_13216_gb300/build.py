@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpbcg.so")
-SOURCES = ["api.cu"]
+SOURCES = ["api.cu", "noalloc.cu"]
 HEADERS = ["exdot.cuh", "kernels.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -42,16 +42,31 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
+    flags = [ARCH, "-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC"]
+    if verbose:
+        flags.append("-Xptxas=-v")
+    # compile the translation units in parallel, then link
+    procs, objs = [], []
+    for src in SOURCES:
+        obj = os.path.join(OUT_DIR, src.replace(".cu", f".{os.getpid()}.o"))
+        objs.append(obj)
+        procs.append(subprocess.Popen([_nvcc()] + flags + ["-c", os.path.join(SRC_DIR, src), "-o", obj],
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    errs = []
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            errs.append(out + err)
+        elif verbose:
+            sys.stderr.write(err)
+    if errs:
+        raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), ARCH, "-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-shared", "-o", tmp] + [os.path.join(SRC_DIR, s) for s in SOURCES]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run([_nvcc(), ARCH, "-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    for o in objs:
+        os.remove(o)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
     return LIB
 

@@ -327,7 +327,7 @@ __device__ __forceinline__ uint32_t bit_at(const uint32_t *w, int lo, int hi, in
     return (w[k] >> (i & 31)) & 1u;
 }
 
-__device__ double gacc_round_reset(GAcc *g, uint32_t *scratch)
+static __device__ double gacc_round_reset(GAcc *g, uint32_t *scratch)
 {
     int nf = *((volatile int *)&g->nf);
     int k0 = *((volatile int *)&g->kmin), k1 = *((volatile int *)&g->kmax);

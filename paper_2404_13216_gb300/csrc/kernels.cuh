@@ -346,7 +346,7 @@ __device__ __forceinline__ void set_cond(Ctl *c)
 }
 
 // the part of a step after the stop test: breakdown checks, beta, alpha, maxit
-__device__ void post_stop(Ctl *c)
+static __device__ void post_stop(Ctl *c)
 {
     if (c->phase == PH_SETUP) {
         if (c->alg == ALG_PIPELINED) {
@@ -388,7 +388,7 @@ __device__ void post_stop(Ctl *c)
 }
 
 // residual of step k, stop test, then post_stop
-__device__ void residual_step(Ctl *c, double rr)
+static __device__ void residual_step(Ctl *c, double rr)
 {
     double res = __ddiv_rn(__dsqrt_rn(rr), c->normb);
     c->res = res;
@@ -401,7 +401,7 @@ __device__ void residual_step(Ctl *c, double rr)
 }
 
 // after the setup dots (b,b), (r0,r0) [, (r0,w0)]
-__device__ void setup_scalar(Ctl *c, double bb, double rho, double rw)
+static __device__ void setup_scalar(Ctl *c, double bb, double rho, double rw)
 {
     c->bb = bb;
     c->rho = rho;
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(THREADS) k_setup2(Mat A, Vecs V, Ctl *c, Work 
 }
 
 // S3 (p-BiCGStab): t0 = A w0
-__global__ void __launch_bounds__(THREADS) k_setup3(Mat A, Vecs V, const Ctl *c)
+static __global__ void __launch_bounds__(THREADS) k_setup3(Mat A, Vecs V, const Ctl *c)
 {
     if (c->status != ST_RUNNING && c->status != ST_CANDIDATE)
         return;
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
 // BiCGStab passes
 // ---------------------------------------------------------------------------
 // P(i), i >= 1: p = fma(beta, fma(-omega, s, p), r)
-__global__ void __launch_bounds__(THREADS) k_bicg_p(Mat A, Vecs V, const Ctl *c)
+static __global__ void __launch_bounds__(THREADS) k_bicg_p(Mat A, Vecs V, const Ctl *c)
 {
     if (c->status != ST_RUNNING || c->it == 0)
         return;
@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(THREADS) k_bicg_c(Mat A, Vecs V, Ctl *c, Work 
 // ---------------------------------------------------------------------------
 // true residual ||b - A x|| / ||b|| with exact dots; resolves a candidate stop
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(THREADS) k_true_res(Mat A, Vecs V, Ctl *c, Work *wk)
+static __global__ void __launch_bounds__(THREADS) k_true_res(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     __shared__ Shm<2> sh;
     shm_init<2, 1>(sh);
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(THREADS) k_dot(long long n, const double *a, c
         *out = sh.dv[0];
 }
 
-__global__ void __launch_bounds__(THREADS) k_spmv(Mat A, const double *x, double *y)
+static __global__ void __launch_bounds__(THREADS) k_spmv(Mat A, const double *x, double *y)
 {
     PBCG_SLICE_LOOP(A)
     {
@@ -897,14 +897,14 @@ __global__ void __launch_bounds__(THREADS) k_spmv(Mat A, const double *x, double
 }
 
 // dst[p] = src[perm[p]] (into solver order)
-__global__ void k_gather(int n, const int *__restrict__ perm, const double *__restrict__ src, double *dst)
+static __global__ void k_gather(int n, const int *__restrict__ perm, const double *__restrict__ src, double *dst)
 {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
         dst[p] = src[perm[p]];
 }
 
 // dst[perm[p]] = src[p] (back to caller order)
-__global__ void k_scatter(int n, const int *__restrict__ perm, const double *__restrict__ src, double *dst)
+static __global__ void k_scatter(int n, const int *__restrict__ perm, const double *__restrict__ src, double *dst)
 {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
         dst[perm[p]] = src[p];

@@ -23,7 +23,7 @@ PLAIN, EXACT = 0, 1
 
 EXPORTS = ("pbcg_create", "pbcg_destroy", "pbcg_last_error", "pbcg_csr_upload", "pbcg_mat_free",
            "pbcg_solve", "pbcg_solve_batched", "pbcg_residual_history", "pbcg_dot", "pbcg_spmv",
-           "pbcg_profile_solve")
+           "pbcg_profile_solve", "pbcg_dot_noalloc")
 
 
 class PbcgError(RuntimeError):
@@ -67,6 +67,8 @@ def load_library(path: str = LIB_PATH):
     lib.pbcg_profile_solve.argtypes = [P, P, P, P, d, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result),
                                        P, P, P, i32, ctypes.POINTER(i32)]
     lib.pbcg_profile_solve.restype = ctypes.c_int
+    lib.pbcg_dot_noalloc.argtypes = [i64, P, P, ctypes.c_int, P, P]
+    lib.pbcg_dot_noalloc.restype = ctypes.c_int
     return lib
 
 
@@ -86,6 +88,15 @@ def _host(a, dtype):
     if hasattr(a, "data_ptr"):
         return a
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def dot_noalloc(a, b, out, mode: int = EXACT, stream=None) -> int:
+    """pbcg_dot_noalloc: (a, b) into out[0]; a, b, out are CUDA tensors on the
+    current device.  Asynchronous on `stream` (a raw cudaStream_t or None).
+    Returns the library's status code (0 or negative)."""
+    n = a.numel()
+    s = ctypes.c_void_p(stream) if stream else None
+    return _lib.pbcg_dot_noalloc(n, _ptr(a), _ptr(b), int(mode), _ptr(out), s)
 
 
 @dataclass
