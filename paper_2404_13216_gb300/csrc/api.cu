@@ -60,6 +60,7 @@ struct pbcg_mat {
     int *ci;               // [padded], solver-order column indices
     double *va;            // [padded]
     int *perm;             // [n] solver row p holds caller row perm[p]; NULL when rows keep their order
+    bool narrow;           // every 256-row tile spans at most MCAP SELL entries (staged in shared memory)
 };
 
 struct pbcg_ctx {
@@ -140,14 +141,16 @@ Vecs vecs_of(Workspace &ws)
 }
 
 // persistent grid: every CTA resident (occupancy of this kernel x SMs), at least one slice per warp
-int grid_for(pbcg_ctx *ctx, const void *fn, long long nslices)
+int grid_for(pbcg_ctx *ctx, const void *fn, long long nslices, size_t smem = 0)
 {
     int per_sm = 0;
     auto it = ctx->occ.find(fn);
     if (it != ctx->occ.end()) {
         per_sm = it->second;
     } else {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, 0) != cudaSuccess || per_sm < 1)
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, smem) != cudaSuccess || per_sm < 1)
             per_sm = 1;
         cudaGetLastError();
         ctx->occ[fn] = per_sm;
@@ -221,8 +224,11 @@ int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
             p = nullptr;
         }
         ws.n_cap = 0;
-        for (auto &p : ws.vec)
-            CK(cudaMalloc(&p, sizeof(double) * (size_t)n));
+        const size_t npad = (size_t)((n + TILE_ROWS - 1) / TILE_ROWS) * TILE_ROWS;
+        for (auto &p : ws.vec) {
+            CK(cudaMalloc(&p, sizeof(double) * npad));
+            CK(cudaMemset(p, 0, sizeof(double) * npad));
+        }
         ws.n_cap = n;
     }
     if (hist_cap > ws.hist_cap) {
@@ -244,6 +250,7 @@ struct Sell {
     int nslices = 0;
     long long padded = 0;
     bool permuted = false;
+    bool narrow = true;
     std::vector<int> sl_off, rlen, ci, perm;
     std::vector<double> va;
 };
@@ -302,9 +309,18 @@ bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val,
         return false;
     S.sl_off[ns] = (int)off;
     S.padded = off;
+    // pad to whole 256-row tiles so that tile copies stay inside the arrays
+    const int ntiles = (ns + TILE_SLICES - 1) / TILE_SLICES;
+    S.sl_off.resize((size_t)ntiles * TILE_SLICES + SLOFF_STAGE, (int)off);
+    S.narrow = true;
+    for (int t = 0; t < ntiles; t++) {
+        int a = S.sl_off[(size_t)t * TILE_SLICES], b = S.sl_off[std::min(ns, (t + 1) * TILE_SLICES)];
+        if (b - a > MCAP)
+            S.narrow = false;
+    }
     S.ci.assign((size_t)off, 0);
     S.va.assign((size_t)off, 0.0);
-    S.rlen.assign((size_t)ns * 32, 0);
+    S.rlen.assign((size_t)((ns + TILE_SLICES - 1) / TILE_SLICES) * TILE_ROWS, 0);
     for (int p = 0; p < n; p++) {
         int i = S.perm[p], s = p / 32, l = p % 32;
         S.rlen[p] = len[i];
@@ -338,12 +354,18 @@ int validate_csr_host(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *rp, 
     return 0;
 }
 
+template <int NV, bool MATS>
+constexpr size_t stage_bytes()
+{
+    return StageLayout<NV, MATS>::TOTAL;
+}
+
 template <int MODE>
 struct Kern {
+    static void *pipe_x_tma(bool mats) { return mats ? (void *)k_pipe_x_tma<MODE, true> : (void *)k_pipe_x_tma<MODE, false>; }
+    static void *pipe_y_tma(bool mats) { return mats ? (void *)k_pipe_y_tma<MODE, true> : (void *)k_pipe_y_tma<MODE, false>; }
     static void *setup1() { return (void *)k_setup1<MODE>; }
     static void *setup2() { return (void *)k_setup2<MODE>; }
-    static void *pipe_x() { return (void *)k_pipe_x<MODE>; }
-    static void *pipe_y() { return (void *)k_pipe_y<MODE>; }
     static void *bicg_a() { return (void *)k_bicg_a<MODE>; }
     static void *bicg_b() { return (void *)k_bicg_b<MODE>; }
     static void *bicg_c() { return (void *)k_bicg_c<MODE>; }
@@ -353,30 +375,35 @@ struct Kern {
 struct BodyKernel {
     void *fn;
     const char *name;
-    int has_work;    // kernel takes (Csr, Vecs, Ctl*, Work*) rather than (Csr, Vecs, const Ctl*)
+    int has_work;    // kernel takes (Mat, Vecs, Ctl*, Work*) rather than (Mat, Vecs, const Ctl*)
+    size_t smem;     // dynamic shared memory
 };
 
-std::vector<BodyKernel> body_kernels(int alg, int mode)
+std::vector<BodyKernel> body_kernels(int alg, int mode, bool narrow)
 {
     std::vector<BodyKernel> k;
     if (alg == PBCG_ALG_PIPELINED) {
-        k.push_back({mode ? Kern<1>::pipe_x() : Kern<0>::pipe_x(), mode ? "pipe_x_exact" : "pipe_x_plain", 1});
-        k.push_back({mode ? Kern<1>::pipe_y() : Kern<0>::pipe_y(), mode ? "pipe_y_exact" : "pipe_y_plain", 1});
+        size_t sx = narrow ? stage_bytes<7, true>() : stage_bytes<7, false>();
+        size_t sy = narrow ? stage_bytes<6, true>() : stage_bytes<6, false>();
+        k.push_back({mode ? Kern<1>::pipe_x_tma(narrow) : Kern<0>::pipe_x_tma(narrow),
+                     mode ? "pipe_x_exact" : "pipe_x_plain", 1, sx});
+        k.push_back({mode ? Kern<1>::pipe_y_tma(narrow) : Kern<0>::pipe_y_tma(narrow),
+                     mode ? "pipe_y_exact" : "pipe_y_plain", 1, sy});
     } else {
-        k.push_back({(void *)k_bicg_p, "bicg_p", 0});
-        k.push_back({mode ? Kern<1>::bicg_a() : Kern<0>::bicg_a(), mode ? "bicg_a_exact" : "bicg_a_plain", 1});
-        k.push_back({mode ? Kern<1>::bicg_b() : Kern<0>::bicg_b(), mode ? "bicg_b_exact" : "bicg_b_plain", 1});
-        k.push_back({mode ? Kern<1>::bicg_c() : Kern<0>::bicg_c(), mode ? "bicg_c_exact" : "bicg_c_plain", 1});
+        k.push_back({(void *)k_bicg_p, "bicg_p", 0, 0});
+        k.push_back({mode ? Kern<1>::bicg_a() : Kern<0>::bicg_a(), mode ? "bicg_a_exact" : "bicg_a_plain", 1, 0});
+        k.push_back({mode ? Kern<1>::bicg_b() : Kern<0>::bicg_b(), mode ? "bicg_b_exact" : "bicg_b_plain", 1, 0});
+        k.push_back({mode ? Kern<1>::bicg_c() : Kern<0>::bicg_c(), mode ? "bicg_c_exact" : "bicg_c_plain", 1, 0});
     }
     return k;
 }
 
-int launch_kernel(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work)
+int launch_kernel(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work, size_t smem)
 {
     void *args4[4] = {&A, &V, &c, &wk};
     void *args3[3] = {&A, &V, &c};
-    int grid = grid_for(ctx, fn, A.nslices);
-    CK(cudaLaunchKernel(fn, dim3(grid), dim3(THREADS), has_work ? args4 : args3, 0, ctx->stream));
+    int grid = grid_for(ctx, fn, A.nslices, smem);
+    CK(cudaLaunchKernel(fn, dim3(grid), dim3(THREADS), has_work ? args4 : args3, smem, ctx->stream));
     return 0;
 }
 
@@ -405,15 +432,15 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, LoopGraph **ou
     Ctl *c = ctx->ws.ctl;
     Work *wk = ctx->ws.wk;
     cudaGraphNode_t prev = nullptr;
-    for (auto &bk : body_kernels(alg, mode)) {
+    for (auto &bk : body_kernels(alg, mode, m->narrow)) {
         void *args4[4] = {&A, &V, &c, &wk};
         void *args3[3] = {&A, &V, &c};
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof kp);
         kp.func = bk.fn;
-        kp.gridDim = dim3(grid_for(ctx, bk.fn, A.nslices));
+        kp.gridDim = dim3(grid_for(ctx, bk.fn, A.nslices, bk.smem));
         kp.blockDim = dim3(THREADS);
-        kp.sharedMemBytes = 0;
+        kp.sharedMemBytes = (unsigned)bk.smem;
         kp.kernelParams = bk.has_work ? args4 : args3;
         cudaGraphNode_t node;
         CK(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
@@ -463,7 +490,7 @@ struct Launcher {
     long long launches = 0;
     std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
 
-    int go(const char *name, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work)
+    int go(const char *name, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work, size_t smem = 0)
     {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (prof) {
@@ -471,7 +498,7 @@ struct Launcher {
             CK(cudaEventCreate(&e1));
             CK(cudaEventRecord(e0, ctx->stream));
         }
-        int rc = launch_kernel(ctx, fn, A, V, c, wk, has_work);
+        int rc = launch_kernel(ctx, fn, A, V, c, wk, has_work, smem);
         if (rc)
             return rc;
         launches++;
@@ -587,7 +614,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         return rc;
     bool cond_on = false;
     bool true_done = false;
-    auto body = body_kernels(alg, mode);
+    auto body = body_kernels(alg, mode, m->narrow);
     bool fresh = false;      // h_ctl already mirrors the device after a graph launch
     for (;;) {
         if (prof && (rc = L.flush()))
@@ -609,7 +636,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         if (prof) {
             // host-driven iteration, one kernel at a time
             for (auto &bk : body)
-                if ((rc = L.go(bk.name, bk.fn, A, V, ws.ctl, ws.wk, bk.has_work)))
+                if ((rc = L.go(bk.name, bk.fn, A, V, ws.ctl, ws.wk, bk.has_work, bk.smem)))
                     return rc;
         } else {
             LoopGraph *G = nullptr;
@@ -650,6 +677,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         CK(cudaMemcpyAsync(&ws.ctl->use_cond, &zero, sizeof zero, cudaMemcpyHostToDevice, ctx->stream));
     }
     Ctl fin_ctl = *ctx->h_ctl;
+    if (fin_ctl.err || fin_ctl.status == ST_TIMEOUT)
+        return fail(ctx, PBCG_ERR_TIMEOUT, "a bounded device wait expired (bulk copy did not complete)");
     if ((rc = vec_out(ctx, m, ws.vec[V_X], x)))
         return rc;
     int hl = fin_ctl.it + 1;
@@ -768,6 +797,7 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     m->padded = S.padded;
     m->sl_off = m->rlen = m->ci = m->perm = nullptr;
     m->va = nullptr;
+    m->narrow = S.narrow;
     size_t P = (size_t)(S.padded ? S.padded : 1);
     cudaError_t e = cudaMalloc(&m->sl_off, sizeof(int) * S.sl_off.size());
     if (e == cudaSuccess)

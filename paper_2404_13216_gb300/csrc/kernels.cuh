@@ -21,6 +21,7 @@
 // Grid: persistent, one contiguous run of slices per warp.
 #pragma once
 #include "exdot.cuh"
+#include "tma.cuh"
 
 namespace pbcg {
 
@@ -42,7 +43,7 @@ constexpr int WARPS = THREADS / 32;
 constexpr int MAXD = 4;                 // most dots merged in one pass
 constexpr int UNR = PBCG_UNR;
 
-enum : int { ST_RUNNING = 100, ST_CANDIDATE = 101 };
+enum : int { ST_RUNNING = 100, ST_CANDIDATE = 101, ST_TIMEOUT = 200 };
 enum : int { PH_SETUP = 0, PH_ITER = 1 };
 enum : int { ALG_BICGSTAB = 0, ALG_PIPELINED = 1 };
 
@@ -54,7 +55,7 @@ struct Ctl {
     double normb, res, target, tol;
     double trueres, bbx, pad_d0, pad_d1;
     int it, maxit, status, phase;
-    int alg, use_cond, pad_i0, pad_i1;
+    int alg, use_cond, err, pad_i1;     // err: a bounded device wait expired
     unsigned long long cond;            // cudaGraphConditionalHandle of the loop
     double *hist;
     int hist_cap, pad_i2;
@@ -521,147 +522,6 @@ static __global__ void __launch_bounds__(THREADS) k_setup3(Mat A, Vecs V, const 
 }
 
 // ---------------------------------------------------------------------------
-// p-BiCGStab passes
-// ---------------------------------------------------------------------------
-// X(i): t_i = A w_i (i >= 1), p_i, s_i, z_i, q_i, y_i; dots (q,y), (y,y), (r0,s), (r0,z); omega_i
-template <int MODE>
-__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN) k_pipe_x(Mat A, Vecs V, Ctl *c, Work *wk)
-{
-    if (c->status != ST_RUNNING)
-        return;
-    __shared__ Shm<4> sh;
-    shm_init<4, MODE>(sh);
-    __syncthreads();
-    const bool first = (c->it == 0);
-    const double alpha = c->alpha, beta = c->beta, omega = c->omega;
-    const double nalpha = -alpha, nomega = -omega;
-    DotSet<4, MODE> D;
-    D.init();
-    PBCG_SLICE_LOOP(A)
-    {
-        int i = PBCG_ROW;
-        bool act = i < A.n;
-        double ri = 0.0, wi = 0.0, r0i = 0.0, pold = 0.0, sold = 0.0, zold = 0.0, vold = 0.0, ti = 0.0;
-        if (act) {
-            ri = V.r[i];
-            wi = V.w[i];
-            r0i = V.r0[i];
-            if (first) {
-                ti = V.t[i];
-            } else {
-                pold = V.p[i];
-                sold = V.s[i];
-                zold = V.z[i];
-                vold = V.v[i];
-            }
-        }
-        if (!first) {
-            RowRef R = row_ref(A, sl_, wr_.lane);
-            ti = spmv_row(A, R, V.w);
-        }
-        double pi, si, zi, q = 0.0, y = 0.0;
-        if (first) {
-            pi = ri;
-            si = wi;
-            zi = ti;
-        } else {
-            pi = __fma_rn(beta, __fma_rn(nomega, sold, pold), ri);
-            si = __fma_rn(beta, __fma_rn(nomega, zold, sold), wi);
-            zi = __fma_rn(beta, __fma_rn(nomega, vold, zold), ti);
-        }
-        if (act) {
-            q = __fma_rn(nalpha, si, ri);
-            y = __fma_rn(nalpha, zi, wi);
-            if (!first)
-                V.t[i] = ti;
-            V.p[i] = pi;
-            V.s[i] = si;
-            V.z[i] = zi;
-            V.q[i] = q;
-            V.y[i] = y;
-        }
-        D.add(sh, 0, q, y, act);
-        D.add(sh, 1, y, y, act);
-        D.add(sh, 2, r0i, si, act);
-        D.add(sh, 3, r0i, zi, act);
-    }
-    if (!finalize<4, MODE>(D, sh, wk))
-        return;
-    if (threadIdx.x == 0) {
-        double qy = sh.dv[0], yy = sh.dv[1];
-        c->qy = qy;
-        c->yy = yy;
-        c->rs = sh.dv[2];
-        c->rz = sh.dv[3];
-        if (!fin(qy) || !fin(yy)) {
-            c->status = 3;
-            set_cond(c);
-        } else {
-            c->omega = (yy == 0.0) ? 0.0 : __ddiv_rn(qy, yy);
-        }
-    }
-}
-
-// Y(i): v_i = A z_i, x_{i+1}, r_{i+1}, w_{i+1}; dots (r0,r), (r0,w), (r,r); beta_i, alpha_{i+1}, stop test
-template <int MODE>
-__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN) k_pipe_y(Mat A, Vecs V, Ctl *c, Work *wk)
-{
-    if (c->status != ST_RUNNING)
-        return;
-    __shared__ Shm<3> sh;
-    shm_init<3, MODE>(sh);
-    __syncthreads();
-    const double alpha = c->alpha, omega = c->omega;
-    const double nalpha = -alpha, nomega = -omega;
-    DotSet<3, MODE> D;
-    D.init();
-    PBCG_SLICE_LOOP(A)
-    {
-        int i = PBCG_ROW;
-        bool act = i < A.n;
-        double q = 0.0, y = 0.0, pi = 0.0, xi = 0.0, ti = 0.0, r0i = 0.0;
-        if (act) {
-            q = V.q[i];
-            y = V.y[i];
-            pi = V.p[i];
-            xi = V.x[i];
-            ti = V.t[i];
-            r0i = V.r0[i];
-        }
-        RowRef R = row_ref(A, sl_, wr_.lane);
-        double vi = spmv_row(A, R, V.z);
-        double rn = 0.0, wn = 0.0;
-        if (act) {
-            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, pi, xi));
-            rn = __fma_rn(nomega, y, q);
-            wn = __fma_rn(nomega, __fma_rn(nalpha, vi, ti), y);
-            V.v[i] = vi;
-            V.r[i] = rn;
-            V.w[i] = wn;
-        }
-        D.add(sh, 0, r0i, rn, act);
-        D.add(sh, 1, r0i, wn, act);
-        D.add(sh, 2, rn, rn, act);
-    }
-    if (!finalize<3, MODE>(D, sh, wk))
-        return;
-    if (threadIdx.x == 0) {
-        double rho_new = sh.dv[0], rw = sh.dv[1], rr = sh.dv[2];
-        c->rho_new = rho_new;
-        c->rw = rw;
-        c->rr = rr;
-        c->phase = PH_ITER;
-        if (!fin(rho_new) || !fin(rw) || !fin(c->rs) || !fin(c->rz) || !fin(rr)) {
-            c->status = 3;
-        } else {
-            c->it += 1;
-            residual_step(c, rr);
-        }
-        set_cond(c);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // BiCGStab passes
 // ---------------------------------------------------------------------------
 // P(i), i >= 1: p = fma(beta, fma(-omega, s, p), r)
@@ -908,6 +768,298 @@ static __global__ void k_scatter(int n, const int *__restrict__ perm, const doub
 {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
         dst[perm[p]] = src[p];
+}
+
+
+// ---------------------------------------------------------------------------
+// staged passes: tiles of 256 rows double-buffered in shared memory by TMA
+// ---------------------------------------------------------------------------
+template <int NV, bool MATS>
+struct TilePipe {
+    using L = StageLayout<NV, MATS>;
+    uint8_t *smem;
+    uint64_t *bar;
+    StageInfo *info;
+
+    __device__ __forceinline__ uint8_t *stage(int k) const { return smem + (size_t)k * L::STAGE; }
+    __device__ __forceinline__ const double *vec(int k, int v) const
+    {
+        return reinterpret_cast<const double *>(stage(k)) + v * TILE_ROWS;
+    }
+    __device__ __forceinline__ const double *va(int k) const
+    {
+        return reinterpret_cast<const double *>(stage(k) + L::VEC);
+    }
+    __device__ __forceinline__ const int *ci(int k) const
+    {
+        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::VA);
+    }
+    __device__ __forceinline__ const int *rlen(int k) const
+    {
+        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::VA + L::CI);
+    }
+    __device__ __forceinline__ const int *sloff(int k) const
+    {
+        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::VA + L::CI + L::RLEN);
+    }
+
+    // thread 0: copy tile `tile` (nv of the NV vectors) into stage k; e0/e1 are
+    // sl_off[first slice] and sl_off[end slice] of the tile, loaded beforehand
+    __device__ __forceinline__ void issue(int k, int tile, int e0, int e1, const Mat &A,
+                                          const double *const (&src)[NV], int nv)
+    {
+        const int s0 = tile * TILE_SLICES;
+        const int span = e1 - e0;
+        const bool staged = MATS && span > 0 && span <= MCAP;
+        info[k].e0 = e0;
+        info[k].staged = staged;
+        uint32_t bytes = (uint32_t)nv * TILE_ROWS * 8 + L::RLEN + L::SLOFF + (staged ? (uint32_t)span * 12u : 0u);
+        fence_async_shared();
+        mbar_arrive_expect_tx(&bar[k], bytes);
+        const size_t row0 = (size_t)tile * TILE_ROWS;
+        for (int v = 0; v < nv; v++)
+            bulk_g2s(stage(k) + (size_t)v * TILE_ROWS * 8, src[v] + row0, TILE_ROWS * 8, &bar[k]);
+        bulk_g2s(stage(k) + L::VEC + L::VA + L::CI, A.rlen + row0, L::RLEN, &bar[k]);
+        bulk_g2s(stage(k) + L::VEC + L::VA + L::CI + L::RLEN, A.sl_off + s0, L::SLOFF, &bar[k]);
+        if (staged) {
+            bulk_g2s(stage(k) + L::VEC + L::VA, A.ci + e0, (uint32_t)span * 4u, &bar[k]);
+            bulk_g2s(stage(k) + L::VEC, A.va + e0, (uint32_t)span * 8u, &bar[k]);
+        }
+    }
+
+    // SpMV row of this lane from stage k (matrix from shared memory when staged)
+    __device__ __forceinline__ double spmv(int k, const Mat &A, int warp, int lane, const double *__restrict__ x) const
+    {
+        const int *so = sloff(k);
+        const int off = so[warp];
+        const int width = (so[warp + 1] - off) >> 5;
+        const int len = rlen(k)[warp * 32 + lane];
+        const bool st = info[k].staged;
+        const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
+        const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
+        double acc = 0.0;
+        for (int j0 = 0; j0 < width; j0 += UNR) {
+            int c[UNR];
+            double v[UNR], xv[UNR];
+#pragma unroll
+            for (int j = 0; j < UNR; j++) {
+                if (j0 + j < len) {
+                    c[j] = cp[(j0 + j) * 32];
+                    v[j] = vp[(j0 + j) * 32];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < UNR; j++)
+                if (j0 + j < len)
+                    xv[j] = __ldg(x + c[j]);
+#pragma unroll
+            for (int j = 0; j < UNR; j++)
+                if (j0 + j < len)
+                    acc = __fma_rn(v[j], xv[j], acc);
+        }
+        return acc;
+    }
+};
+
+// common tile loop: prologue, bounded waits, refill after each tile
+template <int NV, bool MATS, class Body>
+__device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&src)[NV], int nv, Ctl *c,
+                                          uint8_t *dsm, Body body)
+{
+    __shared__ uint64_t bar[NSTAGE];
+    __shared__ StageInfo info[NSTAGE];
+    TilePipe<NV, MATS> P{dsm, bar, info};
+    const int ntiles = (A.nslices + TILE_SLICES - 1) / TILE_SLICES;
+    const int my = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    auto tile_of = [&](int jj) { return (int)blockIdx.x + jj * (int)gridDim.x; };
+    auto end_slice = [&](int t) { return min((t + 1) * TILE_SLICES, A.nslices); };
+    int pe0 = 0, pe1 = 0;            // thread 0: offsets of the next tile to issue
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NSTAGE; k++)
+            mbar_init(&bar[k], 1);
+        fence_mbar_init();
+        fence_async_shared();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NSTAGE && k < my; k++) {
+            const int t = tile_of(k);
+            P.issue(k, t, A.sl_off[t * TILE_SLICES], A.sl_off[end_slice(t)], A, src, nv);
+        }
+        if (NSTAGE < my) {
+            const int t = tile_of(NSTAGE);
+            pe0 = A.sl_off[t * TILE_SLICES];
+            pe1 = A.sl_off[end_slice(t)];
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool tmo = false;
+    int j = 0;
+    for (; j < my; j++) {
+        const int k = j % NSTAGE;
+        const bool ok = mbar_wait_bounded(&bar[k], (uint32_t)(j / NSTAGE) & 1u);
+        if (__syncthreads_or(!ok)) {
+            tmo = true;              // uniform: some thread gave up on this stage
+            break;
+        }
+        body(P, k, tile_of(j), warp, lane);
+        __syncthreads();
+        if (threadIdx.x == 0 && j + NSTAGE < my) {
+            P.issue(k, tile_of(j + NSTAGE), pe0, pe1, A, src, nv);
+            if (j + NSTAGE + 1 < my) {
+                const int t = tile_of(j + NSTAGE + 1);
+                pe0 = A.sl_off[t * TILE_SLICES];
+                pe1 = A.sl_off[end_slice(t)];
+            }
+        }
+    }
+    if (tmo) {
+        // give up: wait (bounded) for this CTA's copies still in flight, then report
+        if (threadIdx.x == 0) {
+            for (int jj = j; jj < my && jj < j + NSTAGE; jj++)
+                mbar_wait_bounded(&bar[jj % NSTAGE], (uint32_t)(jj / NSTAGE) & 1u);
+            atomicOr(&c->err, 1);
+        }
+        __syncthreads();
+    }
+}
+
+// X(i) staged: t_i = A w_i (i >= 1), p, s, z, q, y; dots (q,y), (y,y), (r0,s), (r0,z); omega_i
+template <int MODE, bool MATS>
+__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+    k_pipe_x_tma(Mat A, Vecs V, Ctl *c, Work *wk)
+{
+    if (c->status != ST_RUNNING)
+        return;
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ Shm<4> sh;
+    shm_init<4, MODE>(sh);
+    const bool first = (c->it == 0);
+    const double alpha = c->alpha, beta = c->beta, omega = c->omega;
+    const double nalpha = -alpha, nomega = -omega;
+    DotSet<4, MODE> D;
+    D.init();
+    // stage slots: 0 r, 1 w, 2 r0, 3 p (t when first), 4 s, 5 z, 6 v
+    const double *const src[7] = {V.r, V.w, V.r0, first ? V.t : V.p, V.s, V.z, V.v};
+    tile_loop<7, MATS>(A, src, first ? 4 : 7, c, dsm,
+                       [&](const TilePipe<7, MATS> &P, int k, int tile, int warp, int lane) {
+        const int sl = tile * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const bool act = sl < A.nslices && i < A.n;
+        const int o = warp * 32 + lane;
+        double q = 0.0, y = 0.0, r0i = 0.0, si = 0.0, zi = 0.0;
+        if (sl < A.nslices) {
+            const double ri = P.vec(k, 0)[o], wi = P.vec(k, 1)[o];
+            r0i = P.vec(k, 2)[o];
+            double pi, ti;
+            if (first) {
+                ti = P.vec(k, 3)[o];
+                pi = ri;
+                si = wi;
+                zi = ti;
+            } else {
+                ti = P.spmv(k, A, warp, lane, V.w);
+                const double pold = P.vec(k, 3)[o], sold = P.vec(k, 4)[o];
+                const double zold = P.vec(k, 5)[o], vold = P.vec(k, 6)[o];
+                pi = __fma_rn(beta, __fma_rn(nomega, sold, pold), ri);
+                si = __fma_rn(beta, __fma_rn(nomega, zold, sold), wi);
+                zi = __fma_rn(beta, __fma_rn(nomega, vold, zold), ti);
+            }
+            q = __fma_rn(nalpha, si, ri);
+            y = __fma_rn(nalpha, zi, wi);
+            if (act) {
+                if (!first)
+                    V.t[i] = ti;
+                V.p[i] = pi;
+                V.s[i] = si;
+                V.z[i] = zi;
+                V.q[i] = q;
+                V.y[i] = y;
+            }
+        }
+        D.add(sh, 0, q, y, act);
+        D.add(sh, 1, y, y, act);
+        D.add(sh, 2, r0i, si, act);
+        D.add(sh, 3, r0i, zi, act);
+    });
+    if (!finalize<4, MODE>(D, sh, wk))
+        return;
+    if (threadIdx.x == 0) {
+        double qy = sh.dv[0], yy = sh.dv[1];
+        c->qy = qy;
+        c->yy = yy;
+        c->rs = sh.dv[2];
+        c->rz = sh.dv[3];
+        if (c->err) {
+            c->status = ST_TIMEOUT;
+            set_cond(c);
+        } else if (!fin(qy) || !fin(yy)) {
+            c->status = 3;
+            set_cond(c);
+        } else {
+            c->omega = (yy == 0.0) ? 0.0 : __ddiv_rn(qy, yy);
+        }
+    }
+}
+
+// Y(i) staged: v_i = A z_i, x_{i+1}, r_{i+1}, w_{i+1}; dots (r0,r), (r0,w), (r,r); beta, alpha, stop test
+template <int MODE, bool MATS>
+__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+    k_pipe_y_tma(Mat A, Vecs V, Ctl *c, Work *wk)
+{
+    if (c->status != ST_RUNNING)
+        return;
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ Shm<3> sh;
+    shm_init<3, MODE>(sh);
+    const double alpha = c->alpha, omega = c->omega;
+    const double nalpha = -alpha, nomega = -omega;
+    DotSet<3, MODE> D;
+    D.init();
+    // stage slots: 0 q, 1 y, 2 p, 3 x, 4 t, 5 r0
+    const double *const src[6] = {V.q, V.y, V.p, V.x, V.t, V.r0};
+    tile_loop<6, MATS>(A, src, 6, c, dsm, [&](const TilePipe<6, MATS> &P, int k, int tile, int warp, int lane) {
+        const int sl = tile * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const bool act = sl < A.nslices && i < A.n;
+        const int o = warp * 32 + lane;
+        double rn = 0.0, wn = 0.0, r0i = 0.0;
+        if (sl < A.nslices) {
+            const double vi = P.spmv(k, A, warp, lane, V.z);
+            const double q = P.vec(k, 0)[o], y = P.vec(k, 1)[o];
+            const double xn = __fma_rn(omega, q, __fma_rn(alpha, P.vec(k, 2)[o], P.vec(k, 3)[o]));
+            rn = __fma_rn(nomega, y, q);
+            wn = __fma_rn(nomega, __fma_rn(nalpha, vi, P.vec(k, 4)[o]), y);
+            r0i = P.vec(k, 5)[o];
+            if (act) {
+                V.x[i] = xn;
+                V.v[i] = vi;
+                V.r[i] = rn;
+                V.w[i] = wn;
+            }
+        }
+        D.add(sh, 0, r0i, rn, act);
+        D.add(sh, 1, r0i, wn, act);
+        D.add(sh, 2, rn, rn, act);
+    });
+    if (!finalize<3, MODE>(D, sh, wk))
+        return;
+    if (threadIdx.x == 0) {
+        double rho_new = sh.dv[0], rw = sh.dv[1], rr = sh.dv[2];
+        c->rho_new = rho_new;
+        c->rw = rw;
+        c->rr = rr;
+        c->phase = PH_ITER;
+        if (c->err) {
+            c->status = ST_TIMEOUT;
+        } else if (!fin(rho_new) || !fin(rw) || !fin(c->rs) || !fin(c->rz) || !fin(rr)) {
+            c->status = 3;
+        } else {
+            c->it += 1;
+            residual_step(c, rr);
+        }
+        set_cond(c);
+    }
 }
 
 }  // namespace pbcg
