@@ -245,6 +245,9 @@ def run_ours(args):
     ms_h, its_h_all = reduce(ms_h, its_h)
 
     # per-kernel durations with CUDA events around each launch (host-driven loop, same kernels and grid)
+    batched = None
+    if not args.no_batched:
+        batched = run_batched_leg(ctx, pbcg, torch, dev)
     x_d.zero_()
     _, prof_e = ctx.profile_solve(M, b_d, x_d, TOL, MAXIT, pbcg.PIPELINED, pbcg.EXACT)
     x_d.zero_()
@@ -328,6 +331,7 @@ def run_ours(args):
         "e2e": {"value": its_h_all / (ms_h * 1e-3), "unit": "iter/s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 8 * n + 8 * (res_h.iters + 1), "steps": steps_h},
         "clocks": clocks,
+        "batched": batched,
         "gpu_launches": launches_e,
     }
     print(json.dumps(line), flush=True)
@@ -335,6 +339,61 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=20000, mode=1):
+    """Config 4: nsys 2D convection-diffusion systems (side log-uniform 32..256,
+    Peclet U(1,100)) in one block-diagonal matrix, solved by one batched
+    p-BiCGStab call, against solving each system alone with pbcg_solve."""
+    import numpy as np
+    from paper_2404_13216_gb300 import inputs
+    B = inputs.batched_convdiff(nsys=nsys, seed=4)
+    b = inputs.rhs_ones(B.A)
+    M = ctx.upload_csr(B.A)
+    b_d = torch.from_numpy(b).to(dev)
+    x_d = torch.zeros(B.A.n, dtype=torch.float64, device=dev)
+    tols = np.full(nsys, tol)
+    # warm-up, then timed batched solve
+    ctx.solve_batched(M, B.sys_row_ptr, b_d, x_d, tols, maxit, pbcg.PIPELINED, mode)
+    stream = torch.cuda.current_stream(dev)
+    x_d.zero_()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = ctx.solve_batched(M, B.sys_row_ptr, b_d, x_d, tols, maxit, pbcg.PIPELINED, mode)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_b = e0.elapsed_time(e1) * 1e-3
+    # one at a time: each block uploaded beforehand, then 512 solves back to back
+    singles = []
+    for k in range(nsys):
+        S = inputs.convdiff2d(int(B.sides[k]), float(B.peclet[k]))
+        r0, r1 = int(B.sys_row_ptr[k]), int(B.sys_row_ptr[k + 1])
+        singles.append((ctx.upload_csr(S), b_d[r0:r1], torch.zeros(r1 - r0, dtype=torch.float64, device=dev)))
+    for Ms, bs, xs in singles[:4]:
+        ctx.solve(Ms, bs, xs, tol, maxit, pbcg.PIPELINED, mode)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    single_res = []
+    for Ms, bs, xs in singles:
+        xs.zero_()
+        single_res.append(ctx.solve(Ms, bs, xs, tol, maxit, pbcg.PIPELINED, mode))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_s = e0.elapsed_time(e1) * 1e-3
+    same_iters = all(r.iters == s.iters for r, s in zip(res, single_res))
+    for Ms, _, _ in singles:
+        Ms.free()
+    M.free()
+    its = np.array([r.iters for r in res])
+    return {"nsys": nsys, "rows": int(B.A.n), "nnz": int(B.A.nnz), "dots": "exact" if mode else "plain",
+            "tol": tol, "solves_per_s": nsys / t_b, "seconds": t_b,
+            "one_at_a_time_solves_per_s": nsys / t_s, "one_at_a_time_seconds": t_s,
+            "speedup": t_s / t_b, "converged": int(sum(r.status == 0 for r in res)),
+            "one_at_a_time_converged": int(sum(r.status == 0 for r in single_res)),
+            "max_true_relres": float(max(r.relres_true for r in res)),
+            "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+            "identical_iterations_to_single_solves": bool(same_iters)}
 
 
 def source_sha() -> str:
@@ -375,6 +434,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched leg")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)

@@ -20,7 +20,7 @@
 #include <vector>
 
 #include "../../include/pbcg.h"
-#include "kernels.cuh"
+#include "batched.cuh"
 
 using namespace pbcg;
 
@@ -61,6 +61,19 @@ struct pbcg_mat {
     double *va;            // [padded]
     int *perm;             // [n] solver row p holds caller row perm[p]; NULL when rows keep their order
     bool narrow;           // every 256-row tile spans at most MCAP SELL entries (staged in shared memory)
+    std::vector<int32_t> h_rp, h_ci;   // host copy of the CSR (for per-batch layouts)
+    std::vector<double> h_va;
+    struct BatchLayout *bl;            // tile-aligned layout of the last batched solve, or NULL
+};
+
+// a block-diagonal matrix laid out with every system padded to whole 256-row tiles
+struct BatchLayout {
+    std::vector<int32_t> key;          // the sys_row_ptr it was built for
+    int nsys = 0, n_int = 0, nslices = 0, ntiles = 0;
+    int *sl_off = nullptr, *rlen = nullptr, *ci = nullptr;
+    double *va = nullptr;
+    int *map = nullptr;                // [n_int] caller row of each internal row, -1 for padding
+    int *tile_sys = nullptr, *sys_t0 = nullptr;
 };
 
 struct pbcg_ctx {
@@ -76,6 +89,28 @@ struct pbcg_ctx {
     bool have_hist = false;
     Ctl *h_ctl = nullptr;              // pinned mirror of the control block
     std::map<const void *, int> occ;   // resident CTAs per SM of each kernel
+    // batched solves
+    struct {
+        long long n_cap = 0;
+        int nsys_cap = 0, ntiles_cap = 0;
+        long long hist_cap = 0;
+        double *vec[13] = {};
+        Ctl *ctl = nullptr;
+        GAcc *acc = nullptr;
+        double *part = nullptr;
+        unsigned *done = nullptr;
+        int *flag = nullptr;
+        double *hist = nullptr;
+        double *io = nullptr;          // caller-order staging of b and x
+        long long io_cap = 0;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        const void *g_layout = nullptr;
+        int g_alg = -1, g_mode = -1;
+        std::vector<Ctl> last;         // per-system control blocks of the last batched solve
+        int hist_stride = 0;
+    } b;
+    bool last_batched = false;
 };
 
 namespace {
@@ -112,8 +147,23 @@ Mat mat_of(const pbcg_mat *m)
     return A;
 }
 
+void layout_release(BatchLayout *L)
+{
+    if (!L)
+        return;
+    cudaFree(L->sl_off);
+    cudaFree(L->rlen);
+    cudaFree(L->ci);
+    cudaFree(L->va);
+    cudaFree(L->map);
+    cudaFree(L->tile_sys);
+    cudaFree(L->sys_t0);
+    delete L;
+}
+
 void mat_release(pbcg_mat *m)
 {
+    layout_release(m->bl);
     cudaFree(m->sl_off);
     cudaFree(m->rlen);
     cudaFree(m->ci);
@@ -688,6 +738,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     CK(cudaMemcpyAsync(ctx->hist.data(), ws.hist, sizeof(double) * hl, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->have_hist = true;
+    ctx->last_batched = false;
     if (out) {
         out->iters = fin_ctl.it;
         out->status = fin_ctl.status;
@@ -699,6 +750,420 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     }
     return fin_ctl.status;
 }
+
+
+// ---------------------------------------------------------------------------
+// batched solves
+// ---------------------------------------------------------------------------
+int build_layout(pbcg_ctx *ctx, pbcg_mat *m, const std::vector<int32_t> &srp)
+{
+    if (m->bl && m->bl->key == srp)
+        return 0;
+    layout_release(m->bl);
+    m->bl = nullptr;
+    const int nsys = (int)srp.size() - 1;
+    std::vector<int> ib(nsys + 1, 0), t0(nsys + 1, 0);
+    for (int k = 0; k < nsys; k++) {
+        long long ns = srp[k + 1] - srp[k];
+        long long np = (ns + TILE_ROWS - 1) / TILE_ROWS * TILE_ROWS;
+        if ((long long)ib[k] + np > INT32_MAX / 2)
+            return fail(ctx, PBCG_ERR_INVALID, "batched layout too large");
+        ib[k + 1] = ib[k] + (int)np;
+        t0[k + 1] = t0[k] + (int)(np / TILE_ROWS);
+    }
+    const int n_int = ib[nsys], ntiles = t0[nsys], ns = n_int / 32;
+    std::vector<int> map(n_int, -1), tile_sys(ntiles), len(n_int, 0);
+    for (int k = 0; k < nsys; k++) {
+        for (int i = srp[k]; i < srp[k + 1]; i++) {
+            int p = ib[k] + (i - srp[k]);
+            map[p] = i;
+            len[p] = m->h_rp[i + 1] - m->h_rp[i];
+            for (int e = m->h_rp[i]; e < m->h_rp[i + 1]; e++) {
+                int j = m->h_ci[e];
+                if (j < srp[k] || j >= srp[k + 1])
+                    return fail(ctx, PBCG_ERR_INVALID, "row %d has column %d outside its system %d", i, j, k);
+            }
+        }
+        for (int t = t0[k]; t < t0[k + 1]; t++)
+            tile_sys[t] = k;
+    }
+    std::vector<int> sl_off((size_t)ns + 1 + SLOFF_STAGE, 0);
+    long long off = 0;
+    for (int sl = 0; sl < ns; sl++) {
+        int w = 0;
+        for (int l = 0; l < 32; l++)
+            w = std::max(w, len[sl * 32 + l]);
+        sl_off[sl] = (int)off;
+        off += 32ll * w;
+        if (off > INT32_MAX)
+            return fail(ctx, PBCG_ERR_INVALID, "padded matrix exceeds 2^31 entries");
+    }
+    for (size_t q = ns; q < sl_off.size(); q++)
+        sl_off[q] = (int)off;
+    std::vector<int> ci((size_t)std::max<long long>(off, 1), 0);
+    std::vector<double> va((size_t)std::max<long long>(off, 1), 0.0);
+    for (int k = 0; k < nsys; k++) {
+        for (int i = srp[k]; i < srp[k + 1]; i++) {
+            int p = ib[k] + (i - srp[k]);
+            long long base = sl_off[p / 32] + (p % 32);
+            int j0 = m->h_rp[i];
+            for (int e = 0; e < len[p]; e++) {
+                ci[(size_t)(base + 32ll * e)] = ib[k] + (m->h_ci[j0 + e] - srp[k]);
+                va[(size_t)(base + 32ll * e)] = m->h_va[j0 + e];
+            }
+        }
+    }
+    BatchLayout *L = new BatchLayout();
+    L->key = srp;
+    L->nsys = nsys;
+    L->n_int = n_int;
+    L->nslices = ns;
+    L->ntiles = ntiles;
+    cudaError_t e = cudaMalloc(&L->sl_off, sizeof(int) * sl_off.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L->rlen, sizeof(int) * (size_t)n_int);
+    if (e == cudaSuccess) e = cudaMalloc(&L->ci, sizeof(int) * ci.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L->va, sizeof(double) * va.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L->map, sizeof(int) * (size_t)n_int);
+    if (e == cudaSuccess) e = cudaMalloc(&L->tile_sys, sizeof(int) * (size_t)ntiles);
+    if (e == cudaSuccess) e = cudaMalloc(&L->sys_t0, sizeof(int) * (size_t)(nsys + 1));
+    if (e == cudaSuccess) e = cudaMemcpy(L->sl_off, sl_off.data(), sizeof(int) * sl_off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->rlen, len.data(), sizeof(int) * (size_t)n_int, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->ci, ci.data(), sizeof(int) * ci.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->va, va.data(), sizeof(double) * va.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->map, map.data(), sizeof(int) * (size_t)n_int, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->tile_sys, tile_sys.data(), sizeof(int) * (size_t)ntiles, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L->sys_t0, t0.data(), sizeof(int) * (size_t)(nsys + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        layout_release(L);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "batched layout: %s",
+                    cudaGetErrorString(e));
+    }
+    m->bl = L;
+    return 0;
+}
+
+#define BW ctx->b
+
+void free_batch_graph(pbcg_ctx *ctx)
+{
+    if (BW.exec)
+        cudaGraphExecDestroy(BW.exec);
+    if (BW.graph)
+        cudaGraphDestroy(BW.graph);
+    BW.exec = nullptr;
+    BW.graph = nullptr;
+    BW.g_layout = nullptr;
+}
+
+int ensure_batch_ws(pbcg_ctx *ctx, const BatchLayout *L, long long n_caller, int maxit)
+{
+    if (L->n_int > BW.n_cap) {
+        free_batch_graph(ctx);
+        for (auto &p : BW.vec) {
+            cudaFree(p);
+            p = nullptr;
+        }
+        BW.n_cap = 0;
+        for (auto &p : BW.vec) {
+            CK(cudaMalloc(&p, sizeof(double) * (size_t)L->n_int));
+            CK(cudaMemset(p, 0, sizeof(double) * (size_t)L->n_int));
+        }
+        BW.n_cap = L->n_int;
+    }
+    if (L->nsys > BW.nsys_cap) {
+        free_batch_graph(ctx);
+        cudaFree(BW.ctl);
+        cudaFree(BW.acc);
+        cudaFree(BW.done);
+        BW.ctl = nullptr;
+        BW.acc = nullptr;
+        BW.done = nullptr;
+        BW.nsys_cap = 0;
+        CK(cudaMalloc(&BW.ctl, sizeof(Ctl) * (size_t)L->nsys));
+        CK(cudaMalloc(&BW.acc, sizeof(GAcc) * MAXD * (size_t)L->nsys));
+        CK(cudaMalloc(&BW.done, sizeof(unsigned) * (size_t)L->nsys));
+        BW.nsys_cap = L->nsys;
+    }
+    if (L->ntiles > BW.ntiles_cap) {
+        free_batch_graph(ctx);
+        cudaFree(BW.part);
+        BW.part = nullptr;
+        BW.ntiles_cap = 0;
+        CK(cudaMalloc(&BW.part, sizeof(double) * MAXD * (size_t)L->ntiles));
+        BW.ntiles_cap = L->ntiles;
+    }
+    if (!BW.flag)
+        CK(cudaMalloc(&BW.flag, sizeof(int)));
+    long long hneed = (long long)L->nsys * (maxit + 1);
+    if (hneed > BW.hist_cap) {
+        cudaFree(BW.hist);
+        BW.hist = nullptr;
+        BW.hist_cap = 0;
+        CK(cudaMalloc(&BW.hist, sizeof(double) * (size_t)hneed));
+        BW.hist_cap = hneed;
+    }
+    if (n_caller > BW.io_cap) {
+        cudaFree(BW.io);
+        BW.io = nullptr;
+        BW.io_cap = 0;
+        CK(cudaMalloc(&BW.io, sizeof(double) * (size_t)n_caller));
+        BW.io_cap = n_caller;
+    }
+    return 0;
+}
+
+Mat layout_mat(const BatchLayout *L)
+{
+    Mat A;
+    A.n = L->n_int;
+    A.nslices = L->nslices;
+    A.sl_off = L->sl_off;
+    A.rlen = L->rlen;
+    A.ci = L->ci;
+    A.va = L->va;
+    return A;
+}
+
+Batch batch_of(pbcg_ctx *ctx, const BatchLayout *L)
+{
+    Batch B;
+    B.nsys = L->nsys;
+    B.ntiles = L->ntiles;
+    B.tile_sys = L->tile_sys;
+    B.sys_t0 = L->sys_t0;
+    B.ctl = BW.ctl;
+    B.acc = BW.acc;
+    B.part = BW.part;
+    B.done = BW.done;
+    B.flag = BW.flag;
+    return B;
+}
+
+Vecs batch_vecs(pbcg_ctx *ctx)
+{
+    Vecs V;
+    V.x = BW.vec[V_X];
+    V.b = BW.vec[V_B];
+    V.r0 = BW.vec[V_R0];
+    V.r = BW.vec[V_R];
+    V.w = BW.vec[V_W];
+    V.t = BW.vec[V_T];
+    V.p = BW.vec[V_P];
+    V.s = BW.vec[V_S];
+    V.z = BW.vec[V_Z];
+    V.v = BW.vec[V_V];
+    V.y = BW.vec[V_Y];
+    V.q = BW.vec[V_Q];
+    return V;
+}
+
+struct BKernel {
+    void *fn;
+    const char *name;
+};
+
+template <int MODE>
+std::vector<BKernel> batch_body(int alg)
+{
+    std::vector<BKernel> k;
+    k.push_back({(void *)k_batched<1, StepTrueRes<false>>, "b_true_res"});
+    if (alg == PBCG_ALG_PIPELINED) {
+        k.push_back({(void *)k_batched<MODE, StepPipeX>, MODE ? "b_pipe_x_exact" : "b_pipe_x_plain"});
+        k.push_back({(void *)k_batched<MODE, StepPipeY>, MODE ? "b_pipe_y_exact" : "b_pipe_y_plain"});
+    } else {
+        k.push_back({(void *)k_batched<MODE, StepBicgP>, "b_bicg_p"});
+        k.push_back({(void *)k_batched<MODE, StepBicgA>, MODE ? "b_bicg_a_exact" : "b_bicg_a_plain"});
+        k.push_back({(void *)k_batched<MODE, StepBicgB>, MODE ? "b_bicg_b_exact" : "b_bicg_b_plain"});
+        k.push_back({(void *)k_batched<MODE, StepBicgC>, MODE ? "b_bicg_c_exact" : "b_bicg_c_plain"});
+    }
+    return k;
+}
+
+int bgrid(pbcg_ctx *ctx, const void *fn, int ntiles)
+{
+    int g = grid_for(ctx, fn, (long long)ntiles * TILE_SLICES, 0);
+    return g;
+}
+
+int blaunch(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Batch &B)
+{
+    void *args[3] = {&A, &V, &B};
+    CK(cudaLaunchKernel(fn, dim3(bgrid(ctx, fn, B.ntiles)), dim3(THREADS), args, 0, ctx->stream));
+    return 0;
+}
+
+int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const int32_t *sys_row_ptr, const double *b,
+                       double *x, const double *tol, int32_t maxit, int alg, int mode, pbcg_result *out)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    pbcg_mat *m = const_cast<pbcg_mat *>(Ac);
+    if (!m || !ctx->mats.count(m))
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
+    if (nsys < 1 || !sys_row_ptr || !b || !x || !tol || !out)
+        return fail(ctx, PBCG_ERR_INVALID, "bad batched arguments");
+    if (maxit < 0)
+        return fail(ctx, PBCG_ERR_INVALID, "maxit must be >= 0");
+    if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", alg);
+    if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", mode);
+    CK(cudaSetDevice(ctx->device));
+    std::vector<int32_t> srp((size_t)nsys + 1);
+    std::vector<double> htol((size_t)nsys);
+    CK(cudaMemcpy(srp.data(), sys_row_ptr, sizeof(int32_t) * srp.size(), cudaMemcpyDefault));
+    CK(cudaMemcpy(htol.data(), tol, sizeof(double) * htol.size(), cudaMemcpyDefault));
+    if (srp[0] != 0 || srp[nsys] != m->n)
+        return fail(ctx, PBCG_ERR_INVALID, "sys_row_ptr must start at 0 and end at n");
+    for (int k = 0; k < nsys; k++) {
+        if (srp[k + 1] <= srp[k])
+            return fail(ctx, PBCG_ERR_INVALID, "sys_row_ptr must be strictly increasing (system %d)", k);
+        if (!(htol[k] > 0.0))
+            return fail(ctx, PBCG_ERR_INVALID, "tol[%d] must be > 0", k);
+    }
+    int rc = build_layout(ctx, m, srp);
+    if (rc)
+        return rc;
+    const BatchLayout *L = m->bl;
+    if ((rc = ensure_batch_ws(ctx, L, m->n, maxit)))
+        return rc;
+    Mat A = layout_mat(L);
+    Vecs V = batch_vecs(ctx);
+    Batch B = batch_of(ctx, L);
+    const int np = L->n_int;
+    // inputs into the padded order
+    {
+        CK(cudaMemcpyAsync(BW.io, b, sizeof(double) * (size_t)m->n, cudaMemcpyDefault, ctx->stream));
+        int *mp = L->map;
+        double *src = BW.io, *dst = V.b;
+        void *a1[4] = {(void *)&np, &mp, &src, &dst};
+        CK(cudaLaunchKernel((void *)k_bgather, dim3(ctx->num_sms * 4), dim3(256), a1, 0, ctx->stream));
+        CK(cudaMemcpyAsync(BW.io, x, sizeof(double) * (size_t)m->n, cudaMemcpyDefault, ctx->stream));
+        dst = V.x;
+        void *a2[4] = {(void *)&np, &mp, &src, &dst};
+        CK(cudaLaunchKernel((void *)k_bgather, dim3(ctx->num_sms * 4), dim3(256), a2, 0, ctx->stream));
+    }
+    std::vector<Ctl> hc((size_t)nsys);
+    for (int k = 0; k < nsys; k++) {
+        Ctl &c = hc[k];
+        memset(&c, 0, sizeof c);
+        c.maxit = maxit;
+        c.status = ST_RUNNING;
+        c.tol = htol[k];
+        c.target = htol[k];
+        c.alg = alg;
+        c.use_cond = 0;
+        c.hist = BW.hist + (size_t)k * (maxit + 1);
+        c.hist_cap = maxit + 1;
+        c.trueres = __builtin_nan("");
+    }
+    CK(cudaMemcpyAsync(BW.ctl, hc.data(), sizeof(Ctl) * hc.size(), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        std::vector<GAcc> ga((size_t)nsys * MAXD);
+        for (auto &g : ga) {
+            memset(&g, 0, sizeof g);
+            g.kmin = NDIG;
+            g.kmax = -1;
+        }
+        CK(cudaMemcpyAsync(BW.acc, ga.data(), sizeof(GAcc) * ga.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemsetAsync(BW.done, 0, sizeof(unsigned) * (size_t)nsys, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));   // ga, hc go out of scope
+    }
+    long long launches = 0;
+    if ((rc = blaunch(ctx, mode ? (void *)k_batched<1, StepSetup1> : (void *)k_batched<0, StepSetup1>, A, V, B)))
+        return rc;
+    launches++;
+    if (alg == PBCG_ALG_PIPELINED) {
+        if ((rc = blaunch(ctx, mode ? (void *)k_batched<1, StepSetup2> : (void *)k_batched<0, StepSetup2>, A, V, B)))
+            return rc;
+        if ((rc = blaunch(ctx, (void *)k_batched<0, StepSetup3>, A, V, B)))
+            return rc;
+        launches += 2;
+    }
+    // the loop: WHILE(some system running or awaiting its check) { true-res, passes, control }
+    std::vector<BKernel> body = mode ? batch_body<1>(alg) : batch_body<0>(alg);
+    if (!(BW.exec && BW.g_layout == (const void *)L && BW.g_alg == alg && BW.g_mode == mode)) {
+        free_batch_graph(ctx);
+        CK(cudaGraphCreate(&BW.graph, 0));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, BW.graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        CK(cudaGraphAddNode(&cnode, BW.graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t g = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t prev = nullptr;
+        for (auto &bk : body) {
+            void *args[3] = {&A, &V, &B};
+            cudaKernelNodeParams kp;
+            memset(&kp, 0, sizeof kp);
+            kp.func = bk.fn;
+            kp.gridDim = dim3(bgrid(ctx, bk.fn, B.ntiles));
+            kp.blockDim = dim3(THREADS);
+            kp.kernelParams = args;
+            cudaGraphNode_t node;
+            CK(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+            prev = node;
+        }
+        unsigned long long hv = (unsigned long long)h;
+        int one = 1;
+        void *cargs[3] = {&B, &hv, &one};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void *)k_batch_ctl;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1024);
+        kp.kernelParams = cargs;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        CK(cudaGraphInstantiate(&BW.exec, BW.graph, 0));
+        BW.g_layout = L;
+        BW.g_alg = alg;
+        BW.g_mode = mode;
+    }
+    CK(cudaGraphLaunch(BW.exec, ctx->stream));
+    // final true residual of every system, then results
+    if ((rc = blaunch(ctx, (void *)k_batched<1, StepTrueRes<true>>, A, V, B)))
+        return rc;
+    launches++;
+    BW.last.resize((size_t)nsys);
+    CK(cudaMemcpyAsync(BW.last.data(), BW.ctl, sizeof(Ctl) * (size_t)nsys, cudaMemcpyDeviceToHost, ctx->stream));
+    {
+        int *mp = L->map;
+        double *src = V.x, *dst = BW.io;
+        void *a3[4] = {(void *)&np, &mp, &src, &dst};
+        CK(cudaLaunchKernel((void *)k_bscatter, dim3(ctx->num_sms * 4), dim3(256), a3, 0, ctx->stream));
+        CK(cudaMemcpyAsync(x, BW.io, sizeof(double) * (size_t)m->n, cudaMemcpyDefault, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->last_batched = true;
+    BW.hist_stride = maxit + 1;
+    int maxit_it = 0, worst = 0;
+    for (int k = 0; k < nsys; k++)
+        maxit_it = std::max(maxit_it, BW.last[k].it);
+    launches += (long long)(maxit_it + 1) * (long long)(body.size() + 1);
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < nsys; k++) {
+        const Ctl &c = BW.last[k];
+        if (c.err)
+            return fail(ctx, PBCG_ERR_TIMEOUT, "a bounded device wait expired");
+        out[k].iters = c.it;
+        out[k].status = c.status;
+        out[k].relres_recursive = c.res;
+        out[k].relres_true = c.trueres;
+        out[k].seconds = secs;
+        out[k].launches = (int32_t)std::min<long long>(launches, INT32_MAX);
+        out[k].reserved = 0;
+        worst = std::max(worst, c.status);
+    }
+    return worst;
+}
+
+#undef BW
 
 }  // namespace
 
@@ -750,6 +1215,16 @@ void pbcg_destroy(pbcg_ctx *ctx)
         mat_release(m);
     ctx->mats.clear();
     free_ws(ctx->ws);
+    free_batch_graph(ctx);
+    for (auto &p : ctx->b.vec)
+        cudaFree(p);
+    cudaFree(ctx->b.ctl);
+    cudaFree(ctx->b.acc);
+    cudaFree(ctx->b.part);
+    cudaFree(ctx->b.done);
+    cudaFree(ctx->b.flag);
+    cudaFree(ctx->b.hist);
+    cudaFree(ctx->b.io);
     if (ctx->h_ctl)
         cudaFreeHost(ctx->h_ctl);
     if (ctx->own_stream)
@@ -798,6 +1273,10 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     m->sl_off = m->rlen = m->ci = m->perm = nullptr;
     m->va = nullptr;
     m->narrow = S.narrow;
+    m->bl = nullptr;
+    m->h_rp = std::move(hrp);
+    m->h_ci = std::move(hci);
+    m->h_va = std::move(hva);
     size_t P = (size_t)(S.padded ? S.padded : 1);
     cudaError_t e = cudaMalloc(&m->sl_off, sizeof(int) * S.sl_off.size());
     if (e == cudaSuccess)
@@ -879,6 +1358,18 @@ int pbcg_residual_history(pbcg_ctx *ctx, int32_t sys, double *out, int32_t cap, 
 {
     if (!ctx)
         return PBCG_ERR_INVALID;
+    if (ctx->last_batched) {
+        if (sys < 0 || sys >= (int32_t)ctx->b.last.size())
+            return fail(ctx, PBCG_ERR_INVALID, "no residual history for system %d", sys);
+        int32_t Lb = std::min(ctx->b.last[sys].it + 1, ctx->b.hist_stride);
+        if (len)
+            *len = Lb;
+        if (out && cap > 0) {
+            CK(cudaMemcpy(out, ctx->b.hist + (size_t)sys * ctx->b.hist_stride, sizeof(double) * (size_t)std::min(cap, Lb),
+                          cudaMemcpyDeviceToHost));
+        }
+        return 0;
+    }
     if (sys != 0 || !ctx->have_hist)
         return fail(ctx, PBCG_ERR_INVALID, "no residual history for system %d", sys);
     int32_t L = (int32_t)ctx->hist.size();
@@ -959,9 +1450,7 @@ int pbcg_spmv(pbcg_ctx *ctx, const pbcg_mat *m, const double *x, double *y)
 int pbcg_solve_batched(pbcg_ctx *ctx, const pbcg_mat *A, int32_t nsys, const int32_t *sys_row_ptr, const double *b,
                        double *x, const double *tol, int32_t maxit, int alg, int dot_mode, pbcg_result *out)
 {
-    (void)A; (void)nsys; (void)sys_row_ptr; (void)b; (void)x; (void)tol; (void)maxit; (void)alg; (void)dot_mode;
-    (void)out;
-    return fail(ctx, PBCG_ERR_INVALID, "batched solve not available in this build");
+    return solve_batched_impl(ctx, A, nsys, sys_row_ptr, b, x, tol, maxit, alg, dot_mode, out);
 }
 
 }  // extern "C"

@@ -1,0 +1,550 @@
+// batched.cuh -- many independent systems in one sweep per pass.
+//
+// The systems of a block-diagonal matrix are laid out one after another, each
+// padded to whole 256-row tiles, so every tile belongs to exactly one system.
+// A batched pass walks its CTA's tiles (tile blockIdx.x, + gridDim.x, ...),
+// skips tiles of systems that are not in the state the pass serves, and
+// computes the same row formulas as the single-system passes.  Dot terms are
+// accumulated while consecutive tiles of the CTA belong to the same system and
+// are flushed into that system's accumulators when the system changes.  The
+// CTA whose flush completes a system's tile count (an atomic counter per
+// system) rounds that system's dots and runs its scalar step, so every system
+// advances with its own alpha, beta, omega, residual, history, tolerance and
+// status -- bit for bit the arithmetic of a single solve of its block in
+// exact mode.
+#pragma once
+#include "kernels.cuh"
+
+namespace pbcg {
+
+struct Batch {
+    int nsys, ntiles;
+    const int *__restrict__ tile_sys;    // [ntiles] system of each tile
+    const int *__restrict__ sys_t0;      // [nsys + 1] first tile of each system
+    Ctl *ctl;                            // [nsys]
+    GAcc *acc;                           // [nsys * MAXD]
+    double *part;                        // [ntiles * MAXD] plain partial of the flush group starting at a tile
+    unsigned *done;                      // [nsys] tiles merged in the current pass
+    int *flag;                           // [1] loop condition scratch
+};
+
+// ---------------------------------------------------------------------------
+// generic batched pass
+// ---------------------------------------------------------------------------
+template <int ND, int MODE, class Step>
+__device__ __forceinline__ void b_flush(DotSet<ND, MODE> &D, Shm<ND> &sh, const Batch &B, int sys, int t_first,
+                                        int cnt, const Vecs &V)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (MODE == 1) {
+#pragma unroll
+        for (int d = 0; d < ND; d++) {
+            win_flush<ND>(D.win[d], sh.acc, d);
+            if (D.nf[d])
+                atomicOr(&sh.acc.nf[d], 1);
+        }
+    } else {
+        double tot[ND];
+        warp_sum_plain<ND>(D.s, tot);
+        if (lane == 0) {
+#pragma unroll
+            for (int d = 0; d < ND; d++)
+                sh.wpart[d][warp] = tot[d];
+        }
+    }
+    __syncthreads();
+    if (MODE == 1) {
+        cta_to_global<ND>(sh.acc, B.acc + (size_t)sys * MAXD);
+    } else if (threadIdx.x < ND) {
+        double v = sh.wpart[threadIdx.x][0];
+        for (int w = 1; w < WARPS; w++)
+            v = __dadd_rn(v, sh.wpart[threadIdx.x][w]);
+        B.part[(size_t)t_first * MAXD + threadIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned need = (unsigned)(B.sys_t0[sys + 1] - B.sys_t0[sys]);
+        const unsigned old = atomicAdd(&B.done[sys], (unsigned)cnt);
+        sh.last = (old + (unsigned)cnt == need);
+    }
+    __syncthreads();
+    if (sh.last) {
+        __threadfence();
+        GAcc *g = B.acc + (size_t)sys * MAXD;
+        if (MODE == 1) {
+            if (threadIdx.x < ND)
+                sh.dv[threadIdx.x] = gacc_round_reset(&g[threadIdx.x], sh.scratch[threadIdx.x]);
+        } else if (warp < ND) {
+            // partials of the system's flush groups, in tile order (non-first tiles hold +0)
+            const int t0 = B.sys_t0[sys], t1 = B.sys_t0[sys + 1];
+            double v = 0.0;
+            for (int t = t0 + lane; t < t1; t += 32)
+                v = __dadd_rn(v, __ldcg(B.part + (size_t)t * MAXD + warp));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0)
+                sh.dv[warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            B.done[sys] = 0u;
+            Step::fin(B.ctl + sys, sh.dv, V);
+        }
+    }
+    __syncthreads();
+    // fresh CTA accumulator for the next group
+    if (MODE == 1)
+        cta_acc_init<ND>(sh.acc);
+    if (threadIdx.x == 0)
+        sh.last = 0;
+    __syncthreads();
+}
+
+template <int MODE, class Step>
+__global__ void __launch_bounds__(THREADS) k_batched(Mat A, Vecs V, Batch B)
+{
+    constexpr int ND = Step::ND;
+    __shared__ Shm<ND> sh;
+    shm_init<ND, MODE>(sh);
+    __syncthreads();
+    DotSet<ND, MODE> D;
+    D.init();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int cur = -1, t_first = -1, cnt = 0;
+    bool run = false;
+    typename Step::Scal S;
+    for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+        const int sys = B.tile_sys[t];
+        if (sys != cur) {
+            if (cur >= 0 && cnt > 0) {
+                b_flush<ND, MODE, Step>(D, sh, B, cur, t_first, cnt, V);
+                D.init();
+            }
+            cur = sys;
+            t_first = t;
+            cnt = 0;
+            const Ctl *c = B.ctl + sys;
+            run = Step::wants(c->status);
+            if (run)
+                S = Step::load(c);
+        }
+        if (!run)
+            continue;
+        if (MODE == 0 && threadIdx.x < ND)
+            B.part[(size_t)t * MAXD + threadIdx.x] = 0.0;
+        const int sl = t * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const bool act = sl < A.nslices && i < A.n;
+        double a[ND], b[ND];
+        Step::row(A, V, S, sl, lane, i, act, a, b);
+#pragma unroll
+        for (int d = 0; d < ND; d++)
+            D.add(sh, d, a[d], b[d], act);
+        cnt++;
+    }
+    if (cur >= 0 && cnt > 0)
+        b_flush<ND, MODE, Step>(D, sh, B, cur, t_first, cnt, V);
+}
+
+// ---------------------------------------------------------------------------
+// steps.  Row formulas are those of the single-system passes.
+// ---------------------------------------------------------------------------
+struct NoScal {
+};
+
+// S1: r0 = b - A x0, r = r0 (p = r0 for BiCGStab); dots (b,b), (r0,r0)
+struct StepSetup1 {
+    static constexpr int ND = 2;
+    struct Scal {
+        bool bicg;
+    };
+    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *c) { return Scal{c->alg == ALG_BICGSTAB}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        double bi = 0.0, r0i = 0.0;
+        if (sl < A.nslices) {
+            RowRef R = row_ref(A, sl, lane);
+            double ax = spmv_row(A, R, V.x);
+            if (act) {
+                bi = V.b[i];
+                r0i = __dsub_rn(bi, ax);
+                V.r0[i] = r0i;
+                V.r[i] = r0i;
+                if (S.bicg)
+                    V.p[i] = r0i;
+            }
+        }
+        a[0] = bi, b[0] = bi, a[1] = r0i, b[1] = r0i;
+    }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        c->bb = dv[0];
+        c->rho = dv[1];
+        if (c->alg == ALG_BICGSTAB)
+            setup_scalar(c, dv[0], dv[1], 0.0);
+    }
+};
+
+// S2 (p-BiCGStab): w0 = A r0; dot (r0, w0); setup scalars
+struct StepSetup2 {
+    static constexpr int ND = 1;
+    using Scal = NoScal;
+    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *) { return Scal{}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        double r0i = 0.0, wi = 0.0;
+        if (sl < A.nslices) {
+            RowRef R = row_ref(A, sl, lane);
+            wi = spmv_row(A, R, V.r0);
+            if (act) {
+                r0i = V.r0[i];
+                V.w[i] = wi;
+            } else {
+                wi = 0.0;
+            }
+        }
+        a[0] = r0i, b[0] = wi;
+    }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &) { setup_scalar(c, c->bb, c->rho, dv[0]); }
+};
+
+// S3 (p-BiCGStab): t0 = A w0 (no dots)
+struct StepSetup3 {
+    static constexpr int ND = 1;
+    using Scal = NoScal;
+    static __device__ bool wants(int st) { return st == ST_RUNNING || st == ST_CANDIDATE; }
+    static __device__ Scal load(const Ctl *) { return Scal{}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        if (sl < A.nslices) {
+            RowRef R = row_ref(A, sl, lane);
+            double ti = spmv_row(A, R, V.w);
+            if (act)
+                V.t[i] = ti;
+        }
+        a[0] = 0.0, b[0] = 0.0;
+    }
+    static __device__ void fin(Ctl *, const double *, const Vecs &) {}
+};
+
+// X(i) (p-BiCGStab)
+struct StepPipeX {
+    static constexpr int ND = 4;
+    struct Scal {
+        double alpha, beta, omega;
+        bool first;
+    };
+    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->beta, c->omega, c->it == 0}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        double q = 0.0, y = 0.0, r0i = 0.0, si = 0.0, zi = 0.0;
+        if (sl < A.nslices) {
+            double ti = 0.0;
+            if (!S.first) {
+                RowRef R = row_ref(A, sl, lane);
+                ti = spmv_row(A, R, V.w);
+            }
+            if (act) {
+                const double ri = V.r[i], wi = V.w[i];
+                r0i = V.r0[i];
+                double pi;
+                if (S.first) {
+                    ti = V.t[i];
+                    pi = ri;
+                    si = wi;
+                    zi = ti;
+                } else {
+                    const double nomega = -S.omega;
+                    const double sold = V.s[i], zold = V.z[i];
+                    pi = __fma_rn(S.beta, __fma_rn(nomega, sold, V.p[i]), ri);
+                    si = __fma_rn(S.beta, __fma_rn(nomega, zold, sold), wi);
+                    zi = __fma_rn(S.beta, __fma_rn(nomega, V.v[i], zold), ti);
+                    V.t[i] = ti;
+                }
+                q = __fma_rn(-S.alpha, si, ri);
+                y = __fma_rn(-S.alpha, zi, wi);
+                V.p[i] = pi;
+                V.s[i] = si;
+                V.z[i] = zi;
+                V.q[i] = q;
+                V.y[i] = y;
+            }
+        }
+        a[0] = q, b[0] = y, a[1] = y, b[1] = y, a[2] = r0i, b[2] = si, a[3] = r0i, b[3] = zi;
+    }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        double qy = dv[0], yy = dv[1];
+        c->qy = qy;
+        c->yy = yy;
+        c->rs = dv[2];
+        c->rz = dv[3];
+        if (!pbcg::fin(qy) || !pbcg::fin(yy))
+            c->status = 3;
+        else
+            c->omega = (yy == 0.0) ? 0.0 : __ddiv_rn(qy, yy);
+    }
+};
+
+// Y(i) (p-BiCGStab)
+struct StepPipeY {
+    static constexpr int ND = 3;
+    struct Scal {
+        double alpha, omega;
+    };
+    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->omega}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        double rn = 0.0, wn = 0.0, r0i = 0.0;
+        if (sl < A.nslices) {
+            RowRef R = row_ref(A, sl, lane);
+            const double vi = spmv_row(A, R, V.z);
+            if (act) {
+                const double q = V.q[i], y = V.y[i];
+                V.x[i] = __fma_rn(S.omega, q, __fma_rn(S.alpha, V.p[i], V.x[i]));
+                rn = __fma_rn(-S.omega, y, q);
+                wn = __fma_rn(-S.omega, __fma_rn(-S.alpha, vi, V.t[i]), y);
+                r0i = V.r0[i];
+                V.v[i] = vi;
+                V.r[i] = rn;
+                V.w[i] = wn;
+            }
+        }
+        a[0] = r0i, b[0] = rn, a[1] = r0i, b[1] = wn, a[2] = rn, b[2] = rn;
+    }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        double rho_new = dv[0], rw = dv[1], rr = dv[2];
+        c->rho_new = rho_new;
+        c->rw = rw;
+        c->rr = rr;
+        c->phase = PH_ITER;
+        if (!pbcg::fin(rho_new) || !pbcg::fin(rw) || !pbcg::fin(c->rs) || !pbcg::fin(c->rz) || !pbcg::fin(rr)) {
+            c->status = 3;
+        } else {
+            c->it += 1;
+            residual_step(c, rr);
+        }
+    }
+};
+
+// P(i), i >= 1 (BiCGStab): p = fma(beta, fma(-omega, s, p), r)
+struct StepBicgP {
+    static constexpr int ND = 1;
+    struct Scal {
+        double beta, omega;
+        bool first;
+    };
+    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *c) { return Scal{c->beta, c->omega, c->it == 0}; }
+    static __device__ void row(const Mat &, const Vecs &V, const Scal &S, int, int, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        if (act && !S.first)
+            V.p[i] = __fma_rn(S.beta, __fma_rn(-S.omega, V.s[i], V.p[i]), V.r[i]);
+        a[0] = 0.0, b[0] = 0.0;
+    }
+    static __device__ void fin(Ctl *, const double *, const Vecs &) {}
+};
+
+// A(i) (BiCGStab): s = A p; (r0, s); alpha
+struct StepBicgA {
+    static constexpr int ND = 1;
+    using Scal = NoScal;
+    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *) { return Scal{}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        double si = 0.0, r0i = 0.0;
+        if (sl < A.nslices) {
+            RowRef R = row_ref(A, sl, lane);
+            si = spmv_row(A, R, V.p);
+            if (act) {
+                V.s[i] = si;
+                r0i = V.r0[i];
+            } else {
+                si = 0.0;
+            }
+        }
+        a[0] = r0i, b[0] = si;
+    }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        double rs = dv[0];
+        c->rs = rs;
+        if (!pbcg::fin(rs)) {
+            c->status = 3;
+        } else {
+            double al = __ddiv_rn(c->rho, rs);
+            if (!pbcg::fin(al))
+                c->status = 2;
+            else
+                c->alpha = al;
+        }
+    }
+};
+
+// B(i) (BiCGStab): y = A q, q_j = fma(-alpha, s_j, r_j) in the gather; (q,y), (y,y); omega
+struct StepBicgB {
+    static constexpr int ND = 2;
+    struct Scal {
+        double alpha;
+    };
+    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *c) { return Scal{c->alpha}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        double qi = 0.0, yi = 0.0;
+        if (sl < A.nslices) {
+            RowRef R = row_ref(A, sl, lane);
+            yi = spmv_row_axpy(A, R, -S.alpha, V.s, V.r);
+            if (act) {
+                qi = __fma_rn(-S.alpha, V.s[i], V.r[i]);
+                V.y[i] = yi;
+            } else {
+                yi = 0.0;
+            }
+        }
+        a[0] = qi, b[0] = yi, a[1] = yi, b[1] = yi;
+    }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        double qy = dv[0], yy = dv[1];
+        c->qy = qy;
+        c->yy = yy;
+        if (!pbcg::fin(qy) || !pbcg::fin(yy))
+            c->status = 3;
+        else
+            c->omega = (yy == 0.0) ? 0.0 : __ddiv_rn(qy, yy);
+    }
+};
+
+// C(i) (BiCGStab): x, r; (r0,r), (r,r); beta, stop test
+struct StepBicgC {
+    static constexpr int ND = 2;
+    struct Scal {
+        double alpha, omega;
+    };
+    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->omega}; }
+    static __device__ void row(const Mat &, const Vecs &V, const Scal &S, int, int, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        double rn = 0.0, r0i = 0.0;
+        if (act) {
+            const double q = __fma_rn(-S.alpha, V.s[i], V.r[i]);
+            V.x[i] = __fma_rn(S.omega, q, __fma_rn(S.alpha, V.p[i], V.x[i]));
+            rn = __fma_rn(-S.omega, V.y[i], q);
+            V.r[i] = rn;
+            r0i = V.r0[i];
+        }
+        a[0] = r0i, b[0] = rn, a[1] = rn, b[1] = rn;
+    }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        double rho_new = dv[0], rr = dv[1];
+        c->rho_new = rho_new;
+        c->rr = rr;
+        c->phase = PH_ITER;
+        if (!pbcg::fin(rho_new) || !pbcg::fin(rr)) {
+            c->status = 3;
+        } else {
+            c->it += 1;
+            residual_step(c, rr);
+        }
+    }
+};
+
+// true residual of candidate systems (resolve) or of every system (report)
+template <bool REPORT>
+struct StepTrueRes {
+    static constexpr int ND = 2;
+    using Scal = NoScal;
+    static __device__ bool wants(int st) { return REPORT || st == ST_CANDIDATE; }
+    static __device__ Scal load(const Ctl *) { return Scal{}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        double ri = 0.0, bi = 0.0;
+        if (sl < A.nslices) {
+            RowRef R = row_ref(A, sl, lane);
+            double ax = spmv_row(A, R, V.x);
+            if (act) {
+                bi = V.b[i];
+                ri = __dsub_rn(bi, ax);
+            }
+        }
+        a[0] = ri, b[0] = ri, a[1] = bi, b[1] = bi;
+    }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        double nb = __dsqrt_rn(dv[1]);
+        if (nb == 0.0)
+            nb = 1.0;
+        double tr = __ddiv_rn(__dsqrt_rn(dv[0]), nb);
+        c->trueres = tr;
+        c->bbx = dv[1];
+        if (c->status == ST_CANDIDATE) {
+            if (tr <= c->tol) {
+                c->status = 0;
+            } else {
+                c->target = __dmul_rn(c->tol, __ddiv_rn(c->tol, tr));
+                c->status = ST_RUNNING;
+                post_stop(c);
+            }
+        }
+    }
+};
+
+// loop condition of a batched solve: some system still running or awaiting its true-residual check
+__global__ void k_batch_ctl(Batch B, unsigned long long handle, int use_cond)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0)
+        any = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < B.nsys; s += blockDim.x) {
+        int st = B.ctl[s].status;
+        if (st == ST_RUNNING || st == ST_CANDIDATE)
+            any = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        B.flag[0] = any;
+        if (use_cond)
+            cudaGraphSetConditional((cudaGraphConditionalHandle)handle, any ? 1u : 0u);
+    }
+}
+
+// batched vectors <-> caller order: dst[p] = src[map[p]] (0 for padding rows, map < 0)
+__global__ void k_bgather(int np, const int *__restrict__ map, const double *__restrict__ src, double *dst)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        int c = map[p];
+        dst[p] = c >= 0 ? src[c] : 0.0;
+    }
+}
+
+__global__ void k_bscatter(int np, const int *__restrict__ map, const double *__restrict__ src, double *dst)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        int c = map[p];
+        if (c >= 0)
+            dst[c] = src[p];
+    }
+}
+
+}  // namespace pbcg

@@ -11,10 +11,11 @@
 //   1. decode both doubles into (sign, 53-bit integer mantissa, exponent) with
 //      bit operations;
 //   2. form the exact 106-bit mantissa product with four 32x32->64 multiplies;
-//   3. add it, as a signed 384-bit two's-complement number, into a per-lane
+//   3. add it, as a signed 256-bit two's-complement number, into a per-lane
 //      register window whose bit position (the anchor) is shared by the warp;
-//      a product that falls outside the window goes straight to the CTA's
-//      accumulator with shared-memory atomics;
+//      a term above the window re-anchors it (after flushing), and terms below
+//      it are deposited together into a temporary window anchored at their own
+//      maximum, which is flushed at once;
 //   4. at the end of a pass the warp sums its windows (butterfly with carries)
 //      and adds the total into the CTA accumulator: 32-bit digits held in
 //      int64 (carry-save), bit 0 of digit 0 weighing 2^-2148;
@@ -33,9 +34,9 @@
 namespace pbcg {
 
 constexpr int NDIG = 136;        // 32-bit digits; 136*32 = 4352 bits cover 2^-2148 .. 2^2048 plus carries
-constexpr int WIN_WORDS = 12;    // per-lane window: 384-bit two's complement
-constexpr int WIN_SMAX = 248;    // largest left shift of a 106-bit product inside the window (7 words + 24 bits)
-constexpr int WIN_ROOM = 64;     // bits of room left above the first product when anchoring
+constexpr int WIN_WORDS = 8;     // per-lane window: 256-bit two's complement
+constexpr int WIN_SMAX = 120;    // largest left shift of a 106-bit product inside the window (3 words + 24 bits)
+constexpr int WIN_ROOM = 32;     // bits of room left above the warp maximum when anchoring
 
 // ---------------------------------------------------------------------------
 // decode and exact product
@@ -146,11 +147,12 @@ __device__ __noinline__ void cta_add_product(CtaAcc<ND> &c, int d, const Prod &p
 }
 
 // ---------------------------------------------------------------------------
-// per-lane window: 384-bit two's complement, LSB at bit `anchor` (warp-uniform)
+// per-lane window: 256-bit two's complement, LSB at bit `anchor` (warp-uniform)
 //
-// Headroom: a product shifted by at most WIN_SMAX bits is below 2^354; a lane
-// adds fewer than 2^22 of them and a warp sums 32 lanes, so the total stays
-// below 2^381 and the sign bit (383) is never reached.
+// Headroom: a product shifted by at most WIN_SMAX bits is below 2^226; a lane
+// adds fewer than 2^16 of them between flushes (one per tile of its CTA) and
+// a warp sums 32 lanes, so totals stay below 2^247 and the sign bit (255) is
+// never reached.
 // ---------------------------------------------------------------------------
 struct Win {
     uint32_t a[WIN_WORDS];
@@ -165,57 +167,71 @@ __device__ __forceinline__ void win_init(Win &w)
     w.anchor = -1;
 }
 
-__device__ __forceinline__ void add384(uint32_t (&a)[WIN_WORDS], const uint32_t (&x)[WIN_WORDS])
+__device__ __forceinline__ void add256(uint32_t (&a)[WIN_WORDS], const uint32_t (&x)[WIN_WORDS])
 {
-    asm("add.cc.u32 %0, %0, %12;\n\t"
-        "addc.cc.u32 %1, %1, %13;\n\t"
-        "addc.cc.u32 %2, %2, %14;\n\t"
-        "addc.cc.u32 %3, %3, %15;\n\t"
-        "addc.cc.u32 %4, %4, %16;\n\t"
-        "addc.cc.u32 %5, %5, %17;\n\t"
-        "addc.cc.u32 %6, %6, %18;\n\t"
-        "addc.cc.u32 %7, %7, %19;\n\t"
-        "addc.cc.u32 %8, %8, %20;\n\t"
-        "addc.cc.u32 %9, %9, %21;\n\t"
-        "addc.cc.u32 %10, %10, %22;\n\t"
-        "addc.u32 %11, %11, %23;"
-        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
-          "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11])
-        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]), "r"(x[8]),
-          "r"(x[9]), "r"(x[10]), "r"(x[11]));
+    asm("add.cc.u32 %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32 %7, %7, %15;"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7])
+        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]));
 }
 
-// the flush itself; leaves the window zero (anchor unchanged)
+// add the shifted product s (sh = 32 q + r already applied for r) at word offset q (0..3)
+__device__ __forceinline__ void win_place(uint32_t (&acc)[WIN_WORDS], const Shifted &s, uint32_t q)
+{
+    const bool q1 = q & 1u, q2 = q & 2u;
+    // word t of the shifted product: u[t-q] for t-q in 0..4, the sign word above, 0 below
+    const uint32_t v0 = q1 ? 0u : s.u0, v1 = q1 ? s.u0 : s.u1, v2 = q1 ? s.u1 : s.u2;
+    const uint32_t v3 = q1 ? s.u2 : s.u3, v4 = q1 ? s.u3 : s.u4, v5 = q1 ? s.u4 : s.sgn;
+    uint32_t x[WIN_WORDS];
+    x[0] = q2 ? 0u : v0;
+    x[1] = q2 ? 0u : v1;
+    x[2] = q2 ? v0 : v2;
+    x[3] = q2 ? v1 : v3;
+    x[4] = q2 ? v2 : v4;
+    x[5] = q2 ? v3 : v5;
+    x[6] = q2 ? v4 : s.sgn;
+    x[7] = q2 ? v5 : s.sgn;
+    add256(acc, x);
+}
+
+// Sum the windows of the warp (all lanes call) and add the total, anchored at
+// bit `anchor`, into the CTA digits; leaves the window zero.
 template <int ND>
-__device__ __forceinline__ void win_flush_reset(Win &w, CtaAcc<ND> &c, int d)
+__device__ __forceinline__ void win_flush_words(uint32_t (&a)[WIN_WORDS], int anchor, CtaAcc<ND> &c, int d)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         uint32_t y[WIN_WORDS];
 #pragma unroll
         for (int t = 0; t < WIN_WORDS; t++)
-            y[t] = __shfl_xor_sync(0xffffffffu, w.a[t], o);
-        add384(w.a, y);
+            y[t] = __shfl_xor_sync(0xffffffffu, a[t], o);
+        add256(a, y);
     }
-    int k = w.anchor >> 5;
-    uint32_t r = (uint32_t)(w.anchor & 31);
-    uint32_t sg = (uint32_t)((int)w.a[WIN_WORDS - 1] >> 31);
-    int lane = threadIdx.x & 31;
+    const int k = anchor >> 5;
+    const uint32_t r = (uint32_t)(anchor & 31);
+    const uint32_t sg = (uint32_t)((int)a[WIN_WORDS - 1] >> 31);
+    const int lane = threadIdx.x & 31;
     // lane t (t <= WIN_WORDS) takes word t of (total << r)
     uint32_t lo = 0u, hi = 0u;
 #pragma unroll
     for (int t = 0; t < WIN_WORDS; t++) {
         if (lane == t)
-            hi = w.a[t];
+            hi = a[t];
         if (lane == t + 1)
-            lo = w.a[t];
+            lo = a[t];
     }
     if (lane == WIN_WORDS)
         hi = sg;
-    uint32_t mine = (lane == 0) ? (hi << r) : __funnelshift_l(lo, hi, r);
+    const uint32_t mine = (lane == 0) ? (hi << r) : __funnelshift_l(lo, hi, r);
     if (lane <= WIN_WORDS) {
-        unsigned long long v = (lane < WIN_WORDS) ? (unsigned long long)mine
-                                                  : (unsigned long long)(long long)(int)mine;
+        const unsigned long long v = (lane < WIN_WORDS) ? (unsigned long long)mine
+                                                        : (unsigned long long)(long long)(int)mine;
         if (v != 0ull)
             atomicAdd(&c.dig[d][k + lane], v);
     }
@@ -223,9 +239,14 @@ __device__ __forceinline__ void win_flush_reset(Win &w, CtaAcc<ND> &c, int d)
         cta_touch(c, d, k, k + WIN_WORDS);
 #pragma unroll
     for (int t = 0; t < WIN_WORDS; t++)
-        w.a[t] = 0u;
+        a[t] = 0u;
 }
 
+template <int ND>
+__device__ __forceinline__ void win_flush_reset(Win &w, CtaAcc<ND> &c, int d)
+{
+    win_flush_words<ND>(w.a, w.anchor, c, d);
+}
 
 // Sum the warp's windows and add the total into the CTA digits.  All lanes call.
 template <int ND>
@@ -233,7 +254,121 @@ __device__ __forceinline__ void win_flush(Win &w, CtaAcc<ND> &c, int d)
 {
     if (w.anchor < 0)
         return;                                           // warp-uniform: nothing deposited
-    win_flush_reset<ND>(w, c, d);
+    win_flush_words<ND>(w.a, w.anchor, c, d);
+}
+
+// ---------------------------------------------------------------------------
+// operand-level interface: decode each double once, deposit products of
+// decoded operands (a value shared by several dots is decoded only once)
+// ---------------------------------------------------------------------------
+constexpr int E_ZERO = -100000;    // exponent sentinel of a zero operand: its products drop out
+
+struct Dec {
+    uint32_t lo, hi;     // 53-bit integer mantissa: hi holds the top 21 bits (implicit bit included)
+    int e;               // max(biased exponent, 1), or E_ZERO for +-0
+    uint32_t s;          // sign bit
+    bool nf;             // Inf or NaN
+};
+
+__device__ __forceinline__ Dec decode(double a)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    uint32_t h = (uint32_t)(b >> 32);
+    Dec d;
+    d.lo = (uint32_t)b;
+    uint32_t ef = (h >> 20) & 0x7ffu;
+    d.nf = ef == 0x7ffu;
+    d.hi = (h & 0xfffffu) | (ef ? 0x100000u : 0u);
+    d.s = h >> 31;
+    d.e = ((d.hi | d.lo) == 0u) ? E_ZERO : (ef ? (int)ef : 1);
+    return d;
+}
+
+// exact product of two decoded operands (|a*b| words, sign, LSB offset)
+template <bool SQUARE>
+__device__ __forceinline__ Prod dec_product(const Dec &a, const Dec &b)
+{
+    Prod p;
+    unsigned long long p0 = (unsigned long long)a.lo * b.lo;
+    unsigned long long m = (unsigned long long)a.hi * b.lo + (p0 >> 32);
+    m = (unsigned long long)a.lo * b.hi + m;
+    unsigned long long h = (unsigned long long)a.hi * b.hi + (m >> 32);
+    p.w0 = (uint32_t)p0;
+    p.w1 = (uint32_t)m;
+    p.w2 = (uint32_t)h;
+    p.w3 = (uint32_t)(h >> 32);
+    p.neg = SQUARE ? 0u : (a.s ^ b.s);
+    p.off = a.e + b.e - 2;
+    p.nonfinite = false;
+    return p;
+}
+
+// positive product words shifted left by r (0..31) (squares need no sign handling)
+__device__ __forceinline__ Shifted unsigned_shift(const Prod &p, uint32_t r)
+{
+    Shifted s;
+    s.sgn = 0u;
+    s.u0 = p.w0 << r;
+    s.u1 = __funnelshift_l(p.w0, p.w1, r);
+    s.u2 = __funnelshift_l(p.w1, p.w2, r);
+    s.u3 = __funnelshift_l(p.w2, p.w3, r);
+    s.u4 = __funnelshift_l(p.w3, 0u, r);
+    return s;
+}
+
+template <bool SQUARE>
+__device__ __forceinline__ void place_product(uint32_t (&acc)[WIN_WORDS], const Prod &p, int sh)
+{
+    Shifted s = SQUARE ? unsigned_shift(p, (uint32_t)(sh & 31)) : signed_shift(p, (uint32_t)(sh & 31));
+    win_place(acc, s, (uint32_t)sh >> 5);
+}
+
+// Products below the warp's window: deposit them together into a temporary
+// window anchored at the largest of them and flush it at once; repeat while
+// some are still lower than that window.  All lanes call.
+template <int ND, bool SQUARE>
+__device__ __noinline__ void win_low(CtaAcc<ND> &c, int d, Prod p, int rem)
+{
+    while (__any_sync(0xffffffffu, rem >= 0)) {
+        const int m = __reduce_max_sync(0xffffffffu, rem);
+        const int anc = max(m - WIN_SMAX, 0);
+        uint32_t t[WIN_WORDS];
+#pragma unroll
+        for (int q = 0; q < WIN_WORDS; q++)
+            t[q] = 0u;
+        const bool go = rem >= 0 && rem >= anc;
+        if (go) {
+            place_product<SQUARE>(t, p, rem - anc);
+            rem = -1;
+        }
+        win_flush_words<ND>(t, anc, c, d);
+    }
+}
+
+// Deposit a*b for decoded operands.  All 32 lanes of the warp call together.
+// The anchor is kept warp-uniform: a vote finds lanes whose product would not
+// fit the top of the window; only then is the window flushed and re-anchored
+// at the warp maximum.  Products below the window take win_low.
+template <int ND, bool SQUARE>
+__device__ __forceinline__ void win_add(Win &w, CtaAcc<ND> &c, int d, const Dec &a, const Dec &b, bool act,
+                                        bool &nf)
+{
+    nf |= act && (a.nf || b.nf);
+    const int off = act ? a.e + b.e - 2 : -1;        // negative for zero operands and inactive lanes
+    const bool high = off >= 0 && (w.anchor < 0 || off - w.anchor > WIN_SMAX);
+    if (__any_sync(0xffffffffu, high)) {             // warp-uniform and rare
+        int m = __reduce_max_sync(0xffffffffu, off);
+        if (w.anchor >= 0)
+            win_flush_reset<ND>(w, c, d);
+        w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
+    }
+    const int sh = off - w.anchor;                   // <= WIN_SMAX for every lane with off >= 0
+    const Prod p = dec_product<SQUARE>(a, b);
+    const bool low = off >= 0 && sh < 0;
+    if (off >= 0 && sh >= 0)
+        place_product<SQUARE>(w.a, p, sh);
+    if (__any_sync(0xffffffffu, low))
+        win_low<ND, SQUARE>(c, d, p, low ? off : -1);
 }
 
 // Deposit a*b.  Must be called by all 32 lanes of the warp together (the
@@ -242,50 +377,7 @@ template <int ND>
 __device__ __forceinline__ void win_deposit(Win &w, CtaAcc<ND> &c, int d, double a, double b, bool active,
                                             bool &nf)
 {
-    Prod p = exact_product(a, b);
-    if (!active) {
-        p.off = -1;
-        p.nonfinite = false;
-    }
-    nf |= p.nonfinite;
-    // warp-uniform anchoring: set on the first nonzero term; when a term would
-    // overflow the top of the window, the window is flushed to the CTA digits
-    // and re-anchored on the current terms
-    int m = __reduce_max_sync(0xffffffffu, p.off);
-    if (m >= 0 && (w.anchor < 0 || m - w.anchor > WIN_SMAX)) {
-        if (w.anchor >= 0)
-            win_flush_reset<ND>(w, c, d);
-        w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
-    }
-    if (p.off < 0)
-        return;
-    int sh = p.off - w.anchor;
-    if (w.anchor >= 0 && sh >= 0 && sh <= WIN_SMAX) {
-        Shifted s = signed_shift(p, (uint32_t)(sh & 31));
-        uint32_t q = (uint32_t)sh >> 5;                   // 0..7 whole words
-        bool q1 = q & 1u, q2 = q & 2u, q4 = q & 4u;
-        // word t of the shifted product: u[t-q] inside 0..4, the sign word above, 0 below
-        uint32_t v0 = q1 ? 0u : s.u0, v1 = q1 ? s.u0 : s.u1, v2 = q1 ? s.u1 : s.u2;
-        uint32_t v3 = q1 ? s.u2 : s.u3, v4 = q1 ? s.u3 : s.u4, v5 = q1 ? s.u4 : s.sgn;
-        uint32_t w0 = q2 ? 0u : v0, w1 = q2 ? 0u : v1, w2 = q2 ? v0 : v2, w3 = q2 ? v1 : v3;
-        uint32_t w4 = q2 ? v2 : v4, w5 = q2 ? v3 : v5, w6 = q2 ? v4 : s.sgn, w7 = q2 ? v5 : s.sgn;
-        uint32_t x[WIN_WORDS];
-        x[0] = q4 ? 0u : w0;
-        x[1] = q4 ? 0u : w1;
-        x[2] = q4 ? 0u : w2;
-        x[3] = q4 ? 0u : w3;
-        x[4] = q4 ? w0 : w4;
-        x[5] = q4 ? w1 : w5;
-        x[6] = q4 ? w2 : w6;
-        x[7] = q4 ? w3 : w7;
-        x[8] = q4 ? w4 : s.sgn;
-        x[9] = q4 ? w5 : s.sgn;
-        x[10] = q4 ? w6 : s.sgn;
-        x[11] = q4 ? w7 : s.sgn;
-        add384(w.a, x);
-    } else {
-        cta_add_product(c, d, p);
-    }
+    win_add<ND, false>(w, c, d, decode(a), decode(b), active, nf);
 }
 
 // ---------------------------------------------------------------------------

@@ -219,6 +219,17 @@ struct DotSet {
             s[d] = __fma_rn(a, b, s[d]);
         }
     }
+    // same, with operands already decoded (exact mode); SQUARE when a == b
+    template <bool SQUARE>
+    __device__ __forceinline__ void add2(Shm<ND> &sh, int d, double a, double b, const Dec &da, const Dec &db,
+                                         bool act)
+    {
+        if (MODE == 1) {
+            win_add<ND, SQUARE>(win[d], sh.acc, d, da, db, act, nf[d]);
+        } else if (act) {
+            s[d] = __fma_rn(a, b, s[d]);
+        }
+    }
 };
 
 template <int ND, int MODE>
@@ -977,10 +988,11 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
                 V.y[i] = y;
             }
         }
-        D.add(sh, 0, q, y, act);
-        D.add(sh, 1, y, y, act);
-        D.add(sh, 2, r0i, si, act);
-        D.add(sh, 3, r0i, zi, act);
+        const Dec dq = decode(q), dy = decode(y), dr = decode(r0i), ds = decode(si), dz = decode(zi);
+        D.template add2<false>(sh, 0, q, y, dq, dy, act);
+        D.template add2<true>(sh, 1, y, y, dy, dy, act);
+        D.template add2<false>(sh, 2, r0i, si, dr, ds, act);
+        D.template add2<false>(sh, 3, r0i, zi, dr, dz, act);
     });
     if (!finalize<4, MODE>(D, sh, wk))
         return;
@@ -1038,9 +1050,10 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
                 V.w[i] = wn;
             }
         }
-        D.add(sh, 0, r0i, rn, act);
-        D.add(sh, 1, r0i, wn, act);
-        D.add(sh, 2, rn, rn, act);
+        const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
+        D.template add2<false>(sh, 0, r0i, rn, dr0, dr, act);
+        D.template add2<false>(sh, 1, r0i, wn, dr0, dw, act);
+        D.template add2<true>(sh, 2, rn, rn, dr, dr, act);
     });
     if (!finalize<3, MODE>(D, sh, wk))
         return;
