@@ -105,6 +105,18 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(dist, ms: float, its: int, device):
+    """Whole-job time is the slowest rank's (max), work is summed over ranks."""
+    if dist is None:
+        return ms, its
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([its], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def oracle_sample(A, b, nthreads: int, mode: int, iters: int):
     """Time `iters` iterations of the CPU oracle's p-BiCGStab (setup excluded by
     differencing a 1-iteration run)."""
@@ -232,13 +244,7 @@ def run_ours(args):
     ms_h, its_h, _, res_h, _ = timed(pbcg.EXACT, max(1, args.steps // 2), host=True)
 
     def reduce(ms, its):
-        if dist is None:
-            return ms, its
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([its], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        return float(t.item()), int(c.item())
+        return reduce_over_ranks(dist, ms, its, dev)
 
     ms_e, its_e_all = reduce(ms_e, its_e)
     ms_p, its_p_all = reduce(ms_p, its_p)
@@ -341,7 +347,7 @@ def run_ours(args):
     return 0
 
 
-def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=20000, mode=1):
+def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, mode=1):
     """Config 4: nsys 2D convection-diffusion systems (side log-uniform 32..256,
     Peclet U(1,100)) in one block-diagonal matrix, solved by one batched
     p-BiCGStab call, against solving each system alone with pbcg_solve."""
@@ -392,7 +398,8 @@ def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=20000, mod
             "speedup": t_s / t_b, "converged": int(sum(r.status == 0 for r in res)),
             "one_at_a_time_converged": int(sum(r.status == 0 for r in single_res)),
             "max_true_relres": float(max(r.relres_true for r in res)),
-            "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+            "iters_mean": float(its.mean()), "iters_max": int(its.max()), "maxit": maxit,
+            "status_counts": {str(k): int(sum(r.status == k for r in res)) for k in range(4)},
             "identical_iterations_to_single_solves": bool(same_iters)}
 
 

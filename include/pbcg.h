@@ -52,7 +52,7 @@ enum {
     PBCG_ERR_TIMEOUT = -4   /* a bounded device wait expired */
 };
 
-enum { PBCG_ALG_BICGSTAB = 0, PBCG_ALG_PIPELINED = 1 };
+enum { PBCG_ALG_BICGSTAB = 0, PBCG_ALG_PIPELINED = 1, PBCG_ALG_PIPELINED_RR = 2 };
 enum { PBCG_DOT_PLAIN = 0, PBCG_DOT_EXACT = 1 };
 
 typedef struct {
@@ -94,7 +94,9 @@ int pbcg_mat_free(pbcg_ctx *ctx, pbcg_mat *mat);
 
 /*
  * Solve A x = b from x (in: x_0, out: the last iterate, written for every
- * status).  b and x hold n doubles each.  alg: PBCG_ALG_*; dot_mode: PBCG_DOT_*.
+ * status).  b and x hold n doubles each.  alg: PBCG_ALG_* (PIPELINED_RR is
+ * Algorithm 2 with residual replacement, see pbcg_set_option); dot_mode:
+ * PBCG_DOT_*.
  *
  * Algorithm 2 (p-BiCGStab), with omega the scalar (q,y)/(y,y) and w the
  * vector A r (the paper uses the letter w for both):
@@ -144,6 +146,22 @@ int pbcg_solve_batched(pbcg_ctx *ctx, const pbcg_mat *A, int32_t nsys, const int
  * the full length (iters + 1).  INVALID if no such history exists.
  */
 int pbcg_residual_history(pbcg_ctx *ctx, int32_t sys, double *out, int32_t cap, int32_t *len);
+
+/*
+ * Context options.
+ *   PBCG_OPT_RR_PERIOD: k >= 1, the period of residual replacement used by
+ *     PBCG_ALG_PIPELINED_RR (default 50).  Section 2 names residual replacement
+ *     (resetting r, w, s and z to their true values every k iterations) as the
+ *     stabiliser that exact dot products are proposed to replace, and the
+ *     experiments compare against it (p-BiCGStabRR).  The paper gives no
+ *     schedule beyond "every k iterations"; this library replaces at the start
+ *     of every iteration i > 0 with i mod k == 0: r = b - A x, w = A r, p by
+ *     its recurrence from the new r, s = A p, z = A s (t = A w follows in the
+ *     same iteration); the scalars are kept.
+ * Returns 0, or INVALID for an unknown option or value.
+ */
+enum { PBCG_OPT_RR_PERIOD = 1 };
+int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value);
 
 /*
  * Standalone kernels of the solver, for checks and measurement.

@@ -50,6 +50,11 @@
  *       rho_new = 0, give BREAKDOWN.  A non-finite dot gives NONFINITE.
  *   R8  Exact dot: exact zero gives +0; ties to even; subnormal results exact
  *       at 2^-1074; overflow gives +-inf; any non-finite operand gives NaN.
+ *   R9  Residual replacement (the p-BiCGStabRR of Section 2, period k): at the
+ *       start of every iteration i > 0 with i mod k = 0, r_i := b - A x_i,
+ *       w_i := A r_i, p_i by its recurrence (with the new r_i),
+ *       s_i := A p_i, z_i := A s_i, t_i := A w_i; the scalars are kept.  The
+ *       paper gives no more detail; k = 0 is plain Algorithm 2.
  */
 #include <math.h>
 #include <pthread.h>
@@ -333,6 +338,7 @@ typedef struct {
     const int32_t *rp, *ci;
     const double *v;
     int mode, nthreads;
+    int32_t rr_period;
 } orc_sys;
 
 static double dotm(const orc_sys *S, const double *a, const double *b)
@@ -550,6 +556,17 @@ static int solve_pipelined(const orc_sys *S, const double *b, double *x, double 
             memcpy(p, r, (size_t)n * 8);
             memcpy(s, w, (size_t)n * 8);
             memcpy(z, t, (size_t)n * 8);
+        } else if (S->rr_period > 0 && it % S->rr_period == 0) {
+            /* R9: residual replacement -- true r, w, s, z (and t = A w) */
+            orc_spmv(n, S->rp, S->ci, S->v, x, tmp);
+            for (int32_t i = 0; i < n; i++)
+                r[i] = b[i] - tmp[i];
+            orc_spmv(n, S->rp, S->ci, S->v, r, w);
+            for (int32_t i = 0; i < n; i++)
+                p[i] = fma(beta, fma(-omega, s[i], p[i]), r[i]);
+            orc_spmv(n, S->rp, S->ci, S->v, p, s);
+            orc_spmv(n, S->rp, S->ci, S->v, s, z);
+            orc_spmv(n, S->rp, S->ci, S->v, w, t);
         } else {
             /* p_i, s_i, z_i with beta_{i-1}, omega_{i-1} */
             for (int32_t i = 0; i < n; i++) {
@@ -627,11 +644,28 @@ done:
  * or ORC_INVALID.  hist receives res_0 .. res_iters (up to hist_cap entries);
  * trace (optional) receives alpha_i, omega_i, beta_i, res_{i+1} per iteration.
  */
+int orc_solve_rr(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, const double *b, double *x,
+                 double tol, int32_t maxit, int alg, int mode, int nthreads, int32_t rr_period, double *hist,
+                 int32_t hist_cap, int32_t *hist_len, double *trace, int32_t trace_cap, int32_t *iters,
+                 double *relres_rec, double *relres_true);
+
 int orc_solve(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, const double *b, double *x,
               double tol, int32_t maxit, int alg, int mode, int nthreads, double *hist, int32_t hist_cap,
               int32_t *hist_len, double *trace, int32_t trace_cap, int32_t *iters, double *relres_rec,
               double *relres_true)
 {
+    return orc_solve_rr(n, rp, ci, v, b, x, tol, maxit, alg, mode, nthreads, 0, hist, hist_cap, hist_len, trace,
+                        trace_cap, iters, relres_rec, relres_true);
+}
+
+/* orc_solve with residual replacement every rr_period iterations (Algorithm 2 only; 0 = none) */
+int orc_solve_rr(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, const double *b, double *x,
+                 double tol, int32_t maxit, int alg, int mode, int nthreads, int32_t rr_period, double *hist,
+                 int32_t hist_cap, int32_t *hist_len, double *trace, int32_t trace_cap, int32_t *iters,
+                 double *relres_rec, double *relres_true)
+{
+    if (rr_period < 0 || (rr_period > 0 && alg != ORC_PIPELINED))
+        return ORC_INVALID;
     if (n < 1 || !rp || !ci || !v || !b || !x || !(tol > 0.0) || maxit < 0)
         return ORC_INVALID;
     if (alg != ORC_BICGSTAB && alg != ORC_PIPELINED)
@@ -646,7 +680,7 @@ int orc_solve(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, 
     for (int32_t k = 0; k < rp[n]; k++)
         if (ci[k] < 0 || ci[k] >= n)
             return ORC_INVALID;
-    orc_sys S = { n, rp, ci, v, mode, nthreads };
+    orc_sys S = { n, rp, ci, v, mode, nthreads, rr_period };
     orc_log L = { hist, hist_cap, 0, trace, trace_cap };
     double rel = NAN;
     int32_t it = 0;

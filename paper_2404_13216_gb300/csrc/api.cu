@@ -60,6 +60,8 @@ struct pbcg_mat {
     int *ci;               // [padded], solver-order column indices
     double *va;            // [padded]
     int *perm;             // [n] solver row p holds caller row perm[p]; NULL when rows keep their order
+    int *lci;              // [padded] entry indices into a tile's staged gather blocks
+    int *tblk;             // [ntiles * GMAX] gather blocks of each tile (-1: none / too many)
     bool narrow;           // every 256-row tile spans at most MCAP SELL entries (staged in shared memory)
     std::vector<int32_t> h_rp, h_ci;   // host copy of the CSR (for per-batch layouts)
     std::vector<double> h_va;
@@ -89,6 +91,7 @@ struct pbcg_ctx {
     bool have_hist = false;
     Ctl *h_ctl = nullptr;              // pinned mirror of the control block
     std::map<const void *, int> occ;   // resident CTAs per SM of each kernel
+    int rr_period = 50;                // residual replacement period of PBCG_ALG_PIPELINED_RR
     // batched solves
     struct {
         long long n_cap = 0;
@@ -144,6 +147,8 @@ Mat mat_of(const pbcg_mat *m)
     A.rlen = m->rlen;
     A.ci = m->ci;
     A.va = m->va;
+    A.lci = m->lci;
+    A.tblk = m->tblk;
     return A;
 }
 
@@ -169,6 +174,8 @@ void mat_release(pbcg_mat *m)
     cudaFree(m->ci);
     cudaFree(m->va);
     cudaFree(m->perm);
+    cudaFree(m->lci);
+    cudaFree(m->tblk);
     delete m;
 }
 
@@ -301,7 +308,7 @@ struct Sell {
     long long padded = 0;
     bool permuted = false;
     bool narrow = true;
-    std::vector<int> sl_off, rlen, ci, perm;
+    std::vector<int> sl_off, rlen, ci, perm, lci, tblk;
     std::vector<double> va;
 };
 
@@ -382,6 +389,38 @@ bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val,
     }
     if (!S.permuted)
         S.perm.clear();
+    // per tile: the 256-row blocks of the gathered vector its columns fall in
+    // (at most GMAX, else -1), and each entry's index into those staged blocks
+    const int ntl = (ns + TILE_SLICES - 1) / TILE_SLICES;
+    S.tblk.assign((size_t)ntl * GMAX, -1);
+    S.lci.assign(S.ci.size(), 0);
+    for (int t = 0; t < ntl; t++) {
+        const int sa = t * TILE_SLICES, sb = std::min(ns, sa + TILE_SLICES);
+        std::vector<int> blocks;
+        bool ok = true;
+        for (long long e = S.sl_off[sa]; e < S.sl_off[sb] && ok; e++) {
+            int sl = sa + (int)((e - S.sl_off[sa]) / 32), p = 0;
+            (void)sl;
+            int b = S.ci[(size_t)e] / TILE_ROWS;
+            if (std::find(blocks.begin(), blocks.end(), b) == blocks.end()) {
+                if ((int)blocks.size() == GMAX)
+                    ok = false;
+                else
+                    blocks.push_back(b);
+            }
+            (void)p;
+        }
+        if (!ok || blocks.empty())
+            continue;
+        std::sort(blocks.begin(), blocks.end());
+        for (size_t g = 0; g < blocks.size(); g++)
+            S.tblk[(size_t)t * GMAX + g] = blocks[g];
+        for (long long e = S.sl_off[sa]; e < S.sl_off[sb]; e++) {
+            int b = S.ci[(size_t)e] / TILE_ROWS;
+            int g = (int)(std::lower_bound(blocks.begin(), blocks.end(), b) - blocks.begin());
+            S.lci[(size_t)e] = g * TILE_ROWS + S.ci[(size_t)e] % TILE_ROWS;
+        }
+    }
     return true;
 }
 
@@ -432,7 +471,13 @@ struct BodyKernel {
 std::vector<BodyKernel> body_kernels(int alg, int mode, bool narrow)
 {
     std::vector<BodyKernel> k;
-    if (alg == PBCG_ALG_PIPELINED) {
+    if (alg == PBCG_ALG_PIPELINED_RR) {
+        k.push_back({(void *)k_rr1, "rr1", 0, 0});
+        k.push_back({(void *)k_rr2, "rr2", 0, 0});
+        k.push_back({(void *)k_rr3, "rr3", 0, 0});
+        k.push_back({(void *)k_rr4, "rr4", 0, 0});
+    }
+    if (alg == PBCG_ALG_PIPELINED || alg == PBCG_ALG_PIPELINED_RR) {
         size_t sx = narrow ? stage_bytes<7, true>() : stage_bytes<7, false>();
         size_t sy = narrow ? stage_bytes<6, true>() : stage_bytes<6, false>();
         k.push_back({mode ? Kern<1>::pipe_x_tma(narrow) : Kern<0>::pipe_x_tma(narrow),
@@ -621,7 +666,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         return fail(ctx, PBCG_ERR_INVALID, "tol must be > 0");
     if (maxit < 0)
         return fail(ctx, PBCG_ERR_INVALID, "maxit must be >= 0");
-    if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED)
+    if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED && alg != PBCG_ALG_PIPELINED_RR)
         return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", alg);
     if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
         return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", mode);
@@ -640,7 +685,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     h.status = ST_RUNNING;
     h.tol = tol;
     h.target = tol;
-    h.alg = alg;
+    h.alg = (alg == PBCG_ALG_BICGSTAB) ? ALG_BICGSTAB : ALG_PIPELINED;
+    h.rr_period = (alg == PBCG_ALG_PIPELINED_RR) ? ctx->rr_period : 0;
     h.use_cond = 0;
     h.hist = ws.hist;
     h.hist_cap = maxit + 1;
@@ -651,7 +697,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     Mat A = mat_of(m);
     Vecs V = vecs_of(ws);
     Launcher L{ctx, prof, 0, {}};
-    if (alg == PBCG_ALG_PIPELINED) {
+    if (alg != PBCG_ALG_BICGSTAB) {
         rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), A, V, ws.ctl, ws.wk, 1);
         if (!rc)
             rc = L.go("setup2", mode ? Kern<1>::setup2() : Kern<0>::setup2(), A, V, ws.ctl, ws.wk, 1);
@@ -921,6 +967,8 @@ Mat layout_mat(const BatchLayout *L)
     A.rlen = L->rlen;
     A.ci = L->ci;
     A.va = L->va;
+    A.lci = nullptr;
+    A.tblk = nullptr;
     return A;
 }
 
@@ -967,7 +1015,13 @@ std::vector<BKernel> batch_body(int alg)
 {
     std::vector<BKernel> k;
     k.push_back({(void *)k_batched<1, StepTrueRes<false>>, "b_true_res"});
-    if (alg == PBCG_ALG_PIPELINED) {
+    if (alg == PBCG_ALG_PIPELINED_RR) {
+        k.push_back({(void *)k_batched<0, StepRR<1>>, "b_rr1"});
+        k.push_back({(void *)k_batched<0, StepRR<2>>, "b_rr2"});
+        k.push_back({(void *)k_batched<0, StepRR<3>>, "b_rr3"});
+        k.push_back({(void *)k_batched<0, StepRR<4>>, "b_rr4"});
+    }
+    if (alg == PBCG_ALG_PIPELINED || alg == PBCG_ALG_PIPELINED_RR) {
         k.push_back({(void *)k_batched<MODE, StepPipeX>, MODE ? "b_pipe_x_exact" : "b_pipe_x_plain"});
         k.push_back({(void *)k_batched<MODE, StepPipeY>, MODE ? "b_pipe_y_exact" : "b_pipe_y_plain"});
     } else {
@@ -1005,7 +1059,7 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         return fail(ctx, PBCG_ERR_INVALID, "bad batched arguments");
     if (maxit < 0)
         return fail(ctx, PBCG_ERR_INVALID, "maxit must be >= 0");
-    if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED)
+    if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED && alg != PBCG_ALG_PIPELINED_RR)
         return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", alg);
     if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
         return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", mode);
@@ -1052,7 +1106,8 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         c.status = ST_RUNNING;
         c.tol = htol[k];
         c.target = htol[k];
-        c.alg = alg;
+        c.alg = (alg == PBCG_ALG_BICGSTAB) ? ALG_BICGSTAB : ALG_PIPELINED;
+        c.rr_period = (alg == PBCG_ALG_PIPELINED_RR) ? ctx->rr_period : 0;
         c.use_cond = 0;
         c.hist = BW.hist + (size_t)k * (maxit + 1);
         c.hist_cap = maxit + 1;
@@ -1074,7 +1129,7 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
     if ((rc = blaunch(ctx, mode ? (void *)k_batched<1, StepSetup1> : (void *)k_batched<0, StepSetup1>, A, V, B)))
         return rc;
     launches++;
-    if (alg == PBCG_ALG_PIPELINED) {
+    if (alg != PBCG_ALG_BICGSTAB) {
         if ((rc = blaunch(ctx, mode ? (void *)k_batched<1, StepSetup2> : (void *)k_batched<0, StepSetup2>, A, V, B)))
             return rc;
         if ((rc = blaunch(ctx, (void *)k_batched<0, StepSetup3>, A, V, B)))
@@ -1270,7 +1325,7 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     m->nnz = nnz;
     m->nslices = S.nslices;
     m->padded = S.padded;
-    m->sl_off = m->rlen = m->ci = m->perm = nullptr;
+    m->sl_off = m->rlen = m->ci = m->perm = m->lci = m->tblk = nullptr;
     m->va = nullptr;
     m->narrow = S.narrow;
     m->bl = nullptr;
@@ -1287,6 +1342,14 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
         e = cudaMalloc(&m->va, sizeof(double) * P);
     if (e == cudaSuccess && S.permuted)
         e = cudaMalloc(&m->perm, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->lci, sizeof(int) * P);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->tblk, sizeof(int) * S.tblk.size());
+    if (e == cudaSuccess && S.padded)
+        e = cudaMemcpy(m->lci, S.lci.data(), sizeof(int) * (size_t)S.padded, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->tblk, S.tblk.data(), sizeof(int) * S.tblk.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(m->sl_off, S.sl_off.data(), sizeof(int) * S.sl_off.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -1352,6 +1415,19 @@ int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double
             launches[i] = prof.count[i];
     }
     return rc;
+}
+
+int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (option == PBCG_OPT_RR_PERIOD) {
+        if (value < 1 || value > INT32_MAX)
+            return fail(ctx, PBCG_ERR_INVALID, "residual replacement period must be >= 1");
+        ctx->rr_period = (int)value;
+        return 0;
+    }
+    return fail(ctx, PBCG_ERR_INVALID, "unknown option %d", option);
 }
 
 int pbcg_residual_history(pbcg_ctx *ctx, int32_t sys, double *out, int32_t cap, int32_t *len)

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(THREADS) k_batched(Mat A, Vecs V, Batch B)
             t_first = t;
             cnt = 0;
             const Ctl *c = B.ctl + sys;
-            run = Step::wants(c->status);
+            run = Step::wants(c);
             if (run)
                 S = Step::load(c);
         }
@@ -160,7 +160,7 @@ struct StepSetup1 {
     struct Scal {
         bool bicg;
     };
-    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *c) { return Scal{c->alg == ALG_BICGSTAB}; }
     static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
@@ -193,7 +193,7 @@ struct StepSetup1 {
 struct StepSetup2 {
     static constexpr int ND = 1;
     using Scal = NoScal;
-    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *) { return Scal{}; }
     static __device__ void row(const Mat &A, const Vecs &V, const Scal &, int sl, int lane, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
@@ -218,7 +218,7 @@ struct StepSetup2 {
 struct StepSetup3 {
     static constexpr int ND = 1;
     using Scal = NoScal;
-    static __device__ bool wants(int st) { return st == ST_RUNNING || st == ST_CANDIDATE; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING || st == ST_CANDIDATE; }
     static __device__ Scal load(const Ctl *) { return Scal{}; }
     static __device__ void row(const Mat &A, const Vecs &V, const Scal &, int sl, int lane, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
@@ -239,10 +239,10 @@ struct StepPipeX {
     static constexpr int ND = 4;
     struct Scal {
         double alpha, beta, omega;
-        bool first;
+        bool first, rr;
     };
-    static __device__ bool wants(int st) { return st == ST_RUNNING; }
-    static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->beta, c->omega, c->it == 0}; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
+    static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->beta, c->omega, c->it == 0, rr_now(c)}; }
     static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
     {
@@ -262,6 +262,11 @@ struct StepPipeX {
                     pi = ri;
                     si = wi;
                     zi = ti;
+                } else if (S.rr) {
+                    pi = V.p[i];
+                    si = V.s[i];
+                    zi = V.z[i];
+                    V.t[i] = ti;
                 } else {
                     const double nomega = -S.omega;
                     const double sold = V.s[i], zold = V.z[i];
@@ -301,7 +306,7 @@ struct StepPipeY {
     struct Scal {
         double alpha, omega;
     };
-    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->omega}; }
     static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
@@ -346,7 +351,7 @@ struct StepBicgP {
         double beta, omega;
         bool first;
     };
-    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *c) { return Scal{c->beta, c->omega, c->it == 0}; }
     static __device__ void row(const Mat &, const Vecs &V, const Scal &S, int, int, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
@@ -362,7 +367,7 @@ struct StepBicgP {
 struct StepBicgA {
     static constexpr int ND = 1;
     using Scal = NoScal;
-    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *) { return Scal{}; }
     static __device__ void row(const Mat &A, const Vecs &V, const Scal &, int sl, int lane, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
@@ -402,7 +407,7 @@ struct StepBicgB {
     struct Scal {
         double alpha;
     };
-    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *c) { return Scal{c->alpha}; }
     static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
@@ -438,7 +443,7 @@ struct StepBicgC {
     struct Scal {
         double alpha, omega;
     };
-    static __device__ bool wants(int st) { return st == ST_RUNNING; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->omega}; }
     static __device__ void row(const Mat &, const Vecs &V, const Scal &S, int, int, int i, bool act,
                                double (&a)[ND], double (&b)[ND])
@@ -468,12 +473,46 @@ struct StepBicgC {
     }
 };
 
+// residual replacement steps (p-BiCGStabRR), on systems replacing at this iteration
+template <int WHICH>
+struct StepRR {
+    static constexpr int ND = 1;
+    struct Scal {
+        double beta, omega;
+    };
+    static __device__ bool wants(const Ctl *c) { return c->status == ST_RUNNING && rr_now(c); }
+    static __device__ Scal load(const Ctl *c) { return Scal{c->beta, c->omega}; }
+    static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
+                               double (&a)[ND], double (&b)[ND])
+    {
+        if (sl < A.nslices) {
+            RowRef R = row_ref(A, sl, lane);
+            const double *src = WHICH == 1 ? V.x : WHICH == 2 ? V.r : WHICH == 3 ? V.p : V.s;
+            double y = spmv_row(A, R, src);
+            if (act) {
+                if (WHICH == 1) {
+                    V.r[i] = __dsub_rn(V.b[i], y);
+                } else if (WHICH == 2) {
+                    V.w[i] = y;
+                    V.p[i] = __fma_rn(S.beta, __fma_rn(-S.omega, V.s[i], V.p[i]), V.r[i]);
+                } else if (WHICH == 3) {
+                    V.s[i] = y;
+                } else {
+                    V.z[i] = y;
+                }
+            }
+        }
+        a[0] = 0.0, b[0] = 0.0;
+    }
+    static __device__ void fin(Ctl *, const double *, const Vecs &) {}
+};
+
 // true residual of candidate systems (resolve) or of every system (report)
 template <bool REPORT>
 struct StepTrueRes {
     static constexpr int ND = 2;
     using Scal = NoScal;
-    static __device__ bool wants(int st) { return REPORT || st == ST_CANDIDATE; }
+    static __device__ bool wants(const Ctl *c) { const int st = c->status; return REPORT || st == ST_CANDIDATE; }
     static __device__ Scal load(const Ctl *) { return Scal{}; }
     static __device__ void row(const Mat &A, const Vecs &V, const Scal &, int sl, int lane, int i, bool act,
                                double (&a)[ND], double (&b)[ND])

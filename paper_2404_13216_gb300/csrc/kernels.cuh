@@ -55,7 +55,7 @@ struct Ctl {
     double normb, res, target, tol;
     double trueres, bbx, pad_d0, pad_d1;
     int it, maxit, status, phase;
-    int alg, use_cond, err, pad_i1;     // err: a bounded device wait expired
+    int alg, use_cond, err, rr_period;  // err: a bounded device wait expired; rr_period: 0 = no replacement
     unsigned long long cond;            // cudaGraphConditionalHandle of the loop
     double *hist;
     int hist_cap, pad_i2;
@@ -77,11 +77,20 @@ struct Mat {
     const int *__restrict__ rlen;        // [nslices * 32] row lengths (0 past n)
     const int *__restrict__ ci;          // padded column indices (solver order)
     const double *__restrict__ va;       // padded values
+    const int *__restrict__ lci;         // padded local indices into a tile's staged blocks (or NULL)
+    const int *__restrict__ tblk;        // [ntiles * GMAX] 256-row blocks each tile gathers from, -1 pad;
+                                         // tblk[t * GMAX] == -1: the tile gathers from global memory
 };
 
 struct Vecs {
     double *x, *b, *r0, *r, *w, *t, *p, *s, *z, *v, *y, *q;
 };
+
+// residual replacement at the start of iteration it (every rr_period iterations, never at 0)
+__device__ __forceinline__ bool rr_now(const Ctl *c)
+{
+    return c->rr_period > 0 && c->it > 0 && c->it % c->rr_period == 0;
+}
 
 __device__ __forceinline__ bool fin(double v)
 {
@@ -783,6 +792,71 @@ static __global__ void k_scatter(int n, const int *__restrict__ perm, const doub
 
 
 // ---------------------------------------------------------------------------
+// residual replacement (p-BiCGStabRR): at the start of iteration i, i > 0,
+// i mod k == 0: r = b - A x, w = A r (and p from its recurrence with the new
+// r), s = A p, z = A s.  Each step needs the whole previous vector, so each is
+// its own launch; on other iterations they return at once.
+// ---------------------------------------------------------------------------
+static __global__ void __launch_bounds__(THREADS) k_rr1(Mat A, Vecs V, const Ctl *c)
+{
+    if (c->status != ST_RUNNING || !rr_now(c))
+        return;
+    PBCG_SLICE_LOOP(A)
+    {
+        int i = PBCG_ROW;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double ax = spmv_row(A, R, V.x);
+        if (i < A.n)
+            V.r[i] = __dsub_rn(V.b[i], ax);
+    }
+}
+
+static __global__ void __launch_bounds__(THREADS) k_rr2(Mat A, Vecs V, const Ctl *c)
+{
+    if (c->status != ST_RUNNING || !rr_now(c))
+        return;
+    const double beta = c->beta, nomega = -c->omega;
+    PBCG_SLICE_LOOP(A)
+    {
+        int i = PBCG_ROW;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double wi = spmv_row(A, R, V.r);
+        if (i < A.n) {
+            V.w[i] = wi;
+            V.p[i] = __fma_rn(beta, __fma_rn(nomega, V.s[i], V.p[i]), V.r[i]);
+        }
+    }
+}
+
+static __global__ void __launch_bounds__(THREADS) k_rr3(Mat A, Vecs V, const Ctl *c)
+{
+    if (c->status != ST_RUNNING || !rr_now(c))
+        return;
+    PBCG_SLICE_LOOP(A)
+    {
+        int i = PBCG_ROW;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double si = spmv_row(A, R, V.p);
+        if (i < A.n)
+            V.s[i] = si;
+    }
+}
+
+static __global__ void __launch_bounds__(THREADS) k_rr4(Mat A, Vecs V, const Ctl *c)
+{
+    if (c->status != ST_RUNNING || !rr_now(c))
+        return;
+    PBCG_SLICE_LOOP(A)
+    {
+        int i = PBCG_ROW;
+        RowRef R = row_ref(A, sl_, wr_.lane);
+        double zi = spmv_row(A, R, V.s);
+        if (i < A.n)
+            V.z[i] = zi;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // staged passes: tiles of 256 rows double-buffered in shared memory by TMA
 // ---------------------------------------------------------------------------
 template <int NV, bool MATS>
@@ -797,44 +871,66 @@ struct TilePipe {
     {
         return reinterpret_cast<const double *>(stage(k)) + v * TILE_ROWS;
     }
-    __device__ __forceinline__ const double *va(int k) const
+    __device__ __forceinline__ const double *gwin(int k) const
     {
         return reinterpret_cast<const double *>(stage(k) + L::VEC);
     }
+    __device__ __forceinline__ const double *va(int k) const
+    {
+        return reinterpret_cast<const double *>(stage(k) + L::VEC + L::GWIN);
+    }
     __device__ __forceinline__ const int *ci(int k) const
     {
-        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::VA);
+        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::GWIN + L::VA);
     }
     __device__ __forceinline__ const int *rlen(int k) const
     {
-        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::VA + L::CI);
+        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::GWIN + L::VA + L::CI);
     }
     __device__ __forceinline__ const int *sloff(int k) const
     {
-        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::VA + L::CI + L::RLEN);
+        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::GWIN + L::VA + L::CI + L::RLEN);
     }
 
     // thread 0: copy tile `tile` (nv of the NV vectors) into stage k; e0/e1 are
-    // sl_off[first slice] and sl_off[end slice] of the tile, loaded beforehand
-    __device__ __forceinline__ void issue(int k, int tile, int e0, int e1, const Mat &A,
-                                          const double *const (&src)[NV], int nv)
+    // sl_off[first slice] and sl_off[end slice] of the tile, blk the tile's
+    // gather blocks (blk[0] < 0: none), all loaded beforehand; gx is the
+    // vector the tile's SpMV gathers from (NULL: no SpMV in this pass)
+    __device__ __forceinline__ void issue(int k, int tile, int e0, int e1, const int (&blk)[GMAX], const Mat &A,
+                                          const double *const (&src)[NV], int nv, const double *gx)
     {
         const int s0 = tile * TILE_SLICES;
         const int span = e1 - e0;
         const bool staged = MATS && span > 0 && span <= MCAP;
+        const bool windowed = staged && gx != nullptr && A.lci != nullptr && blk[0] >= 0;
+        int nblk = 0;
+        if (windowed) {
+#pragma unroll
+            for (int g = 0; g < GMAX; g++)
+                nblk += blk[g] >= 0;
+        }
         info[k].e0 = e0;
         info[k].staged = staged;
-        uint32_t bytes = (uint32_t)nv * TILE_ROWS * 8 + L::RLEN + L::SLOFF + (staged ? (uint32_t)span * 12u : 0u);
+        info[k].windowed = windowed;
+        uint32_t bytes = (uint32_t)nv * TILE_ROWS * 8 + L::RLEN + L::SLOFF + (staged ? (uint32_t)span * 12u : 0u) +
+                         (uint32_t)nblk * TILE_ROWS * 8;
         fence_async_shared();
         mbar_arrive_expect_tx(&bar[k], bytes);
         const size_t row0 = (size_t)tile * TILE_ROWS;
         for (int v = 0; v < nv; v++)
             bulk_g2s(stage(k) + (size_t)v * TILE_ROWS * 8, src[v] + row0, TILE_ROWS * 8, &bar[k]);
-        bulk_g2s(stage(k) + L::VEC + L::VA + L::CI, A.rlen + row0, L::RLEN, &bar[k]);
-        bulk_g2s(stage(k) + L::VEC + L::VA + L::CI + L::RLEN, A.sl_off + s0, L::SLOFF, &bar[k]);
+        bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA + L::CI, A.rlen + row0, L::RLEN, &bar[k]);
+        bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA + L::CI + L::RLEN, A.sl_off + s0, L::SLOFF, &bar[k]);
         if (staged) {
-            bulk_g2s(stage(k) + L::VEC + L::VA, A.ci + e0, (uint32_t)span * 4u, &bar[k]);
-            bulk_g2s(stage(k) + L::VEC, A.va + e0, (uint32_t)span * 8u, &bar[k]);
+            bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA, (windowed ? A.lci : A.ci) + e0, (uint32_t)span * 4u, &bar[k]);
+            bulk_g2s(stage(k) + L::VEC + L::GWIN, A.va + e0, (uint32_t)span * 8u, &bar[k]);
+        }
+        if (windowed) {
+#pragma unroll
+            for (int g = 0; g < GMAX; g++)
+                if (blk[g] >= 0)
+                    bulk_g2s(stage(k) + L::VEC + (size_t)g * TILE_ROWS * 8, gx + (size_t)blk[g] * TILE_ROWS,
+                             TILE_ROWS * 8, &bar[k]);
         }
     }
 
@@ -849,6 +945,16 @@ struct TilePipe {
         const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
         const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
         double acc = 0.0;
+        if (info[k].windowed) {                         // gather from the staged blocks
+            const double *xw = gwin(k);
+            for (int j0 = 0; j0 < width; j0 += UNR) {
+#pragma unroll
+                for (int j = 0; j < UNR; j++)
+                    if (j0 + j < len)
+                        acc = __fma_rn(vp[(j0 + j) * 32], xw[cp[(j0 + j) * 32]], acc);
+            }
+            return acc;
+        }
         for (int j0 = 0; j0 < width; j0 += UNR) {
             int c[UNR];
             double v[UNR], xv[UNR];
@@ -874,8 +980,8 @@ struct TilePipe {
 
 // common tile loop: prologue, bounded waits, refill after each tile
 template <int NV, bool MATS, class Body>
-__device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&src)[NV], int nv, Ctl *c,
-                                          uint8_t *dsm, Body body)
+__device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&src)[NV], int nv, const double *gx,
+                                          Ctl *c, uint8_t *dsm, Body body)
 {
     __shared__ uint64_t bar[NSTAGE];
     __shared__ StageInfo info[NSTAGE];
@@ -885,6 +991,12 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
     auto tile_of = [&](int jj) { return (int)blockIdx.x + jj * (int)gridDim.x; };
     auto end_slice = [&](int t) { return min((t + 1) * TILE_SLICES, A.nslices); };
     int pe0 = 0, pe1 = 0;            // thread 0: offsets of the next tile to issue
+    int pblk[GMAX];                  // thread 0: gather blocks of the next tile to issue
+    auto load_blk = [&](int t, int (&blk)[GMAX]) {
+#pragma unroll
+        for (int g = 0; g < GMAX; g++)
+            blk[g] = (MATS && A.tblk && gx) ? A.tblk[(size_t)t * GMAX + g] : -1;
+    };
     if (threadIdx.x == 0) {
         for (int k = 0; k < NSTAGE; k++)
             mbar_init(&bar[k], 1);
@@ -895,12 +1007,15 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
     if (threadIdx.x == 0) {
         for (int k = 0; k < NSTAGE && k < my; k++) {
             const int t = tile_of(k);
-            P.issue(k, t, A.sl_off[t * TILE_SLICES], A.sl_off[end_slice(t)], A, src, nv);
+            int blk[GMAX];
+            load_blk(t, blk);
+            P.issue(k, t, A.sl_off[t * TILE_SLICES], A.sl_off[end_slice(t)], blk, A, src, nv, gx);
         }
         if (NSTAGE < my) {
             const int t = tile_of(NSTAGE);
             pe0 = A.sl_off[t * TILE_SLICES];
             pe1 = A.sl_off[end_slice(t)];
+            load_blk(t, pblk);
         }
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -916,11 +1031,12 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
         body(P, k, tile_of(j), warp, lane);
         __syncthreads();
         if (threadIdx.x == 0 && j + NSTAGE < my) {
-            P.issue(k, tile_of(j + NSTAGE), pe0, pe1, A, src, nv);
+            P.issue(k, tile_of(j + NSTAGE), pe0, pe1, pblk, A, src, nv, gx);
             if (j + NSTAGE + 1 < my) {
                 const int t = tile_of(j + NSTAGE + 1);
                 pe0 = A.sl_off[t * TILE_SLICES];
                 pe1 = A.sl_off[end_slice(t)];
+                load_blk(t, pblk);
             }
         }
     }
@@ -946,13 +1062,14 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
     __shared__ Shm<4> sh;
     shm_init<4, MODE>(sh);
     const bool first = (c->it == 0);
+    const bool rr = rr_now(c);       // p, s, z were just recomputed: no recurrence this iteration
     const double alpha = c->alpha, beta = c->beta, omega = c->omega;
     const double nalpha = -alpha, nomega = -omega;
     DotSet<4, MODE> D;
     D.init();
     // stage slots: 0 r, 1 w, 2 r0, 3 p (t when first), 4 s, 5 z, 6 v
     const double *const src[7] = {V.r, V.w, V.r0, first ? V.t : V.p, V.s, V.z, V.v};
-    tile_loop<7, MATS>(A, src, first ? 4 : 7, c, dsm,
+    tile_loop<7, MATS>(A, src, first ? 4 : 7, first ? nullptr : V.w, c, dsm,
                        [&](const TilePipe<7, MATS> &P, int k, int tile, int warp, int lane) {
         const int sl = tile * TILE_SLICES + warp;
         const int i = sl * 32 + lane;
@@ -972,9 +1089,15 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
                 ti = P.spmv(k, A, warp, lane, V.w);
                 const double pold = P.vec(k, 3)[o], sold = P.vec(k, 4)[o];
                 const double zold = P.vec(k, 5)[o], vold = P.vec(k, 6)[o];
-                pi = __fma_rn(beta, __fma_rn(nomega, sold, pold), ri);
-                si = __fma_rn(beta, __fma_rn(nomega, zold, sold), wi);
-                zi = __fma_rn(beta, __fma_rn(nomega, vold, zold), ti);
+                if (rr) {
+                    pi = pold;
+                    si = sold;
+                    zi = zold;
+                } else {
+                    pi = __fma_rn(beta, __fma_rn(nomega, sold, pold), ri);
+                    si = __fma_rn(beta, __fma_rn(nomega, zold, sold), wi);
+                    zi = __fma_rn(beta, __fma_rn(nomega, vold, zold), ti);
+                }
             }
             q = __fma_rn(nalpha, si, ri);
             y = __fma_rn(nalpha, zi, wi);
@@ -1030,7 +1153,7 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
     D.init();
     // stage slots: 0 q, 1 y, 2 p, 3 x, 4 t, 5 r0
     const double *const src[6] = {V.q, V.y, V.p, V.x, V.t, V.r0};
-    tile_loop<6, MATS>(A, src, 6, c, dsm, [&](const TilePipe<6, MATS> &P, int k, int tile, int warp, int lane) {
+    tile_loop<6, MATS>(A, src, 6, V.z, c, dsm, [&](const TilePipe<6, MATS> &P, int k, int tile, int warp, int lane) {
         const int sl = tile * TILE_SLICES + warp;
         const int i = sl * 32 + lane;
         const bool act = sl < A.nslices && i < A.n;

@@ -20,8 +20,9 @@ namespace pbcg {
 constexpr int TILE_SLICES = 8;                 // = warps per CTA
 constexpr int TILE_ROWS = TILE_SLICES * 32;
 constexpr int NSTAGE = 2;
-constexpr int MCAP = TILE_ROWS * 8;            // staged SELL entries per tile (width <= 8)
+constexpr int MCAP = TILE_ROWS * 7;            // staged SELL entries per tile (width <= 7)
 constexpr int SLOFF_STAGE = 16;                // slice offsets copied per tile (needs 9)
+constexpr int GMAX = 6;                        // 256-row blocks of the gathered vector staged per tile
 constexpr unsigned MBAR_SPIN_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -84,16 +85,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 // Dynamic shared memory of a staged pass with NV input vectors:
-// NSTAGE stages of { vec[NV][256] f64, va[MCAP] f64 (if staged), ci[MCAP] i32 (if staged),
-// rlen[256] i32, sl_off[16] i32 }.
+// NSTAGE stages of { vec[NV][256] f64, gwin[GMAX][256] f64 (if staged), va[MCAP] f64 (if staged),
+// ci[MCAP] i32 (if staged), rlen[256] i32, sl_off[16] i32 }.
+// When a tile's columns fall in at most GMAX 256-row blocks, those blocks of
+// the gathered vector are staged in gwin and ci holds local indices into it.
 template <int NV, bool MATS>
 struct StageLayout {
     static constexpr uint32_t VEC = NV * TILE_ROWS * 8;
+    static constexpr uint32_t GWIN = MATS ? GMAX * TILE_ROWS * 8 : 0;
     static constexpr uint32_t VA = MATS ? MCAP * 8 : 0;
     static constexpr uint32_t CI = MATS ? MCAP * 4 : 0;
     static constexpr uint32_t RLEN = TILE_ROWS * 4;
     static constexpr uint32_t SLOFF = SLOFF_STAGE * 4;
-    static constexpr uint32_t STAGE = VEC + VA + CI + RLEN + SLOFF;
+    static constexpr uint32_t STAGE = VEC + GWIN + VA + CI + RLEN + SLOFF;
     static constexpr uint32_t TOTAL = NSTAGE * STAGE;
     static_assert(STAGE % 16 == 0, "stages must stay 16-byte aligned");
 };
@@ -102,6 +106,7 @@ struct StageLayout {
 struct StageInfo {
     int e0;          // first SELL entry of the tile
     int staged;      // 1 if the tile's ci/va are in shared memory
+    int windowed;    // 1 if the gathered vector's blocks are in shared memory (ci local)
 };
 
 }  // namespace pbcg

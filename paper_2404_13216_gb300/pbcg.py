@@ -18,12 +18,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpbcg.so")
 
 OK, MAXIT, BREAKDOWN, NONFINITE = 0, 1, 2, 3
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = -1, -2, -3, -4
-BICGSTAB, PIPELINED = 0, 1
+BICGSTAB, PIPELINED, PIPELINED_RR = 0, 1, 2
+OPT_RR_PERIOD = 1
 PLAIN, EXACT = 0, 1
 
 EXPORTS = ("pbcg_create", "pbcg_destroy", "pbcg_last_error", "pbcg_csr_upload", "pbcg_mat_free",
            "pbcg_solve", "pbcg_solve_batched", "pbcg_residual_history", "pbcg_dot", "pbcg_spmv",
-           "pbcg_profile_solve", "pbcg_dot_noalloc")
+           "pbcg_profile_solve", "pbcg_dot_noalloc", "pbcg_set_option")
 
 
 class PbcgError(RuntimeError):
@@ -68,6 +69,8 @@ def load_library(path: str = LIB_PATH):
                                        P, P, P, i32, ctypes.POINTER(i32)]
     lib.pbcg_profile_solve.restype = ctypes.c_int
     lib.pbcg_dot_noalloc.argtypes = [i64, P, P, ctypes.c_int, P, P]
+    lib.pbcg_set_option.argtypes = [P, ctypes.c_int, i64]
+    lib.pbcg_set_option.restype = ctypes.c_int
     lib.pbcg_dot_noalloc.restype = ctypes.c_int
     return lib
 
@@ -146,6 +149,9 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_option(self, option: int, value: int):
+        self._check(_lib.pbcg_set_option(self.handle, int(option), int(value)))
 
     def last_error(self) -> str:
         return _lib.pbcg_last_error(self.handle).decode()

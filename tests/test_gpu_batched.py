@@ -129,3 +129,20 @@ def test_batched_config_sample_bitwise_vs_single(ctx):
         assert rs.iters == res[k].iters and rs.status == res[k].status
         assert same(ctx.history(), hb[k]) and same(xs, x[r0:r1])
         Ms.free()
+
+
+def test_batched_residual_replacement_bitwise(ctx, orc):
+    from paper_2404_13216_gb300 import pbcg
+    systems, A, srp, b = small_batch(seed=21, nsys=5)
+    tol = np.full(len(systems), 1e-12)
+    ctx.set_option(pbcg.OPT_RR_PERIOD, 10)
+    M = ctx.upload_csr(A)
+    x = np.zeros(A.n)
+    res = ctx.solve_batched(M, srp, b, x, tol, 2000, pbcg.PIPELINED_RR, 1)
+    for k, S in enumerate(systems):
+        r0, r1 = srp[k], srp[k + 1]
+        ref = orc.solve(S.row_ptr, S.col_idx, S.vals, b[r0:r1], tol=1e-12, maxit=2000, alg=1, mode=1, rr_period=10)
+        assert res[k].status == ref.status and res[k].iters == ref.iters, k
+        assert same(ctx.history(k), ref.history) and same(x[r0:r1], ref.x), k
+    M.free()
+    ctx.set_option(pbcg.OPT_RR_PERIOD, 50)

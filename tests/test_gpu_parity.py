@@ -262,3 +262,66 @@ def test_full_size_128cubed_first_iterations(ctx, orc):
     M.free()
     rel = np.abs(hist - hp) / np.abs(hp)
     assert np.all(rel <= 4 * spread + 1e-13), (rel.max(), spread.max())
+
+
+@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
+def test_powerlaw_exact_bitwise(ctx, orc, alg):
+    """Random power-law rows (the rows are sorted by length inside the library
+    and most tiles gather from global memory): exact solve bit-identical."""
+    A = inputs.powerlaw(n=30000, mean_len=30, max_len=600, seed=5)
+    b = inputs.rhs_ones(A)
+    ref, res, x, hist = run_both(ctx, orc, A, b, 1e-10, 500, alg, 1)
+    assert res.status == ref.status and res.iters == ref.iters
+    assert same(hist, ref.history) and same(x, ref.x)
+
+
+def test_mixed_window_tiles_exact_bitwise(ctx, orc):
+    """A stencil matrix with a few long random rows: some tiles gather from
+    staged blocks, others from global memory, in the same pass."""
+    A = inputs.convdiff3d(20, 30.0)
+    rng = np.random.default_rng(9)
+    rows = []
+    for i in range(A.n):
+        c = list(A.col_idx[A.row_ptr[i]:A.row_ptr[i + 1]])
+        v = list(A.vals[A.row_ptr[i]:A.row_ptr[i + 1]])
+        if i % 997 == 0:
+            extra = rng.choice(A.n, size=12, replace=False)
+            for j in extra:
+                if j not in c:
+                    c.append(int(j))
+                    v.append(float(rng.uniform(-1e-3, 1e-3)))
+            order = np.argsort(c)
+            c = [c[k] for k in order]
+            v = [v[k] for k in order]
+        rows.append((c, v))
+    rp = np.zeros(A.n + 1, np.int32)
+    rp[1:] = np.cumsum([len(c) for c, _ in rows])
+    B = inputs.CSR(A.n, rp, np.concatenate([c for c, _ in rows]).astype(np.int32),
+                   np.concatenate([v for _, v in rows]))
+    b = inputs.rhs_ones(B)
+    ref, res, x, hist = run_both(ctx, orc, B, b, 1e-10, 600, 1, 1)
+    assert res.status == ref.status and res.iters == ref.iters
+    assert same(hist, ref.history) and same(x, ref.x)
+
+
+@pytest.mark.parametrize("mode", [1, 0], ids=["exact", "plain"])
+@pytest.mark.parametrize("k", [7, 25])
+def test_residual_replacement_vs_oracle(ctx, orc, mode, k):
+    """p-BiCGStabRR (residual replacement every k iterations)."""
+    from paper_2404_13216_gb300 import pbcg
+    A = inputs.convdiff3d(24, 50.0)
+    b = inputs.rhs_ones(A)
+    tol = 1e-12
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=tol, maxit=1000, alg=1, mode=mode, rr_period=k, nthreads=8)
+    ctx.set_option(pbcg.OPT_RR_PERIOD, k)
+    M = ctx.upload_csr(A)
+    x = np.zeros(A.n)
+    res = ctx.solve(M, b, x, tol, 1000, pbcg.PIPELINED_RR, mode)
+    hist = ctx.history()
+    M.free()
+    ctx.set_option(pbcg.OPT_RR_PERIOD, 50)
+    if mode == 1:
+        assert res.status == ref.status and res.iters == ref.iters
+        assert same(hist, ref.history) and same(x, ref.x)
+    else:
+        assert res.status == 0 and res.relres_true <= tol

@@ -207,3 +207,43 @@ def test_exact_mode_history_is_partition_free(orc):
     for t in (3, 8):
         res = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=40, alg=1, mode=1, nthreads=t)
         assert np.array_equal(res.history, ref.history) and np.array_equal(res.x, ref.x)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_rr_iterates_follow_rational(orc, seed):
+    """Residual replacement swaps recurrence vectors for their true values,
+    which are equal in exact arithmetic: the FP64 oracle with replacement every
+    2 iterations still follows the rational Algorithm 2."""
+    n = 6
+    A, b = tiny_system(200 + seed, n)
+    Af, bf = frac_mat(A), [Fraction(int(v)) for v in b]
+    runs = ratref.pbicgstab(Af, bf, [Fraction(0)] * n, 5)
+    rp, ci, v = dense_to_csr(A)
+    res = orc.solve(rp, ci, v, b.astype(float), tol=1e-300, maxit=4, alg=1, mode=orc.EXACT, rr_period=2)
+    normb = math.sqrt(float(ratref.dot(bf, bf)))
+    for i in range(min(4, len(runs))):
+        r = runs[i]["r"]
+        want = math.sqrt(float(ratref.dot(r, r))) / normb
+        if want == 0:
+            assert res.history[i + 1] < 1e-12
+        else:
+            assert abs(res.history[i + 1] - want) <= 1e-9 * want + 1e-15
+
+
+def test_rr_keeps_true_residual_on_track(orc):
+    """48^3 convection-diffusion to 1e-12: plain p-BiCGStab loses its true
+    residual; with replacement every 25 iterations it converges."""
+    A = inputs.convdiff3d(32, 50.0)
+    b = inputs.rhs_ones(A)
+    rr = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-12, maxit=1500, alg=1, mode=1, rr_period=25, nthreads=8)
+    assert rr.status == orc.CONVERGED and rr.relres_true <= 1e-12
+    with pytest.raises(ValueError):
+        orc.solve(A.row_ptr, A.col_idx, A.vals, b, alg=0, rr_period=5)
+
+
+def test_rr_period_zero_is_algorithm_2(orc):
+    A = inputs.convdiff2d(16, 5.0)
+    b = inputs.rhs_ones(A)
+    r0 = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=300, alg=1, mode=1)
+    r1 = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=300, alg=1, mode=1, rr_period=0)
+    assert np.array_equal(r0.history, r1.history) and np.array_equal(r0.x, r1.x)
