@@ -148,6 +148,106 @@ int pbcg_solve_batched(pbcg_ctx *ctx, const pbcg_mat *A, int32_t nsys, const int
 int pbcg_residual_history(pbcg_ctx *ctx, int32_t sys, double *out, int32_t cap, int32_t *len);
 
 /*
+ * Pools: continuous batching of independent solves (serving).
+ *
+ * The method is that of pbcg_solve (Section 2, Algorithm 1 or 2 with the
+ * stopping rule above); a pool only changes when each system starts and
+ * stops.  Requests are admitted while others run, every live system advances
+ * in the same launches, and a finished one leaves without stopping the rest.
+ * Each system's arithmetic is the same as its own pbcg_solve: bit for bit in
+ * exact mode.
+ *
+ * Memory: one block-diagonal SELL-32 layout of fixed capacity allocated by
+ * pbcg_pool_create.  A system takes ceil(n / 256) whole 256-row tiles of the
+ * 13 pool vectors and sum over its 32-row slices of 32 * (longest row of the
+ * slice) matrix entries; both come from first-fit range allocators.
+ *
+ * Streams: steps run on the context's stream; uploads and result copies on a
+ * stream the pool creates.  pbcg_pool_step only enqueues work; pbcg_pool_poll
+ * reads control-block snapshots taken after each step and blocks only when
+ * asked to.  One host thread at a time may call a pool's functions.
+ */
+typedef struct pbcg_pool pbcg_pool;  /* opaque, library-owned */
+
+typedef struct {
+    int64_t max_rows;          /* rows of all resident systems together (each rounded up to 256) */
+    int64_t max_entries;       /* SELL-32 entries of all resident systems together */
+    int32_t max_slots;         /* systems resident at a time */
+    int32_t maxit;             /* largest maxit a request may ask for (history length maxit + 1) */
+    int32_t alg;               /* PBCG_ALG_*, for every system of the pool */
+    int32_t dot_mode;          /* PBCG_DOT_*, for every system of the pool */
+    int64_t max_request_rows;  /* largest n of one request */
+    int64_t max_request_nnz;   /* largest nnz of one request (sizes the upload staging) */
+} pbcg_pool_config;
+
+/*
+ * Create a pool on ctx's device.  Device memory: about 8 * (13 * max_rows +
+ * 1.5 * max_entries + max_slots * (maxit + 1)) + 12 * max_request_nnz bytes.
+ * Errors: INVALID (NULL, non-positive or too large sizes, unknown alg or
+ * dot_mode), OOM, CUDA.  A pool must be destroyed before its context.
+ */
+int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out);
+
+/* Wait for the pool's work and free it.  destroy(NULL) is a no-op. */
+void pbcg_pool_destroy(pbcg_pool *pool);
+
+/*
+ * Admit one system A x = b (CSR as for pbcg_csr_upload; row_ptr, col_idx,
+ * vals, b, x0 host or device pointers; x0 NULL means zero) with its own tol
+ * and maxit (<= the pool's maxit).  Its setup passes and iterations run in
+ * the following pbcg_pool_step calls.  The caller's arrays are consumed when
+ * the call returns.  Host work: O(n) on the row pointers; the column indices
+ * are checked on the device, and a request with an index outside [0, n)
+ * finishes at once with PBCG_ERR_INVALID as its result.
+ * Returns 0 and the slot in *slot, 1 when the pool has no room for it now
+ * (no free slot, tile range or entry range; *slot = -1), or an error
+ * (INVALID: NULL pointer, n or nnz beyond the pool's request limits, bad
+ * row_ptr, tol <= 0, maxit out of range).
+ */
+int pbcg_pool_admit(pbcg_pool *pool, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                    const double *vals, const double *b, const double *x0, double tol, int32_t maxit,
+                    int32_t *slot);
+
+/*
+ * Enqueue one step: at most `iters` iterations of every live system (fewer
+ * when none is left running), as one graph launch, followed by a snapshot of
+ * the control blocks.  Does not wait for the GPU unless four steps are
+ * already in flight.  Errors: INVALID (iters < 1), CUDA.
+ */
+int pbcg_pool_step(pbcg_pool *pool, int32_t iters);
+
+/*
+ * Report systems that finished, each once: the newest completed snapshot is
+ * scanned and up to cap finished slots are written to slots[]; *count gets
+ * how many were found (it can exceed cap; the rest are reported by the next
+ * call).  wait != 0 first waits for the newest step.  *pending (may be NULL)
+ * gets the number of steps not yet complete.
+ */
+int pbcg_pool_poll(pbcg_pool *pool, int wait, int32_t *slots, int32_t cap, int32_t *count, int32_t *pending);
+
+/*
+ * Retire a reported slot: copy its n solution entries to x (host or device,
+ * may be NULL) and its result to out (may be NULL; status PBCG_OK ..
+ * PBCG_NONFINITE, or PBCG_ERR_INVALID / PBCG_ERR_TIMEOUT for a request that
+ * failed), then free its slot, tiles and entries for later admissions.
+ * Waits only for the copy of x.  Returns the status, or the request's error,
+ * or INVALID when the slot was not reported by pbcg_pool_poll.
+ */
+int pbcg_pool_result(pbcg_pool *pool, int32_t slot, double *x, pbcg_result *out);
+
+/*
+ * Residual history res_0 .. res_iters of a reported, not yet retired slot,
+ * as for pbcg_residual_history.
+ */
+int pbcg_pool_history(pbcg_pool *pool, int32_t slot, double *out, int32_t cap, int32_t *len);
+
+/*
+ * Free room: free slots, the largest free row range (a multiple of 256) and
+ * the largest free entry range.  Any output may be NULL.
+ */
+int pbcg_pool_room(const pbcg_pool *pool, int32_t *free_slots, int64_t *free_rows, int64_t *free_entries);
+
+/*
  * Context options.
  *   PBCG_OPT_RR_PERIOD: k >= 1, the period of residual replacement used by
  *     PBCG_ALG_PIPELINED_RR (default 50).  Section 2 names residual replacement

@@ -147,6 +147,7 @@ Mat mat_of(const pbcg_mat *m)
     A.rlen = m->rlen;
     A.ci = m->ci;
     A.va = m->va;
+    A.sl_w = nullptr;
     A.lci = m->lci;
     A.tblk = m->tblk;
     return A;
@@ -967,6 +968,7 @@ Mat layout_mat(const BatchLayout *L)
     A.rlen = L->rlen;
     A.ci = L->ci;
     A.va = L->va;
+    A.sl_w = nullptr;
     A.lci = nullptr;
     A.tblk = nullptr;
     return A;
@@ -979,11 +981,13 @@ Batch batch_of(pbcg_ctx *ctx, const BatchLayout *L)
     B.ntiles = L->ntiles;
     B.tile_sys = L->tile_sys;
     B.sys_t0 = L->sys_t0;
+    B.sys_t1 = L->sys_t0 + 1;
     B.ctl = BW.ctl;
     B.acc = BW.acc;
     B.part = BW.part;
     B.done = BW.done;
     B.flag = BW.flag;
+    B.lv_n = B.lv_pre = B.lv_t0 = nullptr;
     return B;
 }
 
@@ -1220,7 +1224,288 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
 
 #undef BW
 
+
+// ---------------------------------------------------------------------------
+// pools: continuous batching of independent systems
+//
+// A pool owns one block-diagonal layout of fixed capacity.  Each resident
+// system (a slot) holds a range of whole 256-row tiles and a range of SELL-32
+// entries.  Admission uploads on the pool's copy stream into ranges that no
+// running step reads (free tiles are skipped by the sweep, and a retired
+// slot's tiles stay skipped because its status is final), then a small kernel
+// on the solve stream makes the slot live.  A step is one graph launch of up
+// to K iterations of every live slot; after it the control blocks are copied
+// into a ring of pinned snapshots, so polling never waits for the GPU.
+// ---------------------------------------------------------------------------
+// first-fit allocator of [start, start + len) ranges
+struct RangeAlloc {
+    std::map<long long, long long> fr;     // start -> end of free ranges
+    void init(long long cap)
+    {
+        fr.clear();
+        if (cap > 0)
+            fr[0] = cap;
+    }
+    long long take(long long len)
+    {
+        for (auto it = fr.begin(); it != fr.end(); ++it) {
+            if (it->second - it->first >= len) {
+                long long a = it->first, e = it->second;
+                fr.erase(it);
+                if (a + len < e)
+                    fr[a + len] = e;
+                return a;
+            }
+        }
+        return -1;
+    }
+    void give(long long a, long long len)
+    {
+        if (len <= 0)
+            return;
+        long long e = a + len;
+        auto nx = fr.lower_bound(a);
+        if (nx != fr.end() && nx->first == e) {
+            e = nx->second;
+            fr.erase(nx);
+        }
+        auto pv = fr.lower_bound(a);
+        if (pv != fr.begin()) {
+            --pv;
+            if (pv->second == a) {
+                a = pv->first;
+                fr.erase(pv);
+            }
+        }
+        fr[a] = e;
+    }
+    long long largest() const
+    {
+        long long m = 0;
+        for (auto &kv : fr)
+            m = std::max(m, kv.second - kv.first);
+        return m;
+    }
+};
+
+struct PoolSlot {
+    bool used = false, reported = false;
+    int gen = 0;
+    int tile0 = 0, ntiles = 0, n = 0;
+    long long e0 = 0, ne = 0;
+    Ctl last;                          // control block at the snapshot that reported it
+};
+
+constexpr int POOL_RING = 4;
+
 }  // namespace
+
+struct pbcg_pool {
+    pbcg_ctx *ctx = nullptr;
+    pbcg_pool_config cfg = {};
+    int max_tiles = 0;
+    cudaStream_t cstream = nullptr;    // uploads and result copies
+    cudaEvent_t up_ev = nullptr;
+    cudaEvent_t ev[POOL_RING] = {};
+    Ctl *snap[POOL_RING] = {};         // pinned
+    long long issued = 0;              // steps launched
+    int *meta = nullptr;               // pinned: rp | sl_w | sl_off of one request
+    int *sl_off = nullptr, *sl_w = nullptr, *rlen = nullptr, *ci = nullptr, *tile_sys = nullptr;
+    int *t0 = nullptr, *t1 = nullptr, *left = nullptr, *flag = nullptr, *bad = nullptr;
+    int *lv_n = nullptr, *lv_pre = nullptr, *lv_t0 = nullptr;    // live-tile list
+    int *st_rp = nullptr, *st_ci = nullptr, *st_meta = nullptr;   // staging of one request
+    double *st_va = nullptr;
+    double *va = nullptr, *hist = nullptr;
+    double *vec[V_COUNT] = {};
+    Ctl *ctl = nullptr;
+    GAcc *acc = nullptr;
+    double *part = nullptr;
+    unsigned *done = nullptr;
+    RangeAlloc tiles, entries;
+    std::vector<PoolSlot> slots;
+    int next_gen = 1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int body_kernels = 0;
+};
+
+namespace {
+
+void pool_release(pbcg_pool *P)
+{
+    if (!P)
+        return;
+    if (P->exec)
+        cudaGraphExecDestroy(P->exec);
+    if (P->graph)
+        cudaGraphDestroy(P->graph);
+    void *ptrs[] = {P->sl_off, P->sl_w, P->rlen,  P->ci,      P->tile_sys, P->t0,   P->t1,   P->left,
+                    P->flag,   P->bad,  P->st_rp, P->st_ci,   P->st_meta,  P->st_va, P->va,  P->hist,
+                    P->ctl,    P->acc,  P->part,  P->done,     P->lv_n, P->lv_pre, P->lv_t0};
+    for (void *q : ptrs)
+        cudaFree(q);
+    for (auto &v : P->vec)
+        cudaFree(v);
+    for (auto &h : P->snap)
+        cudaFreeHost(h);
+    cudaFreeHost(P->meta);
+    for (auto &e : P->ev)
+        if (e)
+            cudaEventDestroy(e);
+    if (P->up_ev)
+        cudaEventDestroy(P->up_ev);
+    if (P->cstream)
+        cudaStreamDestroy(P->cstream);
+    delete P;
+}
+
+Mat pool_mat(const pbcg_pool *P)
+{
+    Mat A;
+    A.n = P->max_tiles * TILE_ROWS;
+    A.nslices = P->max_tiles * TILE_SLICES;
+    A.sl_off = P->sl_off;
+    A.sl_w = P->sl_w;
+    A.rlen = P->rlen;
+    A.ci = P->ci;
+    A.va = P->va;
+    A.lci = nullptr;
+    A.tblk = nullptr;
+    return A;
+}
+
+Vecs pool_vecs(const pbcg_pool *P)
+{
+    Vecs V;
+    V.x = P->vec[V_X];
+    V.b = P->vec[V_B];
+    V.r0 = P->vec[V_R0];
+    V.r = P->vec[V_R];
+    V.w = P->vec[V_W];
+    V.t = P->vec[V_T];
+    V.p = P->vec[V_P];
+    V.s = P->vec[V_S];
+    V.z = P->vec[V_Z];
+    V.v = P->vec[V_V];
+    V.y = P->vec[V_Y];
+    V.q = P->vec[V_Q];
+    return V;
+}
+
+Batch pool_batch(const pbcg_pool *P)
+{
+    Batch B;
+    B.nsys = P->cfg.max_slots;
+    B.ntiles = P->max_tiles;
+    B.tile_sys = P->tile_sys;
+    B.sys_t0 = P->t0;
+    B.sys_t1 = P->t1;
+    B.ctl = P->ctl;
+    B.acc = P->acc;
+    B.part = P->part;
+    B.done = P->done;
+    B.flag = P->flag;
+    B.lv_n = P->lv_n;
+    B.lv_pre = P->lv_pre;
+    B.lv_t0 = P->lv_t0;
+    return B;
+}
+
+template <int MODE>
+std::vector<void *> pool_body(int alg)
+{
+    std::vector<void *> k;
+    k.push_back((void *)k_batched<MODE, PoolSetup1>);
+    if (alg != PBCG_ALG_BICGSTAB) {
+        k.push_back((void *)k_batched<MODE, PoolSetup2>);
+        k.push_back((void *)k_batched<0, PoolSetup3>);
+    }
+    k.push_back((void *)k_batched<1, StepTrueRes<false>>);
+    if (alg == PBCG_ALG_PIPELINED_RR) {
+        k.push_back((void *)k_batched<0, StepRR<1>>);
+        k.push_back((void *)k_batched<0, StepRR<2>>);
+        k.push_back((void *)k_batched<0, StepRR<3>>);
+        k.push_back((void *)k_batched<0, StepRR<4>>);
+    }
+    if (alg == PBCG_ALG_BICGSTAB) {
+        k.push_back((void *)k_batched<MODE, StepBicgP>);
+        k.push_back((void *)k_batched<MODE, StepBicgA>);
+        k.push_back((void *)k_batched<MODE, StepBicgB>);
+        k.push_back((void *)k_batched<MODE, StepBicgC>);
+    } else {
+        k.push_back((void *)k_batched<MODE, StepPipeX>);
+        k.push_back((void *)k_batched<MODE, StepPipeY>);
+    }
+    return k;
+}
+
+// graph: list the live tiles, then WHILE { setup passes of new slots, true
+// residual of candidates, [replacement passes], the iteration's passes, step
+// control (which lists the live tiles again) }
+int pool_build_graph(pbcg_ctx *ctx, pbcg_pool *P)
+{
+    CK(cudaGraphCreate(&P->graph, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, P->graph, 1, cudaGraphCondAssignDefault));
+    Mat A = pool_mat(P);
+    Vecs V = pool_vecs(P);
+    Batch B = pool_batch(P);
+    unsigned long long hv = (unsigned long long)h;
+    int *lvn = P->lv_n, *lvp = P->lv_pre, *lvt = P->lv_t0, *left = P->left;
+    auto ctl_node = [&](cudaGraph_t g, cudaGraphNode_t *dep, int first, cudaGraphNode_t *node) -> int {
+        int f = first;
+        void *cargs[] = {&B, &lvn, &lvp, &lvt, &left, &hv, &f};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void *)k_pool_ctl;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(1024);
+        kp.kernelParams = cargs;
+        CK(cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp));
+        return 0;
+    };
+    cudaGraphNode_t list0;
+    int rc = ctl_node(P->graph, nullptr, 1, &list0);
+    if (rc)
+        return rc;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, P->graph, &list0, nullptr, 1, &cp));
+    cudaGraph_t g = cp.conditional.phGraph_out[0];
+    std::vector<void *> body = P->cfg.dot_mode ? pool_body<1>(P->cfg.alg) : pool_body<0>(P->cfg.alg);
+    cudaGraphNode_t prev = nullptr;
+    for (void *fn : body) {
+        void *args[3] = {&A, &V, &B};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = fn;
+        kp.gridDim = dim3(bgrid(ctx, fn, B.ntiles));
+        kp.blockDim = dim3(THREADS);
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        prev = node;
+    }
+    cudaGraphNode_t last;
+    rc = ctl_node(g, &prev, 0, &last);
+    if (rc)
+        return rc;
+    CK(cudaGraphInstantiate(&P->exec, P->graph, 0));
+    P->body_kernels = (int)body.size() + 1;
+    return 0;
+}
+
+bool final_status(const Ctl &c)
+{
+    return (c.status >= 0 && c.status <= 3) || c.status == ST_INVALID || c.status == ST_TIMEOUT || c.err;
+}
+
+}  // namespace
+
 
 extern "C" {
 
@@ -1527,6 +1812,420 @@ int pbcg_solve_batched(pbcg_ctx *ctx, const pbcg_mat *A, int32_t nsys, const int
                        double *x, const double *tol, int32_t maxit, int alg, int dot_mode, pbcg_result *out)
 {
     return solve_batched_impl(ctx, A, nsys, sys_row_ptr, b, x, tol, maxit, alg, dot_mode, out);
+}
+
+
+int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!cfg || !out)
+        return fail(ctx, PBCG_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    const pbcg_pool_config c = *cfg;
+    if (c.max_rows < 1 || c.max_entries < 1 || c.max_slots < 1 || c.maxit < 0 || c.max_request_rows < 1 ||
+        c.max_request_nnz < 0)
+        return fail(ctx, PBCG_ERR_INVALID, "pool sizes must be positive");
+    if (c.alg != PBCG_ALG_BICGSTAB && c.alg != PBCG_ALG_PIPELINED && c.alg != PBCG_ALG_PIPELINED_RR)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", c.alg);
+    if (c.dot_mode != PBCG_DOT_PLAIN && c.dot_mode != PBCG_DOT_EXACT)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", c.dot_mode);
+    const long long tiles = (c.max_rows + TILE_ROWS - 1) / TILE_ROWS;
+    if (tiles * TILE_ROWS > INT32_MAX / 2 || c.max_entries > INT32_MAX || c.max_request_rows > INT32_MAX / 2 ||
+        c.max_request_nnz >= (1ll << 31) || c.max_slots > (1 << 20))
+        return fail(ctx, PBCG_ERR_INVALID, "pool too large");
+    CK(cudaSetDevice(ctx->device));
+    pbcg_pool *P = new pbcg_pool();
+    P->ctx = ctx;
+    P->cfg = c;
+    P->max_tiles = (int)tiles;
+    const size_t rows = (size_t)tiles * TILE_ROWS, nsl = (size_t)tiles * TILE_SLICES;
+    const size_t req_tiles = (size_t)((c.max_request_rows + TILE_ROWS - 1) / TILE_ROWS);
+    const size_t meta_ints = (size_t)c.max_request_rows + 1 + 2 * req_tiles * TILE_SLICES;
+    const size_t ns = (size_t)c.max_slots;
+    cudaError_t e = cudaSuccess;
+    auto dev = [&](void **q, size_t bytes) {
+        if (e == cudaSuccess)
+            e = cudaMalloc(q, std::max<size_t>(bytes, 16));
+    };
+    dev((void **)&P->sl_off, sizeof(int) * (nsl + 1));
+    dev((void **)&P->sl_w, sizeof(int) * nsl);
+    dev((void **)&P->rlen, sizeof(int) * rows);
+    dev((void **)&P->ci, sizeof(int) * (size_t)c.max_entries);
+    dev((void **)&P->va, sizeof(double) * (size_t)c.max_entries);
+    dev((void **)&P->tile_sys, sizeof(int) * (size_t)tiles);
+    dev((void **)&P->t0, sizeof(int) * ns);
+    dev((void **)&P->t1, sizeof(int) * ns);
+    dev((void **)&P->left, sizeof(int));
+    dev((void **)&P->flag, sizeof(int));
+    dev((void **)&P->bad, sizeof(int) * ns);
+    dev((void **)&P->lv_n, sizeof(int) * 2);
+    dev((void **)&P->lv_pre, sizeof(int) * (ns + 1));
+    dev((void **)&P->lv_t0, sizeof(int) * ns);
+    dev((void **)&P->st_meta, sizeof(int) * meta_ints);
+    dev((void **)&P->st_ci, sizeof(int) * (size_t)c.max_request_nnz);
+    dev((void **)&P->st_va, sizeof(double) * (size_t)c.max_request_nnz);
+    dev((void **)&P->hist, sizeof(double) * ns * (size_t)(c.maxit + 1));
+    dev((void **)&P->ctl, sizeof(Ctl) * ns);
+    dev((void **)&P->acc, sizeof(GAcc) * MAXD * ns);
+    dev((void **)&P->part, sizeof(double) * MAXD * (size_t)tiles);
+    dev((void **)&P->done, sizeof(unsigned) * ns);
+    for (auto &v : P->vec)
+        dev((void **)&v, sizeof(double) * rows);
+    for (auto &h : P->snap)
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&h, sizeof(Ctl) * ns);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&P->meta, sizeof(int) * meta_ints);
+    for (auto &ev : P->ev)
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&P->up_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&P->cstream, cudaStreamNonBlocking);
+    // zeroed state: every tile free, every slot final (skipped), accumulators empty
+    if (e == cudaSuccess)
+        e = cudaMemset(P->tile_sys, 0xff, sizeof(int) * (size_t)tiles);
+    if (e == cudaSuccess)
+        e = cudaMemset(P->sl_off, 0, sizeof(int) * (nsl + 1));
+    if (e == cudaSuccess)
+        e = cudaMemset(P->sl_w, 0, sizeof(int) * nsl);
+    if (e == cudaSuccess)
+        e = cudaMemset(P->rlen, 0, sizeof(int) * rows);
+    if (e == cudaSuccess)
+        e = cudaMemset(P->done, 0, sizeof(unsigned) * ns);
+    if (e == cudaSuccess)
+        e = cudaMemset(P->bad, 0, sizeof(int) * ns);
+    if (e == cudaSuccess)
+        e = cudaMemset(P->st_meta, 0, sizeof(int) * meta_ints);
+    for (auto &v : P->vec)
+        if (e == cudaSuccess)
+            e = cudaMemset(v, 0, sizeof(double) * rows);
+    if (e == cudaSuccess) {
+        std::vector<Ctl> hc(ns);
+        for (auto &q : hc) {
+            memset(&q, 0, sizeof q);
+            q.status = ST_FREE;
+        }
+        e = cudaMemcpy(P->ctl, hc.data(), sizeof(Ctl) * ns, cudaMemcpyHostToDevice);
+        std::vector<GAcc> ga(ns * MAXD);
+        for (auto &g : ga) {
+            memset(&g, 0, sizeof g);
+            g.kmin = NDIG;
+            g.kmax = -1;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->acc, ga.data(), sizeof(GAcc) * ga.size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        pool_release(P);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "pool: %s",
+                    cudaGetErrorString(e));
+    }
+    P->tiles.init(tiles);
+    P->entries.init(c.max_entries);
+    P->slots.assign(ns, PoolSlot());
+    int rc = pool_build_graph(ctx, P);
+    if (rc) {
+        pool_release(P);
+        return rc;
+    }
+    *out = P;
+    return 0;
+}
+
+void pbcg_pool_destroy(pbcg_pool *P)
+{
+    if (!P)
+        return;
+    cudaSetDevice(P->ctx->device);
+    cudaStreamSynchronize(P->ctx->stream);
+    cudaStreamSynchronize(P->cstream);
+    pool_release(P);
+}
+
+int pbcg_pool_admit(pbcg_pool *P, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                    const double *vals, const double *b, const double *x0, double tol, int32_t maxit, int32_t *slot)
+{
+    if (!P)
+        return PBCG_ERR_INVALID;
+    pbcg_ctx *ctx = P->ctx;
+    if (!slot || !row_ptr || !b || (nnz > 0 && (!col_idx || !vals)))
+        return fail(ctx, PBCG_ERR_INVALID, "NULL argument");
+    *slot = -1;
+    if (n < 1 || n > P->cfg.max_request_rows || nnz < 0 || nnz > P->cfg.max_request_nnz)
+        return fail(ctx, PBCG_ERR_INVALID, "request size n = %d, nnz = %lld beyond the pool's limits (%lld, %lld)",
+                    n, (long long)nnz, (long long)P->cfg.max_request_rows, (long long)P->cfg.max_request_nnz);
+    if (!(tol > 0.0) || maxit < 0 || maxit > P->cfg.maxit)
+        return fail(ctx, PBCG_ERR_INVALID, "tol must be > 0 and 0 <= maxit <= %d", P->cfg.maxit);
+    CK(cudaSetDevice(ctx->device));
+    const int ntl = (n + TILE_ROWS - 1) / TILE_ROWS, nsl = ntl * TILE_SLICES, rows = ntl * TILE_ROWS;
+    int *hrp = P->meta, *hw = P->meta + (n + 1), *hoff = hw + nsl;
+    {
+        // row pointers to the host without touching the legacy default stream
+        cudaPointerAttributes pa;
+        bool host = true;
+        if (cudaPointerGetAttributes(&pa, row_ptr) == cudaSuccess)
+            host = pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered;
+        else
+            cudaGetLastError();
+        if (host) {
+            memcpy(hrp, row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+        } else {
+            CK(cudaMemcpyAsync(hrp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDefault, P->cstream));
+            CK(cudaStreamSynchronize(P->cstream));
+        }
+    }
+    if (hrp[0] != 0)
+        return fail(ctx, PBCG_ERR_INVALID, "row_ptr[0] must be 0");
+    if ((int64_t)hrp[n] != nnz)
+        return fail(ctx, PBCG_ERR_INVALID, "row_ptr[n] = %d differs from nnz = %lld", hrp[n], (long long)nnz);
+    long long ne = 0;
+    for (int sl = 0; sl < nsl; sl++) {
+        int w = 0;
+        for (int i = sl * 32; i < std::min(sl * 32 + 32, n); i++) {
+            const int len = hrp[i + 1] - hrp[i];
+            if (len < 0)
+                return fail(ctx, PBCG_ERR_INVALID, "row_ptr decreases at row %d", i);
+            w = std::max(w, len);
+        }
+        hw[sl] = w;
+        hoff[sl] = (int)ne;
+        ne += 32ll * w;
+    }
+    // room: a free slot, a tile range and an entry range (1 = no room now)
+    int sid = -1;
+    for (int k = 0; k < P->cfg.max_slots; k++)
+        if (!P->slots[k].used) {
+            sid = k;
+            break;
+        }
+    if (sid < 0)
+        return 1;
+    const long long tA = P->tiles.take(ntl);
+    if (tA < 0)
+        return 1;
+    const long long eA = ne ? P->entries.take(ne) : 0;
+    if (eA < 0) {
+        P->tiles.give(tA, ntl);
+        return 1;
+    }
+    for (int sl = 0; sl < nsl; sl++)
+        hoff[sl] += (int)eA;
+    const int row0 = (int)tA * TILE_ROWS;
+    const size_t sl0 = (size_t)tA * TILE_SLICES;
+    cudaStream_t cs = P->cstream;
+    // uploads on the copy stream into ranges that no step reads
+    CK(cudaMemcpyAsync(P->st_meta, P->meta, sizeof(int) * ((size_t)n + 1 + 2 * (size_t)nsl), cudaMemcpyHostToDevice,
+                       cs));
+    CK(cudaMemcpyAsync(P->sl_w + sl0, P->st_meta + (n + 1), sizeof(int) * nsl, cudaMemcpyDeviceToDevice, cs));
+    CK(cudaMemcpyAsync(P->sl_off + sl0, P->st_meta + (n + 1) + nsl, sizeof(int) * nsl, cudaMemcpyDeviceToDevice, cs));
+    if (nnz) {
+        CK(cudaMemcpyAsync(P->st_ci, col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDefault, cs));
+        CK(cudaMemcpyAsync(P->st_va, vals, sizeof(double) * (size_t)nnz, cudaMemcpyDefault, cs));
+    }
+    CK(cudaMemsetAsync(P->bad + sid, 0, sizeof(int), cs));
+    {
+        int nn = n, nr = rows, r0 = row0;
+        const int *rp_d = P->st_meta, *ci_d = P->st_ci, *so = P->sl_off + sl0, *sw = P->sl_w + sl0;
+        const double *va_d = P->st_va;
+        int *rl = P->rlen, *co = P->ci, *bd = P->bad + sid;
+        double *vo = P->va;
+        void *args[] = {&nn, &nr, &r0, (void *)&rp_d, (void *)&ci_d, (void *)&va_d, (void *)&so, (void *)&sw,
+                        &rl, &co, &vo, &bd};
+        const int g = std::min((rows + 255) / 256, ctx->num_sms * 8);
+        CK(cudaLaunchKernel((void *)k_pool_scatter, dim3(g), dim3(256), args, 0, cs));
+    }
+    CK(cudaMemsetAsync(P->vec[V_B] + row0, 0, sizeof(double) * rows, cs));
+    CK(cudaMemsetAsync(P->vec[V_X] + row0, 0, sizeof(double) * rows, cs));
+    CK(cudaMemcpyAsync(P->vec[V_B] + row0, b, sizeof(double) * n, cudaMemcpyDefault, cs));
+    if (x0)
+        CK(cudaMemcpyAsync(P->vec[V_X] + row0, x0, sizeof(double) * n, cudaMemcpyDefault, cs));
+    CK(cudaEventRecord(P->up_ev, cs));
+    // the slot goes live on the solve stream once its uploads are in
+    CK(cudaStreamWaitEvent(ctx->stream, P->up_ev, 0));
+    PoolSlot &S = P->slots[sid];
+    S = PoolSlot();
+    S.used = true;
+    S.gen = P->next_gen++;
+    S.tile0 = (int)tA;
+    S.ntiles = ntl;
+    S.n = n;
+    S.e0 = eA;
+    S.ne = ne;
+    Ctl init;
+    memset(&init, 0, sizeof init);
+    init.maxit = maxit;
+    init.status = ST_SETUP1;
+    init.tol = tol;
+    init.target = tol;
+    init.alg = (P->cfg.alg == PBCG_ALG_BICGSTAB) ? ALG_BICGSTAB : ALG_PIPELINED;
+    init.rr_period = (P->cfg.alg == PBCG_ALG_PIPELINED_RR) ? ctx->rr_period : 0;
+    init.hist = P->hist + (size_t)sid * (size_t)(P->cfg.maxit + 1);
+    init.hist_cap = P->cfg.maxit + 1;
+    init.trueres = __builtin_nan("");
+    init.gen = S.gen;
+    {
+        int *ts = P->tile_sys, *a0 = P->t0, *a1 = P->t1;
+        Ctl *cl = P->ctl;
+        int s_ = sid, t_ = (int)tA, k_ = ntl;
+        const int *bd = P->bad;
+        void *args[] = {&ts, &a0, &a1, &cl, &s_, &t_, &k_, &init, (void *)&bd};
+        CK(cudaLaunchKernel((void *)k_pool_activate, dim3(1), dim3(256), args, 0, ctx->stream));
+    }
+    // the caller's arrays and the pinned row pointers are consumed when this returns
+    CK(cudaStreamSynchronize(cs));
+    *slot = sid;
+    return 0;
+}
+
+int pbcg_pool_step(pbcg_pool *P, int32_t iters)
+{
+    if (!P)
+        return PBCG_ERR_INVALID;
+    pbcg_ctx *ctx = P->ctx;
+    if (iters < 1)
+        return fail(ctx, PBCG_ERR_INVALID, "iters must be >= 1");
+    CK(cudaSetDevice(ctx->device));
+    const int k = (int)(P->issued % POOL_RING);
+    // the snapshot buffer about to be reused must not still be in flight
+    CK(cudaEventSynchronize(P->ev[k]));
+    {
+        int *l = P->left;
+        int it = iters;
+        void *args[] = {&l, &it};
+        CK(cudaLaunchKernel((void *)k_pool_arm, dim3(1), dim3(1), args, 0, ctx->stream));
+    }
+    CK(cudaGraphLaunch(P->exec, ctx->stream));
+    CK(cudaMemcpyAsync(P->snap[k], P->ctl, sizeof(Ctl) * (size_t)P->cfg.max_slots, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaEventRecord(P->ev[k], ctx->stream));
+    P->issued++;
+    return 0;
+}
+
+int pbcg_pool_poll(pbcg_pool *P, int wait, int32_t *done_slots, int32_t cap, int32_t *count, int32_t *pending)
+{
+    if (!P)
+        return PBCG_ERR_INVALID;
+    pbcg_ctx *ctx = P->ctx;
+    if (!count || cap < 0 || (cap > 0 && !done_slots))
+        return fail(ctx, PBCG_ERR_INVALID, "bad output arguments");
+    CK(cudaSetDevice(ctx->device));
+    *count = 0;
+    long long newest = -1;
+    const long long lo = std::max(0ll, P->issued - POOL_RING);
+    for (long long j = P->issued - 1; j >= lo; --j) {
+        cudaEvent_t ev = P->ev[j % POOL_RING];
+        if (wait && j == P->issued - 1)
+            CK(cudaEventSynchronize(ev));
+        cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaSuccess) {
+            newest = j;
+            break;
+        }
+        if (q != cudaErrorNotReady)
+            CK(q);
+    }
+    if (pending)
+        *pending = (int32_t)(P->issued - 1 - newest);
+    if (newest < 0)
+        return 0;
+    const Ctl *sn = P->snap[newest % POOL_RING];
+    int k = 0;
+    for (int s = 0; s < P->cfg.max_slots; s++) {
+        PoolSlot &S = P->slots[s];
+        if (!S.used || S.reported || sn[s].gen != S.gen || !final_status(sn[s]))
+            continue;
+        S.reported = true;
+        S.last = sn[s];
+        if (k < cap)
+            done_slots[k] = s;
+        k++;
+    }
+    *count = k;
+    return 0;
+}
+
+int pbcg_pool_result(pbcg_pool *P, int32_t slot, double *x, pbcg_result *out)
+{
+    if (!P)
+        return PBCG_ERR_INVALID;
+    pbcg_ctx *ctx = P->ctx;
+    if (slot < 0 || slot >= P->cfg.max_slots || !P->slots[slot].used || !P->slots[slot].reported)
+        return fail(ctx, PBCG_ERR_INVALID, "slot %d has no finished request", slot);
+    CK(cudaSetDevice(ctx->device));
+    PoolSlot &S = P->slots[slot];
+    // a finished slot's rows are no longer written: copy without waiting for running steps
+    if (x) {
+        CK(cudaMemcpyAsync(x, P->vec[V_X] + (size_t)S.tile0 * TILE_ROWS, sizeof(double) * (size_t)S.n,
+                           cudaMemcpyDefault, P->cstream));
+        CK(cudaStreamSynchronize(P->cstream));
+    }
+    const Ctl &c = S.last;
+    const bool timeout = c.status == ST_TIMEOUT || c.err;
+    const bool invalid = c.status == ST_INVALID;
+    if (out) {
+        out->iters = c.it;
+        out->status = timeout ? PBCG_ERR_TIMEOUT : invalid ? PBCG_ERR_INVALID : c.status;
+        out->relres_recursive = c.res;
+        out->relres_true = c.trueres;
+        out->seconds = 0.0;
+        out->launches = 0;
+        out->reserved = 0;
+    }
+    // retire: the tiles leave the sweep (ordered after running steps), the ranges return
+    {
+        int *ts = P->tile_sys;
+        int t_ = S.tile0, k_ = S.ntiles;
+        void *args[] = {&ts, &t_, &k_};
+        CK(cudaLaunchKernel((void *)k_pool_clear, dim3(1), dim3(256), args, 0, ctx->stream));
+    }
+    P->tiles.give(S.tile0, S.ntiles);
+    P->entries.give(S.e0, S.ne);
+    S = PoolSlot();
+    if (timeout)
+        return fail(ctx, PBCG_ERR_TIMEOUT, "a bounded device wait expired");
+    if (invalid)
+        return fail(ctx, PBCG_ERR_INVALID, "request in slot %d has a column index outside [0, n)", slot);
+    return c.status;
+}
+
+int pbcg_pool_history(pbcg_pool *P, int32_t slot, double *out, int32_t cap, int32_t *len)
+{
+    if (!P)
+        return PBCG_ERR_INVALID;
+    pbcg_ctx *ctx = P->ctx;
+    if (slot < 0 || slot >= P->cfg.max_slots || !P->slots[slot].used || !P->slots[slot].reported)
+        return fail(ctx, PBCG_ERR_INVALID, "slot %d has no finished request", slot);
+    CK(cudaSetDevice(ctx->device));
+    const Ctl &c = P->slots[slot].last;
+    const int32_t L = c.status == ST_INVALID ? 0 : std::min(c.it + 1, P->cfg.maxit + 1);
+    if (len)
+        *len = L;
+    if (out && cap > 0 && L > 0) {
+        CK(cudaMemcpyAsync(out, P->hist + (size_t)slot * (size_t)(P->cfg.maxit + 1),
+                           sizeof(double) * (size_t)std::min(cap, L), cudaMemcpyDeviceToHost, P->cstream));
+        CK(cudaStreamSynchronize(P->cstream));
+    }
+    return 0;
+}
+
+int pbcg_pool_room(const pbcg_pool *P, int32_t *free_slots, int64_t *free_rows, int64_t *free_entries)
+{
+    if (!P)
+        return PBCG_ERR_INVALID;
+    int fs = 0;
+    for (auto &S : P->slots)
+        fs += !S.used;
+    if (free_slots)
+        *free_slots = fs;
+    if (free_rows)
+        *free_rows = P->tiles.largest() * TILE_ROWS;
+    if (free_entries)
+        *free_entries = P->entries.largest();
+    return 0;
 }
 
 }  // extern "C"

@@ -20,12 +20,17 @@ namespace pbcg {
 struct Batch {
     int nsys, ntiles;
     const int *__restrict__ tile_sys;    // [ntiles] system of each tile
-    const int *__restrict__ sys_t0;      // [nsys + 1] first tile of each system
+    const int *__restrict__ sys_t0;      // [nsys] first tile of each system
+    const int *__restrict__ sys_t1;      // [nsys] end tile of each system
     Ctl *ctl;                            // [nsys]
     GAcc *acc;                           // [nsys * MAXD]
     double *part;                        // [ntiles * MAXD] plain partial of the flush group starting at a tile
     unsigned *done;                      // [nsys] tiles merged in the current pass
     int *flag;                           // [1] loop condition scratch
+    // pools only (NULL otherwise): the tiles of the live systems, listed system by
+    // system: lv_n = {live systems, live tiles}; live system j owns list entries
+    // [lv_pre[j], lv_pre[j+1]), which are tiles lv_t0[j], lv_t0[j] + 1, ...
+    const int *lv_n, *lv_pre, *lv_t0;
 };
 
 // ---------------------------------------------------------------------------
@@ -64,7 +69,7 @@ __device__ __forceinline__ void b_flush(DotSet<ND, MODE> &D, Shm<ND> &sh, const 
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned need = (unsigned)(B.sys_t0[sys + 1] - B.sys_t0[sys]);
+        const unsigned need = (unsigned)(B.sys_t1[sys] - B.sys_t0[sys]);
         const unsigned old = atomicAdd(&B.done[sys], (unsigned)cnt);
         sh.last = (old + (unsigned)cnt == need);
     }
@@ -77,7 +82,7 @@ __device__ __forceinline__ void b_flush(DotSet<ND, MODE> &D, Shm<ND> &sh, const 
                 sh.dv[threadIdx.x] = gacc_round_reset(&g[threadIdx.x], sh.scratch[threadIdx.x]);
         } else if (warp < ND) {
             // partials of the system's flush groups, in tile order (non-first tiles hold +0)
-            const int t0 = B.sys_t0[sys], t1 = B.sys_t0[sys + 1];
+            const int t0 = B.sys_t0[sys], t1 = B.sys_t1[sys];
             double v = 0.0;
             for (int t = t0 + lane; t < t1; t += 32)
                 v = __dadd_rn(v, __ldcg(B.part + (size_t)t * MAXD + warp));
@@ -115,8 +120,30 @@ __global__ void __launch_bounds__(THREADS) k_batched(Mat A, Vecs V, Batch B)
     int cur = -1, t_first = -1, cnt = 0;
     bool run = false;
     typename Step::Scal S;
-    for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+    const bool listed = B.lv_n != nullptr;
+    const int nq = listed ? B.lv_n[1] : B.ntiles;
+    int j = 0;
+    if (listed && (int)blockIdx.x < nq) {
+        int lo = 0, hi = B.lv_n[0] - 1;           // last live system with lv_pre[j] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.lv_pre[mid] <= (int)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+        int t = q;
+        if (listed) {
+            while (B.lv_pre[j + 1] <= q)
+                j++;
+            t = B.lv_t0[j] + (q - B.lv_pre[j]);
+        }
         const int sys = B.tile_sys[t];
+        if (sys < 0)
+            continue;                    // unallocated tile of a pool
         if (sys != cur) {
             if (cur >= 0 && cnt > 0) {
                 b_flush<ND, MODE, Step>(D, sh, B, cur, t_first, cnt, V);
@@ -547,6 +574,167 @@ struct StepTrueRes {
         }
     }
 };
+
+// ---------------------------------------------------------------------------
+// pool (continuous batching): slots are admitted in state ST_SETUP1 between
+// steps and go through the setup passes inside the step loop
+// ---------------------------------------------------------------------------
+struct PoolSetup1 : StepSetup1 {
+    static __device__ bool wants(const Ctl *c) { return c->status == ST_SETUP1; }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        c->bb = dv[0];
+        c->rho = dv[1];
+        if (c->alg == ALG_BICGSTAB)
+            setup_scalar(c, dv[0], dv[1], 0.0);
+        else
+            c->status = ST_SETUP2;
+    }
+};
+
+struct PoolSetup2 : StepSetup2 {
+    static __device__ bool wants(const Ctl *c) { return c->status == ST_SETUP2; }
+    static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
+    {
+        setup_scalar(c, c->bb, c->rho, dv[0]);
+        c->need_t = 1;
+    }
+};
+
+struct PoolSetup3 : StepSetup3 {
+    static __device__ bool wants(const Ctl *c) { return c->need_t == 1; }
+    static __device__ void fin(Ctl *c, const double *, const Vecs &) { c->need_t = 0; }
+};
+
+// step control of a pool (one CTA of 1024 threads): lists the tiles of the
+// slots that are still live for the next iteration (in slot order, so that a
+// CTA meets each system in one run of consecutive list entries) and, unless
+// `first`, counts down `left` and sets the loop condition
+__device__ __forceinline__ bool pool_live(const Ctl &c)
+{
+    const int st = c.status;
+    return st == ST_RUNNING || st == ST_CANDIDATE || st == ST_SETUP1 || st == ST_SETUP2 || c.need_t == 1;
+}
+
+__global__ void __launch_bounds__(1024) k_pool_ctl(Batch B, int *lv_n, int *lv_pre, int *lv_t0, int *left,
+                                                   unsigned long long handle, int first)
+{
+    __shared__ unsigned long long wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int C = (B.nsys + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int s0 = min(tid * C, B.nsys), s1 = min(s0 + C, B.nsys);
+    // (systems, tiles) of this thread's slots, packed as systems << 32 | tiles
+    unsigned long long v = 0;
+    for (int s = s0; s < s1; s++)
+        if (pool_live(B.ctl[s]))
+            v += (1ull << 32) | (unsigned long long)(B.sys_t1[s] - B.sys_t0[s]);
+    unsigned long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o)
+            inc += u;
+    }
+    if (lane == 31)
+        wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)blockDim.x >> 5;
+        unsigned long long w = lane < nw ? wsum[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o)
+                w += u;
+        }
+        if (lane < nw)
+            wsum[lane] = w;                       // inclusive over warps
+    }
+    __syncthreads();
+    unsigned long long ex = inc - v + (warp > 0 ? wsum[warp - 1] : 0ull);
+    int js = (int)(ex >> 32), ts = (int)(ex & 0xffffffffull);
+    for (int s = s0; s < s1; s++) {
+        if (pool_live(B.ctl[s])) {
+            lv_t0[js] = B.sys_t0[s];
+            lv_pre[js] = ts;
+            ts += B.sys_t1[s] - B.sys_t0[s];
+            js++;
+        }
+    }
+    if (tid == (int)blockDim.x - 1) {
+        const unsigned long long tot = wsum[((int)blockDim.x >> 5) - 1];
+        const int nl = (int)(tot >> 32), nt = (int)(tot & 0xffffffffull);
+        lv_pre[nl] = nt;
+        lv_n[0] = nl;
+        lv_n[1] = nt;
+        if (!first) {
+            const int l = *left - 1;
+            *left = l;
+            cudaGraphSetConditional((cudaGraphConditionalHandle)handle, (nl > 0 && l > 0) ? 1u : 0u);
+        }
+    }
+}
+
+// admission of a request into a pool slot: its CSR rows (staged in device
+// memory, rows in caller order) into the slot's SELL-32 entries.  nrows = the
+// slot's whole tiles; slices sl_off / sl_w are the slot's own.  A column
+// outside [0, n) raises *bad and is stored as column 0 with value 0.
+__global__ void k_pool_scatter(int n, int nrows, int row0, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const double *__restrict__ va, const int *__restrict__ sl_off,
+                               const int *__restrict__ sl_w, int *rlen, int *ci_out, double *va_out, int *bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
+        const int sl = i >> 5;
+        const long long base = (long long)sl_off[sl] + (i & 31);
+        const int w = sl_w[sl];
+        int k0 = 0, len = 0;
+        if (i < n) {
+            k0 = rp[i];
+            len = rp[i + 1] - k0;
+        }
+        rlen[row0 + i] = len;
+        for (int j = 0; j < w; j++) {
+            int c = 0;
+            double v = 0.0;
+            if (j < len) {
+                c = ci[k0 + j];
+                v = va[k0 + j];
+                if (c < 0 || c >= n) {
+                    *bad = 1;
+                    c = 0;
+                    v = 0.0;
+                }
+            }
+            ci_out[base + 32ll * j] = row0 + c;
+            va_out[base + 32ll * j] = v;
+        }
+    }
+}
+
+// a slot joins the sweep: its tiles, its tile range and its control block
+__global__ void k_pool_activate(int *tile_sys, int *sys_t0, int *sys_t1, Ctl *ctl, int sid, int t0, int ntl,
+                                Ctl init, const int *bad)
+{
+    for (int t = threadIdx.x; t < ntl; t += blockDim.x)
+        tile_sys[t0 + t] = sid;
+    if (threadIdx.x == 0) {
+        sys_t0[sid] = t0;
+        sys_t1[sid] = t0 + ntl;
+        if (bad[sid])
+            init.status = ST_INVALID;
+        ctl[sid] = init;
+    }
+}
+
+// a retired slot's tiles leave the sweep
+__global__ void k_pool_clear(int *tile_sys, int t0, int ntl)
+{
+    for (int t = threadIdx.x; t < ntl; t += blockDim.x)
+        tile_sys[t0 + t] = -1;
+}
+
+__global__ void k_pool_arm(int *left, int iters)
+{
+    *left = iters;
+}
 
 // loop condition of a batched solve: some system still running or awaiting its true-residual check
 __global__ void k_batch_ctl(Batch B, unsigned long long handle, int use_cond)

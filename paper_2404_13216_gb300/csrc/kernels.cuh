@@ -43,7 +43,7 @@ constexpr int WARPS = THREADS / 32;
 constexpr int MAXD = 4;                 // most dots merged in one pass
 constexpr int UNR = PBCG_UNR;
 
-enum : int { ST_RUNNING = 100, ST_CANDIDATE = 101, ST_TIMEOUT = 200 };
+enum : int { ST_RUNNING = 100, ST_CANDIDATE = 101, ST_SETUP1 = 110, ST_SETUP2 = 111, ST_FREE = 120, ST_INVALID = 130, ST_TIMEOUT = 200 };
 enum : int { PH_SETUP = 0, PH_ITER = 1 };
 enum : int { ALG_BICGSTAB = 0, ALG_PIPELINED = 1 };
 
@@ -58,7 +58,8 @@ struct Ctl {
     int alg, use_cond, err, rr_period;  // err: a bounded device wait expired; rr_period: 0 = no replacement
     unsigned long long cond;            // cudaGraphConditionalHandle of the loop
     double *hist;
-    int hist_cap, pad_i2;
+    int hist_cap, need_t;               // need_t: t0 = A w0 still to be formed (pool slots)
+    int gen, pad_i;                     // gen: admission number of a pool slot's occupant
 };
 
 // grid-wide merge workspace
@@ -77,6 +78,7 @@ struct Mat {
     const int *__restrict__ rlen;        // [nslices * 32] row lengths (0 past n)
     const int *__restrict__ ci;          // padded column indices (solver order)
     const double *__restrict__ va;       // padded values
+    const int *__restrict__ sl_w;        // [nslices] slice widths, or NULL: width = (sl_off[s+1] - sl_off[s]) / 32
     const int *__restrict__ lci;         // padded local indices into a tile's staged blocks (or NULL)
     const int *__restrict__ tblk;        // [ntiles * GMAX] 256-row blocks each tile gathers from, -1 pad;
                                          // tblk[t * GMAX] == -1: the tile gathers from global memory
@@ -130,7 +132,7 @@ __device__ __forceinline__ RowRef row_ref(const Mat &A, int s, int lane)
 {
     RowRef R;
     R.base = __ldg(A.sl_off + s);
-    R.width = (__ldg(A.sl_off + s + 1) - R.base) >> 5;
+    R.width = A.sl_w ? __ldg(A.sl_w + s) : (__ldg(A.sl_off + s + 1) - R.base) >> 5;
     R.len = __ldg(A.rlen + s * 32 + lane);
     R.base += lane;
     return R;

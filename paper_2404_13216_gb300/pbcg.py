@@ -24,13 +24,21 @@ PLAIN, EXACT = 0, 1
 
 EXPORTS = ("pbcg_create", "pbcg_destroy", "pbcg_last_error", "pbcg_csr_upload", "pbcg_mat_free",
            "pbcg_solve", "pbcg_solve_batched", "pbcg_residual_history", "pbcg_dot", "pbcg_spmv",
-           "pbcg_profile_solve", "pbcg_dot_noalloc", "pbcg_set_option")
+           "pbcg_profile_solve", "pbcg_dot_noalloc", "pbcg_set_option", "pbcg_pool_create", "pbcg_pool_destroy",
+           "pbcg_pool_admit", "pbcg_pool_step", "pbcg_pool_poll", "pbcg_pool_result", "pbcg_pool_history",
+           "pbcg_pool_room")
 
 
 class PbcgError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"pbcg error {code}: {msg}")
         self.code = code
+
+
+class _PoolConfig(ctypes.Structure):
+    _fields_ = [("max_rows", ctypes.c_int64), ("max_entries", ctypes.c_int64), ("max_slots", ctypes.c_int32),
+                ("maxit", ctypes.c_int32), ("alg", ctypes.c_int32), ("dot_mode", ctypes.c_int32),
+                ("max_request_rows", ctypes.c_int64), ("max_request_nnz", ctypes.c_int64)]
 
 
 class _Result(ctypes.Structure):
@@ -72,6 +80,22 @@ def load_library(path: str = LIB_PATH):
     lib.pbcg_set_option.argtypes = [P, ctypes.c_int, i64]
     lib.pbcg_set_option.restype = ctypes.c_int
     lib.pbcg_dot_noalloc.restype = ctypes.c_int
+    lib.pbcg_pool_create.argtypes = [P, ctypes.POINTER(_PoolConfig), ctypes.POINTER(P)]
+    lib.pbcg_pool_create.restype = ctypes.c_int
+    lib.pbcg_pool_destroy.argtypes = [P]
+    lib.pbcg_pool_destroy.restype = None
+    lib.pbcg_pool_admit.argtypes = [P, i32, i64, P, P, P, P, P, d, i32, ctypes.POINTER(i32)]
+    lib.pbcg_pool_admit.restype = ctypes.c_int
+    lib.pbcg_pool_step.argtypes = [P, i32]
+    lib.pbcg_pool_step.restype = ctypes.c_int
+    lib.pbcg_pool_poll.argtypes = [P, ctypes.c_int, P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.pbcg_pool_poll.restype = ctypes.c_int
+    lib.pbcg_pool_result.argtypes = [P, i32, P, ctypes.POINTER(_Result)]
+    lib.pbcg_pool_result.restype = ctypes.c_int
+    lib.pbcg_pool_history.argtypes = [P, i32, P, i32, ctypes.POINTER(i32)]
+    lib.pbcg_pool_history.restype = ctypes.c_int
+    lib.pbcg_pool_room.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.pbcg_pool_room.restype = ctypes.c_int
     return lib
 
 
@@ -227,3 +251,91 @@ class Context:
         for i in range(min(k.value, cap)):
             prof[bytes(names[i]).split(b"\0")[0].decode()] = (float(ms[i]), int(cnt[i]))
         return Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds, r.launches), prof
+
+
+def sell_entries(row_ptr) -> int:
+    """SELL-32 entries a system takes in a pool: 32 x the longest row of each 32-row slice."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    n = rp.size - 1
+    ln = np.zeros(((n + 31) // 32) * 32, dtype=np.int64)
+    ln[:n] = np.diff(rp)
+    return int(32 * ln.reshape(-1, 32).max(axis=1).sum())
+
+
+class Pool:
+    """A pbcg_pool: continuous batching of independent solves on one context.
+
+    admit() returns a slot or None when the pool has no room now; step()
+    enqueues K iterations of every live system; poll() returns the slots that
+    finished (each once); result() retires a slot and returns (x, Result)."""
+
+    def __init__(self, ctx: Context, max_rows: int, max_entries: int, max_slots: int, maxit: int,
+                 alg: int = PIPELINED, mode: int = EXACT, max_request_rows: int = None,
+                 max_request_nnz: int = None):
+        cfg = _PoolConfig(int(max_rows), int(max_entries), int(max_slots), int(maxit), int(alg), int(mode),
+                          int(max_request_rows or max_rows), int(max_request_nnz or max_entries))
+        h = ctypes.c_void_p()
+        ctx._check(_lib.pbcg_pool_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.ctx, self.handle, self.max_slots = ctx, h, int(max_slots)
+        self.sizes = {}
+        self._buf = np.zeros(self.max_slots, dtype=np.int32)
+
+    def close(self):
+        if self.handle:
+            _lib.pbcg_pool_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def admit(self, A, b, x0=None, tol: float = 1e-8, maxit: int = 1000):
+        rp, ci, va = _host(A.row_ptr, np.int32), _host(A.col_idx, np.int32), _host(A.vals, np.float64)
+        b = _host(b, np.float64)
+        x0 = None if x0 is None else _host(x0, np.float64)
+        n = (rp.numel() if hasattr(rp, "numel") else rp.size) - 1
+        nnz = va.numel() if hasattr(va, "numel") else va.size
+        slot = ctypes.c_int32(-1)
+        rc = self.ctx._check(_lib.pbcg_pool_admit(self.handle, n, nnz, _ptr(rp), _ptr(ci), _ptr(va), _ptr(b),
+                                                  _ptr(x0), float(tol), int(maxit), ctypes.byref(slot)))
+        if rc == 1:
+            return None
+        self.sizes[slot.value] = n
+        return slot.value
+
+    def step(self, iters: int):
+        self.ctx._check(_lib.pbcg_pool_step(self.handle, int(iters)))
+
+    def poll(self, wait: bool = False):
+        """(finished slots, steps still in flight)."""
+        cnt, pend = ctypes.c_int32(0), ctypes.c_int32(0)
+        self.ctx._check(_lib.pbcg_pool_poll(self.handle, int(bool(wait)), _ptr(self._buf), self.max_slots,
+                                            ctypes.byref(cnt), ctypes.byref(pend)))
+        return [int(v) for v in self._buf[:min(cnt.value, self.max_slots)]], pend.value
+
+    def history(self, slot: int) -> np.ndarray:
+        ln = ctypes.c_int32(0)
+        self.ctx._check(_lib.pbcg_pool_history(self.handle, int(slot), None, 0, ctypes.byref(ln)))
+        out = np.empty(ln.value, dtype=np.float64)
+        self.ctx._check(_lib.pbcg_pool_history(self.handle, int(slot), _ptr(out), ln.value, ctypes.byref(ln)))
+        return out
+
+    def result(self, slot: int, x=None):
+        """Retire `slot`: (x, Result).  A request that failed (bad column
+        index, device wait expired) gives a Result with its negative code."""
+        if x is None:
+            x = np.empty(self.sizes[slot], dtype=np.float64)
+        r = _Result()
+        rc = _lib.pbcg_pool_result(self.handle, int(slot), _ptr(x), ctypes.byref(r))
+        if rc < 0 and r.status >= 0:
+            raise PbcgError(rc, self.ctx.last_error())
+        self.sizes.pop(slot, None)
+        return x, Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds, r.launches)
+
+    def room(self):
+        """(free slots, largest free row range, largest free entry range)."""
+        fs, fr, fe = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        self.ctx._check(_lib.pbcg_pool_room(self.handle, ctypes.byref(fs), ctypes.byref(fr), ctypes.byref(fe)))
+        return fs.value, fr.value, fe.value
