@@ -254,6 +254,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = run_batched_leg(ctx, pbcg, torch, dev)
+    serving = None
+    if not args.no_serving and ws == 1:
+        serving = run_serving_leg(requests=args.serving_requests)
     x_d.zero_()
     _, prof_e = ctx.profile_solve(M, b_d, x_d, TOL, MAXIT, pbcg.PIPELINED, pbcg.EXACT)
     x_d.zero_()
@@ -338,6 +341,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * n + 8 * (res_h.iters + 1), "steps": steps_h},
         "clocks": clocks,
         "batched": batched,
+        "serving": serving,
         "gpu_launches": launches_e,
     }
     print(json.dumps(line), flush=True)
@@ -403,6 +407,26 @@ def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, mode
             "identical_iterations_to_single_solves": bool(same_iters)}
 
 
+def run_serving_leg(requests=1000, rate=2000.0, templates=64, K=8, maxit=2000):
+    """Config 5: an open-loop Poisson stream of solves (2D/3D convection-diffusion,
+    n log-uniform 4k..1M, tol 1e-8 or 1e-10, exact or plain dots) through two
+    pools (exact, plain) with continuous batching; latency = arrival to result."""
+    from paper_2404_13216_gb300 import inputs, pbcg, serve
+    reqs = inputs.serving_requests(count=requests, rate=rate, seed=5)
+    tmpl = serve.make_templates(reqs, templates)
+    ce, cp = pbcg.Context(0), pbcg.Context(0)
+    pools = serve.make_pools(ce, cp, tmpl, 48 << 20, 384 << 20, 512, maxit, pbcg.PIPELINED)
+    out = serve.serve(reqs, tmpl, pools, K=K, maxit=maxit)
+    summary = serve.summarize(reqs, tmpl, out, rate)
+    summary.update({"iters_per_step": K, "maxit_limit": maxit, "alg": "p-BiCGStab",
+                    "pool": {"max_rows": 48 << 20, "max_entries": 384 << 20, "max_slots": 512}})
+    for p in pools.values():
+        p.close()
+    ce.close()
+    cp.close()
+    return summary
+
+
 def source_sha() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -442,6 +466,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)

@@ -149,7 +149,8 @@ def summarize(reqs, templates, out, rate):
         "solves_per_s": float(ok.sum() / out["wall"]), "wall_s": out["wall"],
         "p50_ms": percentile(lat[ok] * 1e3, 50), "p99_ms": percentile(lat[ok] * 1e3, 99),
         "converged": int((st == 0).sum()), "maxit": int((st == 1).sum()), "breakdown": int((st == 2).sum()),
-        "nonfinite": int((st == 3).sum()), "failed": int((st < 0).sum()),
+        "nonfinite": int((st == 3).sum()), "rejected": int((st == REJECTED).sum()),
+        "failed": int(((st < 0) & (st != REJECTED)).sum()),
         "mean_iters": float(out["iters"][ok].mean()) if ok.any() else None,
         "mean_n": float(ns.mean()), "templates": len(templates),
         "exact_share": float(np.mean([r.exact for r in reqs])), "steps": out["steps"],
