@@ -254,6 +254,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = run_batched_leg(ctx, pbcg, torch, dev)
+    configs = None
+    if not args.no_configs:
+        configs = run_config_legs(ctx, pbcg, torch, dev, peaks()[0])
     serving = None
     if not args.no_serving and ws == 1:
         serving = run_serving_leg(requests=args.serving_requests)
@@ -342,6 +345,7 @@ def run_ours(args):
         "clocks": clocks,
         "batched": batched,
         "serving": serving,
+        "configs": configs,
         "gpu_launches": launches_e,
     }
     print(json.dumps(line), flush=True)
@@ -407,6 +411,60 @@ def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, mode
             "identical_iterations_to_single_solves": bool(same_iters)}
 
 
+def time_solve(ctx, M, b_d, x_d, tol, maxit, alg, mode, torch, dev, reps=1):
+    """One warm-up solve, then `reps` timed solves from x0 = 0 (CUDA events on
+    the library's stream); returns (ms per solve, last result)."""
+    stream = torch.cuda.current_stream(dev)
+    x_d.zero_()
+    ctx.solve(M, b_d, x_d, tol, maxit, alg, mode)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        x_d.zero_()
+        res = ctx.solve(M, b_d, x_d, tol, maxit, alg, mode)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps, res
+
+
+def run_config_legs(ctx, pbcg, torch, dev, peak):
+    """The other configurations and algorithms: the 64^2 system (L2-resident,
+    latency-bound), BiCGStab and p-BiCGStabRR on the 128^3 system, and the
+    power-law matrix (n = 2^22)."""
+    from paper_2404_13216_gb300 import inputs
+    out = {}
+
+    def leg(A, alg, mode, tol, maxit, reps, vec_reads):
+        M = ctx.upload_csr(A)
+        b_d = torch.from_numpy(inputs.rhs_ones(A)).to(dev)
+        x_d = torch.zeros(A.n, dtype=torch.float64, device=dev)
+        ms, res = time_solve(ctx, M, b_d, x_d, tol, maxit, alg, mode, torch, dev, reps)
+        M.free()
+        us_it = 1e3 * ms / max(res.iters, 1)
+        by = 2 * A.matrix_bytes() + vec_reads * 8 * A.n
+        return {"iters": res.iters, "status": res.status, "relres_true": res.relres_true,
+                "ms_per_solve": ms, "us_per_iter": us_it, "bytes_per_iter": by,
+                "hbm_gbs": by / (us_it * 1e-6) / 1e9, "frac_of_measured_hbm": by / (us_it * 1e-6) / 1e9 / peak}
+
+    A = inputs.convdiff2d(64, 10.0)
+    for alg, name in ((pbcg.PIPELINED, "pbicgstab"), (pbcg.BICGSTAB, "bicgstab")):
+        for mode, mn in ((pbcg.EXACT, "exact"), (pbcg.PLAIN, "plain")):
+            out[f"convdiff64_{name}_{mn}"] = leg(A, alg, mode, 1e-8, 2000, 20, 23 if alg else 17)
+    A = inputs.convdiff3d(N_SIDE, PECLET, WIND)
+    for mode, mn in ((pbcg.EXACT, "exact"), (pbcg.PLAIN, "plain")):
+        out[f"convdiff128_bicgstab_{mn}"] = leg(A, pbcg.BICGSTAB, mode, 1e-300, 300, 1, 17)
+    ctx.set_option(pbcg.OPT_RR_PERIOD, 50)
+    out["convdiff128_pbicgstab_rr50_exact"] = leg(A, pbcg.PIPELINED_RR, pbcg.EXACT, TOL, MAXIT, 1, 23)
+    A = inputs.powerlaw()
+    for mode, mn in ((pbcg.EXACT, "exact"), (pbcg.PLAIN, "plain")):
+        out[f"powerlaw_pbicgstab_{mn}"] = leg(A, pbcg.PIPELINED, mode, 1e-300, 100, 1, 23)
+    out["notes"] = ("us_per_iter = solve time / iterations (setup and the true-residual check included); "
+                    "bytes_per_iter = 2M + 23V (p-BiCGStab) or 2M + 17V (BiCGStab); the 64^2 system is "
+                    "L2-resident, so its GB/s is not an HBM figure; tol 1e-300 runs exactly maxit iterations")
+    return out
+
+
 def run_serving_leg(requests=1000, rate=2000.0, templates=64, K=8, maxit=2000):
     """Config 5: an open-loop Poisson stream of solves (2D/3D convection-diffusion,
     n log-uniform 4k..1M, tol 1e-8 or 1e-10, exact or plain dots) through two
@@ -467,6 +525,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other-configuration legs")
     ap.add_argument("--serving-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.ncu_case:

@@ -61,7 +61,7 @@ struct pbcg_mat {
     double *va;            // [padded]
     int *perm;             // [n] solver row p holds caller row perm[p]; NULL when rows keep their order
     int *lci;              // [padded] entry indices into a tile's staged gather blocks
-    int *tblk;             // [ntiles * GMAX] gather blocks of each tile (-1: none / too many)
+    int *tmeta;            // [ntiles * TMETA] per tile: first and end entry, gather blocks (-1: none / too many)
     bool narrow;           // every 256-row tile spans at most MCAP SELL entries (staged in shared memory)
     std::vector<int32_t> h_rp, h_ci;   // host copy of the CSR (for per-batch layouts)
     std::vector<double> h_va;
@@ -149,7 +149,7 @@ Mat mat_of(const pbcg_mat *m)
     A.va = m->va;
     A.sl_w = nullptr;
     A.lci = m->lci;
-    A.tblk = m->tblk;
+    A.tmeta = m->tmeta;
     return A;
 }
 
@@ -176,7 +176,7 @@ void mat_release(pbcg_mat *m)
     cudaFree(m->va);
     cudaFree(m->perm);
     cudaFree(m->lci);
-    cudaFree(m->tblk);
+    cudaFree(m->tmeta);
     delete m;
 }
 
@@ -309,7 +309,7 @@ struct Sell {
     long long padded = 0;
     bool permuted = false;
     bool narrow = true;
-    std::vector<int> sl_off, rlen, ci, perm, lci, tblk;
+    std::vector<int> sl_off, rlen, ci, perm, lci, tmeta;
     std::vector<double> va;
 };
 
@@ -390,18 +390,19 @@ bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val,
     }
     if (!S.permuted)
         S.perm.clear();
-    // per tile: the 256-row blocks of the gathered vector its columns fall in
-    // (at most GMAX, else -1), and each entry's index into those staged blocks
+    // per tile: its entry range, the 256-row blocks of the gathered vector its
+    // columns fall in (at most GMAX, else -1), and each entry's index into
+    // those staged blocks
     const int ntl = (ns + TILE_SLICES - 1) / TILE_SLICES;
-    S.tblk.assign((size_t)ntl * GMAX, -1);
+    S.tmeta.assign((size_t)ntl * TMETA, -1);
     S.lci.assign(S.ci.size(), 0);
     for (int t = 0; t < ntl; t++) {
         const int sa = t * TILE_SLICES, sb = std::min(ns, sa + TILE_SLICES);
+        S.tmeta[(size_t)t * TMETA + 0] = S.sl_off[sa];
+        S.tmeta[(size_t)t * TMETA + 1] = S.sl_off[sb];
         std::vector<int> blocks;
         bool ok = true;
         for (long long e = S.sl_off[sa]; e < S.sl_off[sb] && ok; e++) {
-            int sl = sa + (int)((e - S.sl_off[sa]) / 32), p = 0;
-            (void)sl;
             int b = S.ci[(size_t)e] / TILE_ROWS;
             if (std::find(blocks.begin(), blocks.end(), b) == blocks.end()) {
                 if ((int)blocks.size() == GMAX)
@@ -409,13 +410,12 @@ bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val,
                 else
                     blocks.push_back(b);
             }
-            (void)p;
         }
         if (!ok || blocks.empty())
             continue;
         std::sort(blocks.begin(), blocks.end());
         for (size_t g = 0; g < blocks.size(); g++)
-            S.tblk[(size_t)t * GMAX + g] = blocks[g];
+            S.tmeta[(size_t)t * TMETA + 2 + g] = blocks[g];
         for (long long e = S.sl_off[sa]; e < S.sl_off[sb]; e++) {
             int b = S.ci[(size_t)e] / TILE_ROWS;
             int g = (int)(std::lower_bound(blocks.begin(), blocks.end(), b) - blocks.begin());
@@ -970,7 +970,7 @@ Mat layout_mat(const BatchLayout *L)
     A.va = L->va;
     A.sl_w = nullptr;
     A.lci = nullptr;
-    A.tblk = nullptr;
+    A.tmeta = nullptr;
     return A;
 }
 
@@ -1370,7 +1370,7 @@ Mat pool_mat(const pbcg_pool *P)
     A.ci = P->ci;
     A.va = P->va;
     A.lci = nullptr;
-    A.tblk = nullptr;
+    A.tmeta = nullptr;
     return A;
 }
 
@@ -1610,7 +1610,7 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     m->nnz = nnz;
     m->nslices = S.nslices;
     m->padded = S.padded;
-    m->sl_off = m->rlen = m->ci = m->perm = m->lci = m->tblk = nullptr;
+    m->sl_off = m->rlen = m->ci = m->perm = m->lci = m->tmeta = nullptr;
     m->va = nullptr;
     m->narrow = S.narrow;
     m->bl = nullptr;
@@ -1630,11 +1630,11 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     if (e == cudaSuccess)
         e = cudaMalloc(&m->lci, sizeof(int) * P);
     if (e == cudaSuccess)
-        e = cudaMalloc(&m->tblk, sizeof(int) * S.tblk.size());
+        e = cudaMalloc(&m->tmeta, sizeof(int) * S.tmeta.size());
     if (e == cudaSuccess && S.padded)
         e = cudaMemcpy(m->lci, S.lci.data(), sizeof(int) * (size_t)S.padded, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(m->tblk, S.tblk.data(), sizeof(int) * S.tblk.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(m->tmeta, S.tmeta.data(), sizeof(int) * S.tmeta.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(m->sl_off, S.sl_off.data(), sizeof(int) * S.sl_off.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)

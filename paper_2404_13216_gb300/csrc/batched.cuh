@@ -78,8 +78,7 @@ __device__ __forceinline__ void b_flush(DotSet<ND, MODE> &D, Shm<ND> &sh, const 
         __threadfence();
         GAcc *g = B.acc + (size_t)sys * MAXD;
         if (MODE == 1) {
-            if (threadIdx.x < ND)
-                sh.dv[threadIdx.x] = gacc_round_reset(&g[threadIdx.x], sh.scratch[threadIdx.x]);
+            gacc_round_reset_cta<ND>(g, sh.acc, sh.scratch, sh.dv);
         } else if (warp < ND) {
             // partials of the system's flush groups, in tile order (non-first tiles hold +0)
             const int t0 = B.sys_t0[sys], t1 = B.sys_t1[sys];

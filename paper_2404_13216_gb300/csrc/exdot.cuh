@@ -409,8 +409,9 @@ __device__ __forceinline__ void cta_to_global(CtaAcc<ND> &c, GAcc *g)
     }
 }
 
-// Round the exact sum held in g (read through L2) to the nearest double and
-// reset g for the next use.  Called by one thread; `scratch` is NDIG words.
+// Round the exact sum held in digits dig[k0..k1] (signed carry-save 32-bit
+// digits, bit 0 of digit 0 weighing 2^-2148; digits outside the range are 0)
+// to the nearest double.  One thread; `scratch` is NDIG words.
 __device__ __forceinline__ uint32_t bit_at(const uint32_t *w, int lo, int hi, int i)
 {
     int k = i >> 5;
@@ -419,80 +420,103 @@ __device__ __forceinline__ uint32_t bit_at(const uint32_t *w, int lo, int hi, in
     return (w[k] >> (i & 31)) & 1u;
 }
 
-static __device__ double gacc_round_reset(GAcc *g, uint32_t *scratch)
+static __device__ double round_digits(const unsigned long long *dig, int k0, int k1, int nf, uint32_t *scratch)
 {
-    int nf = *((volatile int *)&g->nf);
-    int k0 = *((volatile int *)&g->kmin), k1 = *((volatile int *)&g->kmax);
-    double result = 0.0;
-    if (nf) {
-        result = __longlong_as_double(0x7ff8000000000000ll);
-    } else if (k1 >= k0) {
-        // carry normalisation from k0 upward; digits above k1 start at 0
-        long long carry = 0;
-        int top = k0;
-        for (int k = k0; k < NDIG; k++) {
-            long long v = (k <= k1) ? (long long)__ldcg(&g->dig[k]) : 0ll;
-            // v + carry without overflow: |digit| < 2^62 and |carry| < 2^31 here
-            long long s = v + carry;
+    if (nf)
+        return __longlong_as_double(0x7ff8000000000000ll);
+    if (k1 < k0)
+        return 0.0;
+    // carry normalisation from k0 upward; digits above k1 start at 0
+    long long carry = 0;
+    int top = k0;
+    for (int k = k0; k < NDIG; k++) {
+        long long v = (k <= k1) ? (long long)dig[k] : 0ll;
+        // v + carry without overflow: |digit| < 2^62 and |carry| < 2^31 here
+        long long s = v + carry;
+        scratch[k] = (uint32_t)s;
+        carry = s >> 32;
+        top = k;
+        // stop once the rest is pure sign extension of a canonical top word
+        if (k >= k1 && ((carry == 0 && !(scratch[k] >> 31)) || (carry == -1 && (scratch[k] >> 31))))
+            break;
+    }
+    bool negv = carry < 0;
+    if (negv) {
+        // magnitude = -value over digits k0..top (infinite sign extension above)
+        uint32_t c1 = 1u;
+        for (int k = k0; k <= top; k++) {
+            uint32_t x = ~scratch[k];
+            unsigned long long s = (unsigned long long)x + c1;
             scratch[k] = (uint32_t)s;
-            carry = s >> 32;
-            top = k;
-            // stop once the rest is pure sign extension of a canonical top word
-            if (k >= k1 && ((carry == 0 && !(scratch[k] >> 31)) || (carry == -1 && (scratch[k] >> 31))))
-                break;
-        }
-        bool negv = carry < 0;
-        if (negv) {
-            // magnitude = -value over digits k0..top (infinite sign extension above)
-            uint32_t c1 = 1u;
-            for (int k = k0; k <= top; k++) {
-                uint32_t x = ~scratch[k];
-                unsigned long long s = (unsigned long long)x + c1;
-                scratch[k] = (uint32_t)s;
-                c1 = (uint32_t)(s >> 32);
-            }
-        }
-        int hk = -1;
-        for (int k = top; k >= k0; k--) {
-            if (scratch[k] != 0u) {
-                hk = k;
-                break;
-            }
-        }
-        if (hk >= 0) {
-            int h = hk * 32 + 31 - __clz(scratch[hk]);
-            int lsb = max(h - 52, 1074);
-            unsigned long long m = 0ull;
-            for (int i = h; i >= lsb; i--)
-                m = (m << 1) | bit_at(scratch, k0, top, i);
-            uint32_t rb = bit_at(scratch, k0, top, lsb - 1);
-            uint32_t st = 0u;
-            int sk = (lsb - 1) >> 5;
-            for (int k = k0; k < sk && k <= top; k++)
-                st |= scratch[k];
-            if (sk >= k0 && sk <= top)
-                st |= scratch[sk] & ((1u << ((lsb - 1) & 31)) - 1u);
-            if (rb && (st || (m & 1ull)))
-                m += 1ull;
-            // value = m * 2^(lsb - 2148); biased exponent field = lsb - 1074 (+1 via the implicit bit)
-            long long ef = (long long)(lsb - 1074);
-            unsigned long long bits = ((unsigned long long)ef << 52) + m;
-            if (bits >= 0x7ff0000000000000ull)
-                bits = 0x7ff0000000000000ull;            // overflow rounds to infinity
-            if (negv)
-                bits |= 0x8000000000000000ull;
-            result = __longlong_as_double((long long)bits);
-        } else if (negv) {
-            result = 0.0;
+            c1 = (uint32_t)(s >> 32);
         }
     }
-    // clear every touched digit, also when a non-finite operand made the result NaN
-    for (int k = k0; k <= k1; k++)
-        g->dig[k] = 0ull;
-    g->kmin = NDIG;
-    g->kmax = -1;
-    g->nf = 0;
-    return result;
+    int hk = -1;
+    for (int k = top; k >= k0; k--) {
+        if (scratch[k] != 0u) {
+            hk = k;
+            break;
+        }
+    }
+    if (hk < 0)
+        return 0.0;
+    int h = hk * 32 + 31 - __clz(scratch[hk]);
+    int lsb = max(h - 52, 1074);
+    unsigned long long m = 0ull;
+    for (int i = h; i >= lsb; i--)
+        m = (m << 1) | bit_at(scratch, k0, top, i);
+    uint32_t rb = bit_at(scratch, k0, top, lsb - 1);
+    uint32_t st = 0u;
+    int sk = (lsb - 1) >> 5;
+    for (int k = k0; k < sk && k <= top; k++)
+        st |= scratch[k];
+    if (sk >= k0 && sk <= top)
+        st |= scratch[sk] & ((1u << ((lsb - 1) & 31)) - 1u);
+    if (rb && (st || (m & 1ull)))
+        m += 1ull;
+    // value = m * 2^(lsb - 2148); biased exponent field = lsb - 1074 (+1 via the implicit bit)
+    long long ef = (long long)(lsb - 1074);
+    unsigned long long bits = ((unsigned long long)ef << 52) + m;
+    if (bits >= 0x7ff0000000000000ull)
+        bits = 0x7ff0000000000000ull;            // overflow rounds to infinity
+    if (negv)
+        bits |= 0x8000000000000000ull;
+    return __longlong_as_double((long long)bits);
+}
+
+// Round the ND global accumulators g[0..ND-1] and reset them; every thread of
+// the CTA calls.  The touched digits are first copied, in parallel, into the
+// CTA accumulator c (free at this point: its contents were merged into g), so
+// that the serial rounding (one thread per dot) reads shared memory only.
+// dv[d] receives the rounded dots.
+template <int ND>
+__device__ void gacc_round_reset_cta(GAcc *g, CtaAcc<ND> &c, uint32_t (*scratch)[NDIG], double *dv)
+{
+    __syncthreads();
+    if (threadIdx.x < ND) {
+        const int d = threadIdx.x;
+        c.kmin[d] = *((volatile int *)&g[d].kmin);
+        c.kmax[d] = *((volatile int *)&g[d].kmax);
+        c.nf[d] = *((volatile int *)&g[d].nf);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d = 0; d < ND; d++) {
+        const int k0 = c.kmin[d], k1 = c.kmax[d];
+        for (int k = k0 + (int)threadIdx.x; k <= k1; k += blockDim.x) {
+            c.dig[d][k] = __ldcg(&g[d].dig[k]);
+            g[d].dig[k] = 0ull;                      // clear every touched digit, NaN results included
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < ND) {
+        const int d = threadIdx.x;
+        dv[d] = round_digits(c.dig[d], c.kmin[d], c.kmax[d], c.nf[d], scratch[d]);
+        g[d].kmin = NDIG;
+        g[d].kmax = -1;
+        g[d].nf = 0;
+    }
+    __syncthreads();
 }
 
 }  // namespace pbcg

@@ -80,8 +80,8 @@ struct Mat {
     const double *__restrict__ va;       // padded values
     const int *__restrict__ sl_w;        // [nslices] slice widths, or NULL: width = (sl_off[s+1] - sl_off[s]) / 32
     const int *__restrict__ lci;         // padded local indices into a tile's staged blocks (or NULL)
-    const int *__restrict__ tblk;        // [ntiles * GMAX] 256-row blocks each tile gathers from, -1 pad;
-                                         // tblk[t * GMAX] == -1: the tile gathers from global memory
+    const int *__restrict__ tmeta;       // [ntiles * TMETA] per tile: first and end SELL entry, then the GMAX
+                                         // 256-row blocks it gathers from (-1 pad; all -1: gathers from global)
 };
 
 struct Vecs {
@@ -340,8 +340,7 @@ __device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
         return false;
     __threadfence();
     if (MODE == 1) {
-        if (threadIdx.x < ND)
-            sh.dv[threadIdx.x] = gacc_round_reset(&wk->g[threadIdx.x], sh.scratch[threadIdx.x]);
+        gacc_round_reset_cta<ND>(wk->g, sh.acc, sh.scratch, sh.dv);
     } else if (warp < ND) {
         const double *pp = wk->part + warp * wk->maxgrid;
         double v = 0.0;
@@ -893,36 +892,43 @@ struct TilePipe {
     {
         return reinterpret_cast<const int *>(stage(k) + L::VEC + L::GWIN + L::VA + L::CI + L::RLEN);
     }
+    __device__ __forceinline__ const int *meta(int k) const
+    {
+        return reinterpret_cast<const int *>(stage(k) + L::VEC + L::GWIN + L::VA + L::CI + L::RLEN + L::SLOFF);
+    }
 
-    // thread 0: copy tile `tile` (nv of the NV vectors) into stage k; e0/e1 are
-    // sl_off[first slice] and sl_off[end slice] of the tile, blk the tile's
-    // gather blocks (blk[0] < 0: none), all loaded beforehand; gx is the
-    // vector the tile's SpMV gathers from (NULL: no SpMV in this pass)
-    __device__ __forceinline__ void issue(int k, int tile, int e0, int e1, const int (&blk)[GMAX], const Mat &A,
-                                          const double *const (&src)[NV], int nv, const double *gx)
+    // thread 0 or the refilling lane: copy tile `tile` (nv of the NV vectors),
+    // described by its record rec, into stage k, together with the record of
+    // tile tn, the next one for this stage (-1: none); gx is the vector the
+    // tile's SpMV gathers from (NULL: no SpMV in this pass)
+    __device__ __forceinline__ void issue(int k, int tile, const int (&rec)[TMETA], const Mat &A,
+                                          const double *const (&src)[NV], int nv, const double *gx, int tn)
     {
         const int s0 = tile * TILE_SLICES;
-        const int span = e1 - e0;
+        const int e0 = rec[0], span = rec[1] - rec[0];
         const bool staged = MATS && span > 0 && span <= MCAP;
-        const bool windowed = staged && gx != nullptr && A.lci != nullptr && blk[0] >= 0;
+        const bool windowed = staged && gx != nullptr && A.lci != nullptr && rec[2] >= 0;
         int nblk = 0;
         if (windowed) {
 #pragma unroll
             for (int g = 0; g < GMAX; g++)
-                nblk += blk[g] >= 0;
+                nblk += rec[2 + g] >= 0;
         }
         info[k].e0 = e0;
         info[k].staged = staged;
         info[k].windowed = windowed;
         uint32_t bytes = (uint32_t)nv * TILE_ROWS * 8 + L::RLEN + L::SLOFF + (staged ? (uint32_t)span * 12u : 0u) +
-                         (uint32_t)nblk * TILE_ROWS * 8;
+                         (uint32_t)nblk * TILE_ROWS * 8 + (tn >= 0 ? TMETA * 4u : 0u);
         fence_async_shared();
         mbar_arrive_expect_tx(&bar[k], bytes);
         const size_t row0 = (size_t)tile * TILE_ROWS;
         for (int v = 0; v < nv; v++)
             bulk_g2s(stage(k) + (size_t)v * TILE_ROWS * 8, src[v] + row0, TILE_ROWS * 8, &bar[k]);
-        bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA + L::CI, A.rlen + row0, L::RLEN, &bar[k]);
-        bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA + L::CI + L::RLEN, A.sl_off + s0, L::SLOFF, &bar[k]);
+        uint8_t *tail = stage(k) + L::VEC + L::GWIN + L::VA + L::CI;
+        bulk_g2s(tail, A.rlen + row0, L::RLEN, &bar[k]);
+        bulk_g2s(tail + L::RLEN, A.sl_off + s0, L::SLOFF, &bar[k]);
+        if (tn >= 0)
+            bulk_g2s(tail + L::RLEN + L::SLOFF, A.tmeta + (size_t)tn * TMETA, TMETA * 4, &bar[k]);
         if (staged) {
             bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA, (windowed ? A.lci : A.ci) + e0, (uint32_t)span * 4u, &bar[k]);
             bulk_g2s(stage(k) + L::VEC + L::GWIN, A.va + e0, (uint32_t)span * 8u, &bar[k]);
@@ -930,8 +936,8 @@ struct TilePipe {
         if (windowed) {
 #pragma unroll
             for (int g = 0; g < GMAX; g++)
-                if (blk[g] >= 0)
-                    bulk_g2s(stage(k) + L::VEC + (size_t)g * TILE_ROWS * 8, gx + (size_t)blk[g] * TILE_ROWS,
+                if (rec[2 + g] >= 0)
+                    bulk_g2s(stage(k) + L::VEC + (size_t)g * TILE_ROWS * 8, gx + (size_t)rec[2 + g] * TILE_ROWS,
                              TILE_ROWS * 8, &bar[k]);
         }
     }
@@ -980,73 +986,99 @@ struct TilePipe {
     }
 };
 
-// common tile loop: prologue, bounded waits, refill after each tile
+// Common tile loop.  No CTA-wide barrier per tile: each warp waits on the
+// stage's mbarrier for its own data, and the last warp to finish with a stage
+// (a shared counter) issues the copies of the tile that reuses it, reading
+// that tile's record from the stage itself (no global load on the refill
+// path).  Warps thus drift apart by up to NSTAGE - 1 tiles, so one
+// warp's integer (exact-dot) work overlaps another's FP64 and memory work.
+// Every wait is bounded; a warp that gives up raises a flag that stops the
+// others, and before the CTA returns one thread waits (bounded) for copies
+// still in flight.
 template <int NV, bool MATS, class Body>
 __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&src)[NV], int nv, const double *gx,
                                           Ctl *c, uint8_t *dsm, Body body)
 {
     __shared__ uint64_t bar[NSTAGE];
     __shared__ StageInfo info[NSTAGE];
+    __shared__ int done_cnt[NSTAGE];         // warps finished with the stage's current tile
+    __shared__ int nissued[NSTAGE];          // tiles issued into each stage
+    __shared__ int tmo;
     TilePipe<NV, MATS> P{dsm, bar, info};
     const int ntiles = (A.nslices + TILE_SLICES - 1) / TILE_SLICES;
     const int my = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-    auto tile_of = [&](int jj) { return (int)blockIdx.x + jj * (int)gridDim.x; };
-    auto end_slice = [&](int t) { return min((t + 1) * TILE_SLICES, A.nslices); };
-    int pe0 = 0, pe1 = 0;            // thread 0: offsets of the next tile to issue
-    int pblk[GMAX];                  // thread 0: gather blocks of the next tile to issue
-    auto load_blk = [&](int t, int (&blk)[GMAX]) {
+    auto tile_of = [&](int jj) { return jj < my ? (int)blockIdx.x + jj * (int)gridDim.x : -1; };
+    const bool recs = A.tmeta != nullptr;     // tile records travel with the stages
+    auto record = [&](int t, int (&rec)[TMETA]) {   // from global memory
+        if (recs) {
 #pragma unroll
-        for (int g = 0; g < GMAX; g++)
-            blk[g] = (MATS && A.tblk && gx) ? A.tblk[(size_t)t * GMAX + g] : -1;
+            for (int q = 0; q < TMETA; q++)
+                rec[q] = A.tmeta[(size_t)t * TMETA + q];
+        } else {
+            rec[0] = A.sl_off[t * TILE_SLICES];
+            rec[1] = A.sl_off[min((t + 1) * TILE_SLICES, A.nslices)];
+#pragma unroll
+            for (int q = 2; q < TMETA; q++)
+                rec[q] = -1;
+        }
     };
     if (threadIdx.x == 0) {
-        for (int k = 0; k < NSTAGE; k++)
+        for (int k = 0; k < NSTAGE; k++) {
             mbar_init(&bar[k], 1);
+            done_cnt[k] = 0;
+            nissued[k] = 0;
+        }
+        tmo = 0;
         fence_mbar_init();
         fence_async_shared();
+        for (int k = 0; k < NSTAGE && k < my; k++) {
+            int rec[TMETA];
+            record(tile_of(k), rec);
+            nissued[k] += 1;
+            P.issue(k, tile_of(k), rec, A, src, nv, gx, recs ? tile_of(k + NSTAGE) : -1);
+        }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < NSTAGE && k < my; k++) {
-            const int t = tile_of(k);
-            int blk[GMAX];
-            load_blk(t, blk);
-            P.issue(k, t, A.sl_off[t * TILE_SLICES], A.sl_off[end_slice(t)], blk, A, src, nv, gx);
-        }
-        if (NSTAGE < my) {
-            const int t = tile_of(NSTAGE);
-            pe0 = A.sl_off[t * TILE_SLICES];
-            pe1 = A.sl_off[end_slice(t)];
-            load_blk(t, pblk);
-        }
-    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    bool tmo = false;
-    int j = 0;
-    for (; j < my; j++) {
+    for (int j = 0; j < my; j++) {
         const int k = j % NSTAGE;
-        const bool ok = mbar_wait_bounded(&bar[k], (uint32_t)(j / NSTAGE) & 1u);
-        if (__syncthreads_or(!ok)) {
-            tmo = true;              // uniform: some thread gave up on this stage
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[k], (uint32_t)(j / NSTAGE) & 1u));
+        if (!ok || *(volatile int *)&tmo) {
+            if (lane == 0)
+                tmo = 1;
             break;
         }
         body(P, k, tile_of(j), warp, lane);
-        __syncthreads();
-        if (threadIdx.x == 0 && j + NSTAGE < my) {
-            P.issue(k, tile_of(j + NSTAGE), pe0, pe1, pblk, A, src, nv, gx);
-            if (j + NSTAGE + 1 < my) {
-                const int t = tile_of(j + NSTAGE + 1);
-                pe0 = A.sl_off[t * TILE_SLICES];
-                pe1 = A.sl_off[end_slice(t)];
-                load_blk(t, pblk);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&done_cnt[k], 1) == WARPS - 1) {
+                // last warp out of this stage: every warp has read it
+                __threadfence_block();
+                done_cnt[k] = 0;
+                const int jn = j + NSTAGE;
+                if (jn < my) {
+                    int rec[TMETA];
+                    if (recs) {
+                        const int *m = P.meta(k);
+#pragma unroll
+                        for (int q = 0; q < TMETA; q++)
+                            rec[q] = m[q];
+                    } else {
+                        record(tile_of(jn), rec);
+                    }
+                    nissued[k] += 1;
+                    P.issue(k, tile_of(jn), rec, A, src, nv, gx, recs ? tile_of(jn + NSTAGE) : -1);
+                }
             }
         }
     }
+    __syncthreads();
     if (tmo) {
-        // give up: wait (bounded) for this CTA's copies still in flight, then report
         if (threadIdx.x == 0) {
-            for (int jj = j; jj < my && jj < j + NSTAGE; jj++)
-                mbar_wait_bounded(&bar[jj % NSTAGE], (uint32_t)(jj / NSTAGE) & 1u);
+            for (int k = 0; k < NSTAGE; k++)
+                if (nissued[k] > 0)
+                    mbar_wait_bounded(&bar[k], (uint32_t)(nissued[k] - 1) & 1u);
             atomicOr(&c->err, 1);
         }
         __syncthreads();

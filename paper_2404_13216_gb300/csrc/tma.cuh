@@ -23,6 +23,7 @@ constexpr int NSTAGE = 2;
 constexpr int MCAP = TILE_ROWS * 7;            // staged SELL entries per tile (width <= 7)
 constexpr int SLOFF_STAGE = 16;                // slice offsets copied per tile (needs 9)
 constexpr int GMAX = 6;                        // 256-row blocks of the gathered vector staged per tile
+constexpr int TMETA = 8;                       // ints per tile record: first entry, end entry, GMAX blocks
 constexpr unsigned MBAR_SPIN_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -86,7 +87,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 // Dynamic shared memory of a staged pass with NV input vectors:
 // NSTAGE stages of { vec[NV][256] f64, gwin[GMAX][256] f64 (if staged), va[MCAP] f64 (if staged),
-// ci[MCAP] i32 (if staged), rlen[256] i32, sl_off[16] i32 }.
+// ci[MCAP] i32 (if staged), rlen[256] i32, sl_off[16] i32, meta[TMETA] i32 }.
+// meta holds the record of the tile this stage takes next, so the warp that
+// refills the stage needs no global load.
 // When a tile's columns fall in at most GMAX 256-row blocks, those blocks of
 // the gathered vector are staged in gwin and ci holds local indices into it.
 template <int NV, bool MATS>
@@ -97,7 +100,8 @@ struct StageLayout {
     static constexpr uint32_t CI = MATS ? MCAP * 4 : 0;
     static constexpr uint32_t RLEN = TILE_ROWS * 4;
     static constexpr uint32_t SLOFF = SLOFF_STAGE * 4;
-    static constexpr uint32_t STAGE = VEC + GWIN + VA + CI + RLEN + SLOFF;
+    static constexpr uint32_t META = TMETA * 4;
+    static constexpr uint32_t STAGE = VEC + GWIN + VA + CI + RLEN + SLOFF + META;
     static constexpr uint32_t TOTAL = NSTAGE * STAGE;
     static_assert(STAGE % 16 == 0, "stages must stay 16-byte aligned");
 };
