@@ -301,8 +301,13 @@ int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
 }
 
 // SELL-32 layout of a CSR matrix (host side), with an optional row order
-// sorted by length inside windows of SELL_SIGMA rows when that saves padding
+// sorted by length when that saves padding.  Up to SELL_GLOBAL rows (their
+// gathered vectors fit easily in L2) the sort is global, so the longest rows
+// open the first tiles and slices, and the passes' round-robin assignment of
+// tiles to CTAs (and slices to warps) deals the heavy ones out evenly; larger
+// matrices are sorted inside windows of SELL_SIGMA rows to keep locality.
 constexpr int SELL_SIGMA = 4096;
+constexpr int SELL_GLOBAL = 1 << 23;
 
 struct Sell {
     int nslices = 0;
@@ -339,8 +344,9 @@ bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val,
     };
     long long pad0 = padded_of(S.perm);
     if ((double)pad0 > 1.10 * (double)nnz + 32.0 * ns) {
-        for (int w0 = 0; w0 < n; w0 += SELL_SIGMA) {
-            int w1 = std::min(n, w0 + SELL_SIGMA);
+        const int sigma = n <= SELL_GLOBAL ? n : SELL_SIGMA;
+        for (int w0 = 0; w0 < n; w0 += sigma) {
+            int w1 = std::min(n, w0 + sigma);
             std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1,
                              [&](int a, int b) { return len[a] > len[b]; });
         }
