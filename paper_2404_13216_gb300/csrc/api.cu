@@ -1018,35 +1018,37 @@ Vecs batch_vecs(pbcg_ctx *ctx)
 struct BKernel {
     void *fn;
     const char *name;
+    size_t smem;     // dynamic shared memory (staged passes), 0 otherwise
 };
 
 template <int MODE>
 std::vector<BKernel> batch_body(int alg)
 {
     std::vector<BKernel> k;
-    k.push_back({(void *)k_batched<1, StepTrueRes<false>>, "b_true_res"});
+    k.push_back({(void *)k_batched<1, StepTrueRes<false>>, "b_true_res", 0});
     if (alg == PBCG_ALG_PIPELINED_RR) {
-        k.push_back({(void *)k_batched<0, StepRR<1>>, "b_rr1"});
-        k.push_back({(void *)k_batched<0, StepRR<2>>, "b_rr2"});
-        k.push_back({(void *)k_batched<0, StepRR<3>>, "b_rr3"});
-        k.push_back({(void *)k_batched<0, StepRR<4>>, "b_rr4"});
+        k.push_back({(void *)k_batched<0, StepRR<1>>, "b_rr1", 0});
+        k.push_back({(void *)k_batched<0, StepRR<2>>, "b_rr2", 0});
+        k.push_back({(void *)k_batched<0, StepRR<3>>, "b_rr3", 0});
+        k.push_back({(void *)k_batched<0, StepRR<4>>, "b_rr4", 0});
     }
     if (alg == PBCG_ALG_PIPELINED || alg == PBCG_ALG_PIPELINED_RR) {
-        k.push_back({(void *)k_batched<MODE, StepPipeX>, MODE ? "b_pipe_x_exact" : "b_pipe_x_plain"});
-        k.push_back({(void *)k_batched<MODE, StepPipeY>, MODE ? "b_pipe_y_exact" : "b_pipe_y_plain"});
+        k.push_back({(void *)k_bstaged<MODE, BPipeX>, MODE ? "b_pipe_x_exact" : "b_pipe_x_plain",
+                     StageLayout<BPipeX::NV, true>::TOTAL});
+        k.push_back({(void *)k_bstaged<MODE, BPipeY>, MODE ? "b_pipe_y_exact" : "b_pipe_y_plain",
+                     StageLayout<BPipeY::NV, true>::TOTAL});
     } else {
-        k.push_back({(void *)k_batched<MODE, StepBicgP>, "b_bicg_p"});
-        k.push_back({(void *)k_batched<MODE, StepBicgA>, MODE ? "b_bicg_a_exact" : "b_bicg_a_plain"});
-        k.push_back({(void *)k_batched<MODE, StepBicgB>, MODE ? "b_bicg_b_exact" : "b_bicg_b_plain"});
-        k.push_back({(void *)k_batched<MODE, StepBicgC>, MODE ? "b_bicg_c_exact" : "b_bicg_c_plain"});
+        k.push_back({(void *)k_batched<MODE, StepBicgP>, "b_bicg_p", 0});
+        k.push_back({(void *)k_batched<MODE, StepBicgA>, MODE ? "b_bicg_a_exact" : "b_bicg_a_plain", 0});
+        k.push_back({(void *)k_batched<MODE, StepBicgB>, MODE ? "b_bicg_b_exact" : "b_bicg_b_plain", 0});
+        k.push_back({(void *)k_batched<MODE, StepBicgC>, MODE ? "b_bicg_c_exact" : "b_bicg_c_plain", 0});
     }
     return k;
 }
 
-int bgrid(pbcg_ctx *ctx, const void *fn, int ntiles)
+int bgrid(pbcg_ctx *ctx, const void *fn, int ntiles, size_t smem = 0)
 {
-    int g = grid_for(ctx, fn, (long long)ntiles * TILE_SLICES, 0);
-    return g;
+    return grid_for(ctx, fn, (long long)ntiles * TILE_SLICES, smem);
 }
 
 int blaunch(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Batch &B)
@@ -1167,8 +1169,9 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
             cudaKernelNodeParams kp;
             memset(&kp, 0, sizeof kp);
             kp.func = bk.fn;
-            kp.gridDim = dim3(bgrid(ctx, bk.fn, B.ntiles));
+            kp.gridDim = dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem));
             kp.blockDim = dim3(THREADS);
+            kp.sharedMemBytes = (unsigned)bk.smem;
             kp.kernelParams = args;
             cudaGraphNode_t node;
             CK(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
@@ -1418,29 +1421,29 @@ Batch pool_batch(const pbcg_pool *P)
 }
 
 template <int MODE>
-std::vector<void *> pool_body(int alg)
+std::vector<BKernel> pool_body(int alg)
 {
-    std::vector<void *> k;
-    k.push_back((void *)k_batched<MODE, PoolSetup1>);
+    std::vector<BKernel> k;
+    k.push_back({(void *)k_batched<MODE, PoolSetup1>, "pool_setup1", 0});
     if (alg != PBCG_ALG_BICGSTAB) {
-        k.push_back((void *)k_batched<MODE, PoolSetup2>);
-        k.push_back((void *)k_batched<0, PoolSetup3>);
+        k.push_back({(void *)k_batched<MODE, PoolSetup2>, "pool_setup2", 0});
+        k.push_back({(void *)k_batched<0, PoolSetup3>, "pool_setup3", 0});
     }
-    k.push_back((void *)k_batched<1, StepTrueRes<false>>);
+    k.push_back({(void *)k_batched<1, StepTrueRes<false>>, "pool_true_res", 0});
     if (alg == PBCG_ALG_PIPELINED_RR) {
-        k.push_back((void *)k_batched<0, StepRR<1>>);
-        k.push_back((void *)k_batched<0, StepRR<2>>);
-        k.push_back((void *)k_batched<0, StepRR<3>>);
-        k.push_back((void *)k_batched<0, StepRR<4>>);
+        k.push_back({(void *)k_batched<0, StepRR<1>>, "pool_rr1", 0});
+        k.push_back({(void *)k_batched<0, StepRR<2>>, "pool_rr2", 0});
+        k.push_back({(void *)k_batched<0, StepRR<3>>, "pool_rr3", 0});
+        k.push_back({(void *)k_batched<0, StepRR<4>>, "pool_rr4", 0});
     }
     if (alg == PBCG_ALG_BICGSTAB) {
-        k.push_back((void *)k_batched<MODE, StepBicgP>);
-        k.push_back((void *)k_batched<MODE, StepBicgA>);
-        k.push_back((void *)k_batched<MODE, StepBicgB>);
-        k.push_back((void *)k_batched<MODE, StepBicgC>);
+        k.push_back({(void *)k_batched<MODE, StepBicgP>, "pool_bicg_p", 0});
+        k.push_back({(void *)k_batched<MODE, StepBicgA>, "pool_bicg_a", 0});
+        k.push_back({(void *)k_batched<MODE, StepBicgB>, "pool_bicg_b", 0});
+        k.push_back({(void *)k_batched<MODE, StepBicgC>, "pool_bicg_c", 0});
     } else {
-        k.push_back((void *)k_batched<MODE, StepPipeX>);
-        k.push_back((void *)k_batched<MODE, StepPipeY>);
+        k.push_back({(void *)k_bstaged<MODE, BPipeX>, "pool_pipe_x", StageLayout<BPipeX::NV, true>::TOTAL});
+        k.push_back({(void *)k_bstaged<MODE, BPipeY>, "pool_pipe_y", StageLayout<BPipeY::NV, true>::TOTAL});
     }
     return k;
 }
@@ -1482,15 +1485,16 @@ int pool_build_graph(pbcg_ctx *ctx, pbcg_pool *P)
     cudaGraphNode_t cnode;
     CK(cudaGraphAddNode(&cnode, P->graph, &list0, nullptr, 1, &cp));
     cudaGraph_t g = cp.conditional.phGraph_out[0];
-    std::vector<void *> body = P->cfg.dot_mode ? pool_body<1>(P->cfg.alg) : pool_body<0>(P->cfg.alg);
+    std::vector<BKernel> body = P->cfg.dot_mode ? pool_body<1>(P->cfg.alg) : pool_body<0>(P->cfg.alg);
     cudaGraphNode_t prev = nullptr;
-    for (void *fn : body) {
+    for (auto &bk : body) {
         void *args[3] = {&A, &V, &B};
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof kp);
-        kp.func = fn;
-        kp.gridDim = dim3(bgrid(ctx, fn, B.ntiles));
+        kp.func = bk.fn;
+        kp.gridDim = dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem));
         kp.blockDim = dim3(THREADS);
+        kp.sharedMemBytes = (unsigned)bk.smem;
         kp.kernelParams = args;
         cudaGraphNode_t node;
         CK(cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
@@ -1854,7 +1858,7 @@ int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out
         if (e == cudaSuccess)
             e = cudaMalloc(q, std::max<size_t>(bytes, 16));
     };
-    dev((void **)&P->sl_off, sizeof(int) * (nsl + 1));
+    dev((void **)&P->sl_off, sizeof(int) * (nsl + SLOFF_STAGE));
     dev((void **)&P->sl_w, sizeof(int) * nsl);
     dev((void **)&P->rlen, sizeof(int) * rows);
     dev((void **)&P->ci, sizeof(int) * (size_t)c.max_entries);
@@ -1894,7 +1898,7 @@ int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out
     if (e == cudaSuccess)
         e = cudaMemset(P->tile_sys, 0xff, sizeof(int) * (size_t)tiles);
     if (e == cudaSuccess)
-        e = cudaMemset(P->sl_off, 0, sizeof(int) * (nsl + 1));
+        e = cudaMemset(P->sl_off, 0, sizeof(int) * (nsl + SLOFF_STAGE));
     if (e == cudaSuccess)
         e = cudaMemset(P->sl_w, 0, sizeof(int) * nsl);
     if (e == cudaSuccess)
@@ -2077,7 +2081,9 @@ int pbcg_pool_admit(pbcg_pool *P, int32_t n, int64_t nnz, const int32_t *row_ptr
         Ctl *cl = P->ctl;
         int s_ = sid, t_ = (int)tA, k_ = ntl;
         const int *bd = P->bad;
-        void *args[] = {&ts, &a0, &a1, &cl, &s_, &t_, &k_, &init, (void *)&bd};
+        unsigned *dn = P->done;
+        GAcc *ac = P->acc;
+        void *args[] = {&ts, &a0, &a1, &cl, &s_, &t_, &k_, &init, (void *)&bd, &dn, &ac};
         CK(cudaLaunchKernel((void *)k_pool_activate, dim3(1), dim3(256), args, 0, ctx->stream));
     }
     // the caller's arrays and the pinned row pointers are consumed when this returns

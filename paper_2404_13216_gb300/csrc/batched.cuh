@@ -119,21 +119,25 @@ __global__ void __launch_bounds__(THREADS) k_batched(Mat A, Vecs V, Batch B)
     int cur = -1, t_first = -1, cnt = 0;
     bool run = false;
     typename Step::Scal S;
+    // each CTA serves one contiguous chunk of the tile list (the live list of a
+    // pool, else all tiles), so a system's tiles form few flush groups
     const bool listed = B.lv_n != nullptr;
     const int nq = listed ? B.lv_n[1] : B.ntiles;
+    const int q0 = (int)(((long long)nq * blockIdx.x) / gridDim.x);
+    const int q1 = (int)(((long long)nq * (blockIdx.x + 1)) / gridDim.x);
     int j = 0;
-    if (listed && (int)blockIdx.x < nq) {
-        int lo = 0, hi = B.lv_n[0] - 1;           // last live system with lv_pre[j] <= blockIdx.x
+    if (listed && q0 < q1) {
+        int lo = 0, hi = B.lv_n[0] - 1;           // last live system with lv_pre[j] <= q0
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (B.lv_pre[mid] <= (int)blockIdx.x)
+            if (B.lv_pre[mid] <= q0)
                 lo = mid;
             else
                 hi = mid - 1;
         }
         j = lo;
     }
-    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    for (int q = q0; q < q1;) {
         int t = q;
         if (listed) {
             while (B.lv_pre[j + 1] <= q)
@@ -141,8 +145,10 @@ __global__ void __launch_bounds__(THREADS) k_batched(Mat A, Vecs V, Batch B)
             t = B.lv_t0[j] + (q - B.lv_pre[j]);
         }
         const int sys = B.tile_sys[t];
-        if (sys < 0)
+        if (sys < 0) {
+            q++;
             continue;                    // unallocated tile of a pool
+        }
         if (sys != cur) {
             if (cur >= 0 && cnt > 0) {
                 b_flush<ND, MODE, Step>(D, sh, B, cur, t_first, cnt, V);
@@ -156,8 +162,12 @@ __global__ void __launch_bounds__(THREADS) k_batched(Mat A, Vecs V, Batch B)
             if (run)
                 S = Step::load(c);
         }
-        if (!run)
+        if (!run) {                      // skip the rest of this system
+            const int qend = listed ? B.lv_pre[j + 1] : B.sys_t1[sys];
+            q = max(q + 1, min(q1, qend));
             continue;
+        }
+        q++;
         if (MODE == 0 && threadIdx.x < ND)
             B.part[(size_t)t * MAXD + threadIdx.x] = 0.0;
         const int sl = t * TILE_SLICES + warp;
@@ -282,30 +292,20 @@ struct StepPipeX {
             if (act) {
                 const double ri = V.r[i], wi = V.w[i];
                 r0i = V.r0[i];
-                double pi;
-                if (S.first) {
+                if (S.first)
                     ti = V.t[i];
-                    pi = ri;
-                    si = wi;
-                    zi = ti;
-                } else if (S.rr) {
-                    pi = V.p[i];
-                    si = V.s[i];
-                    zi = V.z[i];
+                else
                     V.t[i] = ti;
-                } else {
-                    const double nomega = -S.omega;
-                    const double sold = V.s[i], zold = V.z[i];
-                    pi = __fma_rn(S.beta, __fma_rn(nomega, sold, V.p[i]), ri);
-                    si = __fma_rn(S.beta, __fma_rn(nomega, zold, sold), wi);
-                    zi = __fma_rn(S.beta, __fma_rn(nomega, V.v[i], zold), ti);
-                    V.t[i] = ti;
-                }
-                q = __fma_rn(-S.alpha, si, ri);
-                y = __fma_rn(-S.alpha, zi, wi);
-                V.p[i] = pi;
-                V.s[i] = si;
-                V.z[i] = zi;
+                const XRow X = S.first ? pipe_x_row(true, false, -S.alpha, S.beta, -S.omega, ri, wi, ti, 0.0, 0.0, 0.0, 0.0)
+                                       : pipe_x_row(false, S.rr, -S.alpha, S.beta, -S.omega, ri, wi, ti, V.p[i],
+                                                    V.s[i], V.z[i], V.v[i]);
+                si = X.s;
+                zi = X.z;
+                q = X.q;
+                y = X.y;
+                V.p[i] = X.p;
+                V.s[i] = X.s;
+                V.z[i] = X.z;
                 V.q[i] = q;
                 V.y[i] = y;
             }
@@ -342,10 +342,11 @@ struct StepPipeY {
             RowRef R = row_ref(A, sl, lane);
             const double vi = spmv_row(A, R, V.z);
             if (act) {
-                const double q = V.q[i], y = V.y[i];
-                V.x[i] = __fma_rn(S.omega, q, __fma_rn(S.alpha, V.p[i], V.x[i]));
-                rn = __fma_rn(-S.omega, y, q);
-                wn = __fma_rn(-S.omega, __fma_rn(-S.alpha, vi, V.t[i]), y);
+                const YRow Yr = pipe_y_row(S.alpha, S.omega, -S.alpha, -S.omega, V.q[i], V.y[i], V.p[i], V.x[i],
+                                           V.t[i], vi);
+                V.x[i] = Yr.x;
+                rn = Yr.r;
+                wn = Yr.w;
                 r0i = V.r0[i];
                 V.v[i] = vi;
                 V.r[i] = rn;
@@ -369,6 +370,251 @@ struct StepPipeY {
         }
     }
 };
+
+// ---------------------------------------------------------------------------
+// staged batched passes (p-BiCGStab X and Y)
+//
+// The tiles a CTA serves travel through two shared-memory stages by bulk
+// copies, as in the single-system passes.  Thread 0 walks the CTA's tile
+// positions ahead of the warps, skips whole systems the pass does not serve,
+// and records each staged tile's system; the loop stays CTA-synchronous so a
+// flush group can close at any tile.  Row arithmetic and dots are those of
+// the generic steps (pipe_x_row / pipe_y_row), so results are bit-identical.
+// ---------------------------------------------------------------------------
+struct BTag {
+    int tile;        // -1: no more tiles for this CTA
+    int sys;
+    int first;       // pass X: the system's first iteration (no SpMV, t staged in p's slot)
+};
+
+struct BPipeX : StepPipeX {
+    static constexpr int NV = 7;     // r, w, r0, p (t when first), s, z, v
+    static __device__ int flags(const Ctl *c) { return c->it == 0; }
+    static __device__ void srcs(const Vecs &V, int first, const double *(&src)[NV], const double *&gx)
+    {
+        src[0] = V.r;
+        src[1] = V.w;
+        src[2] = V.r0;
+        src[3] = first ? V.t : V.p;
+        src[4] = V.s;
+        src[5] = V.z;
+        src[6] = V.v;
+        gx = first ? nullptr : V.w;
+    }
+    template <int MODE>
+    static __device__ __forceinline__ void row(const TilePipe<NV, true> &P, int k, const Mat &A, const Vecs &V,
+                                               const Scal &S, int tile, int warp, int lane, DotSet<ND, MODE> &D,
+                                               Shm<ND> &sh)
+    {
+        const int sl = tile * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const bool act = sl < A.nslices && i < A.n;
+        const int o = warp * 32 + lane;
+        const double ri = P.vec(k, 0)[o], wi = P.vec(k, 1)[o], r0i = P.vec(k, 2)[o];
+        const double ti = S.first ? P.vec(k, 3)[o] : P.spmv(k, A, warp, lane, V.w);
+        const XRow X = S.first ? pipe_x_row(true, false, -S.alpha, S.beta, -S.omega, ri, wi, ti, 0.0, 0.0, 0.0, 0.0)
+                               : pipe_x_row(false, S.rr, -S.alpha, S.beta, -S.omega, ri, wi, ti, P.vec(k, 3)[o],
+                                            P.vec(k, 4)[o], P.vec(k, 5)[o], P.vec(k, 6)[o]);
+        if (act) {
+            if (!S.first)
+                V.t[i] = ti;
+            V.p[i] = X.p;
+            V.s[i] = X.s;
+            V.z[i] = X.z;
+            V.q[i] = X.q;
+            V.y[i] = X.y;
+        }
+        const double q = act ? X.q : 0.0, y = act ? X.y : 0.0, r0 = act ? r0i : 0.0;
+        const double s = act ? X.s : 0.0, z = act ? X.z : 0.0;
+        const Dec dq = decode(q), dy = decode(y), dr = decode(r0), ds = decode(s), dz = decode(z);
+        D.template add2<false>(sh, 0, q, y, dq, dy, act);
+        D.template add2<true>(sh, 1, y, y, dy, dy, act);
+        D.template add2<false>(sh, 2, r0, s, dr, ds, act);
+        D.template add2<false>(sh, 3, r0, z, dr, dz, act);
+    }
+};
+
+struct BPipeY : StepPipeY {
+    static constexpr int NV = 6;     // q, y, p, x, t, r0
+    static __device__ int flags(const Ctl *) { return 0; }
+    static __device__ void srcs(const Vecs &V, int, const double *(&src)[NV], const double *&gx)
+    {
+        src[0] = V.q;
+        src[1] = V.y;
+        src[2] = V.p;
+        src[3] = V.x;
+        src[4] = V.t;
+        src[5] = V.r0;
+        gx = V.z;
+    }
+    template <int MODE>
+    static __device__ __forceinline__ void row(const TilePipe<NV, true> &P, int k, const Mat &A, const Vecs &V,
+                                               const Scal &S, int tile, int warp, int lane, DotSet<ND, MODE> &D,
+                                               Shm<ND> &sh)
+    {
+        const int sl = tile * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const bool act = sl < A.nslices && i < A.n;
+        const int o = warp * 32 + lane;
+        const double vi = P.spmv(k, A, warp, lane, V.z);
+        const YRow Yr = pipe_y_row(S.alpha, S.omega, -S.alpha, -S.omega, P.vec(k, 0)[o], P.vec(k, 1)[o],
+                                   P.vec(k, 2)[o], P.vec(k, 3)[o], P.vec(k, 4)[o], vi);
+        if (act) {
+            V.x[i] = Yr.x;
+            V.v[i] = vi;
+            V.r[i] = Yr.r;
+            V.w[i] = Yr.w;
+        }
+        const double r0 = act ? P.vec(k, 5)[o] : 0.0, rn = act ? Yr.r : 0.0, wn = act ? Yr.w : 0.0;
+        const Dec dr0 = decode(r0), dr = decode(rn), dw = decode(wn);
+        D.template add2<false>(sh, 0, r0, rn, dr0, dr, act);
+        D.template add2<false>(sh, 1, r0, wn, dr0, dw, act);
+        D.template add2<true>(sh, 2, rn, rn, dr, dr, act);
+    }
+};
+
+template <int MODE, class Step>
+__global__ void __launch_bounds__(THREADS, 2) k_bstaged(Mat A, Vecs V, Batch B)
+{
+    constexpr int ND = Step::ND, NV = Step::NV;
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ Shm<ND> sh;
+    __shared__ uint64_t bar[NSTAGE];
+    __shared__ StageInfo info[NSTAGE];
+    __shared__ BTag tag[NSTAGE];
+    shm_init<ND, MODE>(sh);
+    TilePipe<NV, true> P{dsm, bar, info};
+    DotSet<ND, MODE> D;
+    D.init();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // thread 0: cursor over this CTA's contiguous chunk [q0, q1) of the tile
+    // list (the live list of a pool, else all tiles)
+    const bool listed = B.lv_n != nullptr;
+    const int nq = listed ? B.lv_n[1] : B.ntiles;
+    const int q1 = (int)(((long long)nq * (blockIdx.x + 1)) / gridDim.x);
+    int q = (int)(((long long)nq * blockIdx.x) / gridDim.x), j = 0, ls = -1, lf = 0;
+    bool lw = false;
+    if (threadIdx.x == 0 && listed && q < q1) {
+        int lo = 0, hi = B.lv_n[0] - 1;                // last live system with lv_pre[j] <= q
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.lv_pre[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        j = lo;
+    }
+    // next tile this pass serves (thread 0); -1 when none is left
+    auto next_tile = [&](BTag &tg) {
+        tg.tile = -1;
+        while (q < q1) {
+            int t = q, qend;
+            if (listed) {
+                while (B.lv_pre[j + 1] <= q)
+                    j++;
+                t = B.lv_t0[j] + (q - B.lv_pre[j]);
+            }
+            const int sys = B.tile_sys[t];
+            if (sys >= 0) {
+                if (sys != ls) {
+                    ls = sys;
+                    lw = Step::wants(B.ctl + sys);
+                    lf = Step::flags(B.ctl + sys);
+                }
+                if (lw) {
+                    tg.tile = t;
+                    tg.sys = sys;
+                    tg.first = lf;
+                    q++;
+                    return;
+                }
+                qend = listed ? B.lv_pre[j + 1] : B.sys_t1[sys];    // skip the rest of this system
+            } else {
+                qend = q + 1;
+            }
+            q = max(q + 1, min(q1, qend));
+        }
+    };
+    auto issue = [&](int k, const BTag &tg) {
+        const double *src[NV];
+        const double *gx;
+        Step::srcs(V, tg.first, src, gx);
+        const int s0 = tg.tile * TILE_SLICES;
+        int rec[TMETA];
+        rec[0] = A.sl_off[s0];
+        rec[1] = A.sl_w ? A.sl_off[s0 + TILE_SLICES - 1] + 32 * A.sl_w[s0 + TILE_SLICES - 1] : A.sl_off[s0 + TILE_SLICES];
+#pragma unroll
+        for (int g = 2; g < TMETA; g++)
+            rec[g] = -1;
+        P.issue(k, tg.tile, rec, A, src, NV, gx, -1);
+    };
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NSTAGE; k++)
+            mbar_init(&bar[k], 1);
+        fence_mbar_init();
+        fence_async_shared();
+        for (int k = 0; k < NSTAGE; k++) {
+            next_tile(tag[k]);
+            if (tag[k].tile >= 0)
+                issue(k, tag[k]);
+        }
+    }
+    __syncthreads();
+    int cur = -1, t_first = -1, cnt = 0;
+    bool tmo = false;
+    typename Step::Scal S;
+    int c = 0;
+    for (;; c++) {
+        const int k = c % NSTAGE;
+        const BTag tg = tag[k];
+        if (tg.tile < 0)
+            break;
+        const bool ok = mbar_wait_bounded(&bar[k], (uint32_t)(c / NSTAGE) & 1u);
+        if (__syncthreads_or(!ok)) {
+            tmo = true;
+            break;
+        }
+        if (tg.sys != cur) {
+            if (cur >= 0 && cnt > 0) {
+                b_flush<ND, MODE, Step>(D, sh, B, cur, t_first, cnt, V);
+                D.init();
+            }
+            cur = tg.sys;
+            t_first = tg.tile;
+            cnt = 0;
+            S = Step::load(B.ctl + cur);
+        }
+        if (MODE == 0 && threadIdx.x < ND)
+            B.part[(size_t)tg.tile * MAXD + threadIdx.x] = 0.0;
+        Step::template row<MODE>(P, k, A, V, S, tg.tile, warp, lane, D, sh);
+        cnt++;
+        __syncthreads();                       // stage k consumed by every warp
+        if (threadIdx.x == 0) {
+            next_tile(tag[k]);
+            if (tag[k].tile >= 0)
+                issue(k, tag[k]);
+        }
+    }
+    if (tmo) {
+        // give up: wait (bounded) for this CTA's copies still in flight, flag the systems
+        if (threadIdx.x == 0) {
+            for (int cc = c; cc < c + NSTAGE; cc++) {
+                const BTag tg = tag[cc % NSTAGE];
+                if (tg.tile >= 0) {
+                    mbar_wait_bounded(&bar[cc % NSTAGE], (uint32_t)(cc / NSTAGE) & 1u);
+                    atomicOr(&B.ctl[tg.sys].err, 1);
+                }
+            }
+            if (cur >= 0)
+                atomicOr(&B.ctl[cur].err, 1);
+        }
+        __syncthreads();
+        return;
+    }
+    if (cur >= 0 && cnt > 0)
+        b_flush<ND, MODE, Step>(D, sh, B, cur, t_first, cnt, V);
+}
 
 // P(i), i >= 1 (BiCGStab): p = fma(beta, fma(-omega, s, p), r)
 struct StepBicgP {
@@ -612,7 +858,7 @@ struct PoolSetup3 : StepSetup3 {
 __device__ __forceinline__ bool pool_live(const Ctl &c)
 {
     const int st = c.status;
-    return st == ST_RUNNING || st == ST_CANDIDATE || st == ST_SETUP1 || st == ST_SETUP2 || c.need_t == 1;
+    return c.err == 0 && (st == ST_RUNNING || st == ST_CANDIDATE || st == ST_SETUP1 || st == ST_SETUP2 || c.need_t == 1);
 }
 
 __global__ void __launch_bounds__(1024) k_pool_ctl(Batch B, int *lv_n, int *lv_pre, int *lv_t0, int *left,
@@ -710,10 +956,21 @@ __global__ void k_pool_scatter(int n, int nrows, int row0, const int *__restrict
 
 // a slot joins the sweep: its tiles, its tile range and its control block
 __global__ void k_pool_activate(int *tile_sys, int *sys_t0, int *sys_t1, Ctl *ctl, int sid, int t0, int ntl,
-                                Ctl init, const int *bad)
+                                Ctl init, const int *bad, unsigned *done, GAcc *acc)
 {
     for (int t = threadIdx.x; t < ntl; t += blockDim.x)
         tile_sys[t0 + t] = sid;
+    // a previous occupant stopped by an expired wait may have left partial sums
+    GAcc *g = acc + (size_t)sid * MAXD;
+    for (int k = threadIdx.x; k < MAXD * NDIG; k += blockDim.x)
+        g[k / NDIG].dig[k % NDIG] = 0ull;
+    if (threadIdx.x < MAXD) {
+        g[threadIdx.x].kmin = NDIG;
+        g[threadIdx.x].kmax = -1;
+        g[threadIdx.x].nf = 0;
+    }
+    if (threadIdx.x == 0)
+        done[sid] = 0u;
     if (threadIdx.x == 0) {
         sys_t0[sid] = t0;
         sys_t1[sid] = t0 + ntl;
@@ -744,6 +1001,10 @@ __global__ void k_batch_ctl(Batch B, unsigned long long handle, int use_cond)
     __syncthreads();
     for (int s = threadIdx.x; s < B.nsys; s += blockDim.x) {
         int st = B.ctl[s].status;
+        if ((st == ST_RUNNING || st == ST_CANDIDATE) && B.ctl[s].err) {
+            B.ctl[s].status = ST_TIMEOUT;             // a bounded wait expired: the system stops
+            st = ST_TIMEOUT;
+        }
         if (st == ST_RUNNING || st == ST_CANDIDATE)
             any = 1;
     }

@@ -917,6 +917,7 @@ struct TilePipe {
         info[k].e0 = e0;
         info[k].staged = staged;
         info[k].windowed = windowed;
+        info[k].tile = tile;
         uint32_t bytes = (uint32_t)nv * TILE_ROWS * 8 + L::RLEN + L::SLOFF + (staged ? (uint32_t)span * 12u : 0u) +
                          (uint32_t)nblk * TILE_ROWS * 8 + (tn >= 0 ? TMETA * 4u : 0u);
         fence_async_shared();
@@ -947,7 +948,9 @@ struct TilePipe {
     {
         const int *so = sloff(k);
         const int off = so[warp];
-        const int width = (so[warp + 1] - off) >> 5;
+        // the slice's width: explicit for pools (a tile's last slice need not be
+        // followed by the same slot's entries), else the distance to the next slice
+        const int width = A.sl_w ? __ldg(A.sl_w + (size_t)(info[k].tile * TILE_SLICES + warp)) : (so[warp + 1] - off) >> 5;
         const int len = rlen(k)[warp * 32 + lane];
         const bool st = info[k].staged;
         const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
@@ -1085,6 +1088,51 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
     }
 }
 
+// Row arithmetic of the p-BiCGStab passes (Algorithm 2), shared by the
+// single-system and batched passes so that both round identically.
+// Pass X: p, s, z (bit copies of r, w, t at i = 0; kept as they are right
+// after a residual replacement), then q and y.
+struct XRow {
+    double p, s, z, q, y;
+};
+
+__device__ __forceinline__ XRow pipe_x_row(bool first, bool rr, double nalpha, double beta, double nomega, double ri,
+                                           double wi, double ti, double pold, double sold, double zold, double vold)
+{
+    XRow o;
+    if (first) {
+        o.p = ri;
+        o.s = wi;
+        o.z = ti;
+    } else if (rr) {
+        o.p = pold;
+        o.s = sold;
+        o.z = zold;
+    } else {
+        o.p = __fma_rn(beta, __fma_rn(nomega, sold, pold), ri);
+        o.s = __fma_rn(beta, __fma_rn(nomega, zold, sold), wi);
+        o.z = __fma_rn(beta, __fma_rn(nomega, vold, zold), ti);
+    }
+    o.q = __fma_rn(nalpha, o.s, ri);
+    o.y = __fma_rn(nalpha, o.z, wi);
+    return o;
+}
+
+// Pass Y: x_{i+1}, r_{i+1}, w_{i+1} from q, y, p, x, t and v = A z.
+struct YRow {
+    double x, r, w;
+};
+
+__device__ __forceinline__ YRow pipe_y_row(double alpha, double omega, double nalpha, double nomega, double q, double y,
+                                           double p, double x, double t, double v)
+{
+    YRow o;
+    o.x = __fma_rn(omega, q, __fma_rn(alpha, p, x));
+    o.r = __fma_rn(nomega, y, q);
+    o.w = __fma_rn(nomega, __fma_rn(nalpha, v, t), y);
+    return o;
+}
+
 // X(i) staged: t_i = A w_i (i >= 1), p, s, z, q, y; dots (q,y), (y,y), (r0,s), (r0,z); omega_i
 template <int MODE, bool MATS>
 __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
@@ -1113,34 +1161,27 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
         if (sl < A.nslices) {
             const double ri = P.vec(k, 0)[o], wi = P.vec(k, 1)[o];
             r0i = P.vec(k, 2)[o];
-            double pi, ti;
+            double ti, pold = 0.0, sold = 0.0, zold = 0.0, vold = 0.0;
             if (first) {
                 ti = P.vec(k, 3)[o];
-                pi = ri;
-                si = wi;
-                zi = ti;
             } else {
                 ti = P.spmv(k, A, warp, lane, V.w);
-                const double pold = P.vec(k, 3)[o], sold = P.vec(k, 4)[o];
-                const double zold = P.vec(k, 5)[o], vold = P.vec(k, 6)[o];
-                if (rr) {
-                    pi = pold;
-                    si = sold;
-                    zi = zold;
-                } else {
-                    pi = __fma_rn(beta, __fma_rn(nomega, sold, pold), ri);
-                    si = __fma_rn(beta, __fma_rn(nomega, zold, sold), wi);
-                    zi = __fma_rn(beta, __fma_rn(nomega, vold, zold), ti);
-                }
+                pold = P.vec(k, 3)[o];
+                sold = P.vec(k, 4)[o];
+                zold = P.vec(k, 5)[o];
+                vold = P.vec(k, 6)[o];
             }
-            q = __fma_rn(nalpha, si, ri);
-            y = __fma_rn(nalpha, zi, wi);
+            const XRow X = pipe_x_row(first, rr, nalpha, beta, nomega, ri, wi, ti, pold, sold, zold, vold);
+            si = X.s;
+            zi = X.z;
+            q = X.q;
+            y = X.y;
             if (act) {
                 if (!first)
                     V.t[i] = ti;
-                V.p[i] = pi;
-                V.s[i] = si;
-                V.z[i] = zi;
+                V.p[i] = X.p;
+                V.s[i] = X.s;
+                V.z[i] = X.z;
                 V.q[i] = q;
                 V.y[i] = y;
             }
@@ -1195,13 +1236,13 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
         double rn = 0.0, wn = 0.0, r0i = 0.0;
         if (sl < A.nslices) {
             const double vi = P.spmv(k, A, warp, lane, V.z);
-            const double q = P.vec(k, 0)[o], y = P.vec(k, 1)[o];
-            const double xn = __fma_rn(omega, q, __fma_rn(alpha, P.vec(k, 2)[o], P.vec(k, 3)[o]));
-            rn = __fma_rn(nomega, y, q);
-            wn = __fma_rn(nomega, __fma_rn(nalpha, vi, P.vec(k, 4)[o]), y);
+            const YRow Yr = pipe_y_row(alpha, omega, nalpha, nomega, P.vec(k, 0)[o], P.vec(k, 1)[o], P.vec(k, 2)[o],
+                                       P.vec(k, 3)[o], P.vec(k, 4)[o], vi);
+            rn = Yr.r;
+            wn = Yr.w;
             r0i = P.vec(k, 5)[o];
             if (act) {
-                V.x[i] = xn;
+                V.x[i] = Yr.x;
                 V.v[i] = vi;
                 V.r[i] = rn;
                 V.w[i] = wn;

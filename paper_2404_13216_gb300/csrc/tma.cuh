@@ -111,6 +111,7 @@ struct StageInfo {
     int e0;          // first SELL entry of the tile
     int staged;      // 1 if the tile's ci/va are in shared memory
     int windowed;    // 1 if the gathered vector's blocks are in shared memory (ci local)
+    int tile;        // the tile held
 };
 
 }  // namespace pbcg
