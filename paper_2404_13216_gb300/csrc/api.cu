@@ -462,9 +462,9 @@ struct Kern {
     static void *pipe_y_tma(bool mats) { return mats ? (void *)k_pipe_y_tma<MODE, true> : (void *)k_pipe_y_tma<MODE, false>; }
     static void *setup1() { return (void *)k_setup1<MODE>; }
     static void *setup2() { return (void *)k_setup2<MODE>; }
-    static void *bicg_a() { return (void *)k_bicg_a<MODE>; }
-    static void *bicg_b() { return (void *)k_bicg_b<MODE>; }
-    static void *bicg_c() { return (void *)k_bicg_c<MODE>; }
+    static void *bicg_a(bool mats) { return mats ? (void *)k_bicg_a_tma<MODE, true> : (void *)k_bicg_a_tma<MODE, false>; }
+    static void *bicg_b(bool mats) { return mats ? (void *)k_bicg_b_tma<MODE, true> : (void *)k_bicg_b_tma<MODE, false>; }
+    static void *bicg_c() { return (void *)k_bicg_c_tma<MODE>; }
 };
 
 // kernel list of one loop body
@@ -492,10 +492,15 @@ std::vector<BodyKernel> body_kernels(int alg, int mode, bool narrow)
         k.push_back({mode ? Kern<1>::pipe_y_tma(narrow) : Kern<0>::pipe_y_tma(narrow),
                      mode ? "pipe_y_exact" : "pipe_y_plain", 1, sy});
     } else {
-        k.push_back({(void *)k_bicg_p, "bicg_p", 0, 0});
-        k.push_back({mode ? Kern<1>::bicg_a() : Kern<0>::bicg_a(), mode ? "bicg_a_exact" : "bicg_a_plain", 1, 0});
-        k.push_back({mode ? Kern<1>::bicg_b() : Kern<0>::bicg_b(), mode ? "bicg_b_exact" : "bicg_b_plain", 1, 0});
-        k.push_back({mode ? Kern<1>::bicg_c() : Kern<0>::bicg_c(), mode ? "bicg_c_exact" : "bicg_c_plain", 1, 0});
+        const size_t sa = narrow ? stage_bytes<1, true>() : stage_bytes<1, false>();
+        const size_t sb = narrow ? stage_bytes<2, true>() : stage_bytes<2, false>();
+        k.push_back({(void *)k_bicg_p_tma, "bicg_p", 1, stage_bytes<3, false>()});
+        k.push_back({mode ? Kern<1>::bicg_a(narrow) : Kern<0>::bicg_a(narrow), mode ? "bicg_a_exact" : "bicg_a_plain", 1,
+                     sa});
+        k.push_back({mode ? Kern<1>::bicg_b(narrow) : Kern<0>::bicg_b(narrow), mode ? "bicg_b_exact" : "bicg_b_plain", 1,
+                     sb});
+        k.push_back({mode ? Kern<1>::bicg_c() : Kern<0>::bicg_c(), mode ? "bicg_c_exact" : "bicg_c_plain", 1,
+                     stage_bytes<6, false>()});
     }
     return k;
 }

@@ -543,153 +543,6 @@ static __global__ void __launch_bounds__(THREADS) k_setup3(Mat A, Vecs V, const 
 }
 
 // ---------------------------------------------------------------------------
-// BiCGStab passes
-// ---------------------------------------------------------------------------
-// P(i), i >= 1: p = fma(beta, fma(-omega, s, p), r)
-static __global__ void __launch_bounds__(THREADS) k_bicg_p(Mat A, Vecs V, const Ctl *c)
-{
-    if (c->status != ST_RUNNING || c->it == 0)
-        return;
-    const double beta = c->beta, nomega = -c->omega;
-    PBCG_SLICE_LOOP(A)
-    {
-        int i = PBCG_ROW;
-        if (i < A.n)
-            V.p[i] = __fma_rn(beta, __fma_rn(nomega, V.s[i], V.p[i]), V.r[i]);
-    }
-}
-
-// A(i): s = A p; dot (r0, s); alpha_i
-template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_bicg_a(Mat A, Vecs V, Ctl *c, Work *wk)
-{
-    if (c->status != ST_RUNNING)
-        return;
-    __shared__ Shm<1> sh;
-    shm_init<1, MODE>(sh);
-    __syncthreads();
-    DotSet<1, MODE> D;
-    D.init();
-    PBCG_SLICE_LOOP(A)
-    {
-        int i = PBCG_ROW;
-        bool act = i < A.n;
-        RowRef R = row_ref(A, sl_, wr_.lane);
-        double si = spmv_row(A, R, V.p);
-        double r0i = 0.0;
-        if (act) {
-            V.s[i] = si;
-            r0i = V.r0[i];
-        }
-        D.add(sh, 0, r0i, si, act);
-    }
-    if (!finalize<1, MODE>(D, sh, wk))
-        return;
-    if (threadIdx.x == 0) {
-        double rs = sh.dv[0];
-        c->rs = rs;
-        if (!fin(rs)) {
-            c->status = 3;
-        } else {
-            double a = __ddiv_rn(c->rho, rs);
-            if (!fin(a))
-                c->status = 2;
-            else
-                c->alpha = a;
-        }
-        if (c->status != ST_RUNNING)
-            set_cond(c);
-    }
-}
-
-// B(i): y = A q with q_j = fma(-alpha, s_j, r_j) formed in the gather; dots (q,y), (y,y); omega_i
-template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_bicg_b(Mat A, Vecs V, Ctl *c, Work *wk)
-{
-    if (c->status != ST_RUNNING)
-        return;
-    __shared__ Shm<2> sh;
-    shm_init<2, MODE>(sh);
-    __syncthreads();
-    const double nalpha = -c->alpha;
-    DotSet<2, MODE> D;
-    D.init();
-    PBCG_SLICE_LOOP(A)
-    {
-        int i = PBCG_ROW;
-        bool act = i < A.n;
-        RowRef R = row_ref(A, sl_, wr_.lane);
-        double yi = spmv_row_axpy(A, R, nalpha, V.s, V.r);
-        double qi = 0.0;
-        if (act) {
-            qi = __fma_rn(nalpha, V.s[i], V.r[i]);
-            V.y[i] = yi;
-        }
-        D.add(sh, 0, qi, yi, act);
-        D.add(sh, 1, yi, yi, act);
-    }
-    if (!finalize<2, MODE>(D, sh, wk))
-        return;
-    if (threadIdx.x == 0) {
-        double qy = sh.dv[0], yy = sh.dv[1];
-        c->qy = qy;
-        c->yy = yy;
-        if (!fin(qy) || !fin(yy)) {
-            c->status = 3;
-            set_cond(c);
-        } else {
-            c->omega = (yy == 0.0) ? 0.0 : __ddiv_rn(qy, yy);
-        }
-    }
-}
-
-// C(i): x, r updates; dots (r0,r), (r,r); beta_i, stop test
-template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_bicg_c(Mat A, Vecs V, Ctl *c, Work *wk)
-{
-    if (c->status != ST_RUNNING)
-        return;
-    __shared__ Shm<2> sh;
-    shm_init<2, MODE>(sh);
-    __syncthreads();
-    const double alpha = c->alpha, omega = c->omega;
-    const double nalpha = -alpha, nomega = -omega;
-    DotSet<2, MODE> D;
-    D.init();
-    PBCG_SLICE_LOOP(A)
-    {
-        int i = PBCG_ROW;
-        bool act = i < A.n;
-        double rn = 0.0, r0i = 0.0;
-        if (act) {
-            double si = V.s[i], ri = V.r[i], pi = V.p[i], xi = V.x[i], yi = V.y[i];
-            r0i = V.r0[i];
-            double q = __fma_rn(nalpha, si, ri);
-            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, pi, xi));
-            rn = __fma_rn(nomega, yi, q);
-            V.r[i] = rn;
-        }
-        D.add(sh, 0, r0i, rn, act);
-        D.add(sh, 1, rn, rn, act);
-    }
-    if (!finalize<2, MODE>(D, sh, wk))
-        return;
-    if (threadIdx.x == 0) {
-        double rho_new = sh.dv[0], rr = sh.dv[1];
-        c->rho_new = rho_new;
-        c->rr = rr;
-        c->phase = PH_ITER;
-        if (!fin(rho_new) || !fin(rr)) {
-            c->status = 3;
-        } else {
-            c->it += 1;
-            residual_step(c, rr);
-        }
-        set_cond(c);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // true residual ||b - A x|| / ||b|| with exact dots; resolves a candidate stop
 // ---------------------------------------------------------------------------
 static __global__ void __launch_bounds__(THREADS) k_true_res(Mat A, Vecs V, Ctl *c, Work *wk)
@@ -987,6 +840,44 @@ struct TilePipe {
         }
         return acc;
     }
+
+    // SpMV row of (r - alpha s) with alpha = -na: each gathered entry forms
+    // fma(na, s_j, r_j) first (one rounding), then the row's fma chain
+    __device__ __forceinline__ double spmv_axpy(int k, const Mat &A, int warp, int lane, double na,
+                                                const double *__restrict__ s, const double *__restrict__ r) const
+    {
+        const int *so = sloff(k);
+        const int off = so[warp];
+        const int width = A.sl_w ? __ldg(A.sl_w + (size_t)(info[k].tile * TILE_SLICES + warp)) : (so[warp + 1] - off) >> 5;
+        const int len = rlen(k)[warp * 32 + lane];
+        const bool st = info[k].staged;
+        const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
+        const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
+        double acc = 0.0;
+        for (int j0 = 0; j0 < width; j0 += UNR) {
+            int c[UNR];
+            double v[UNR], xs[UNR], xr[UNR];
+#pragma unroll
+            for (int j = 0; j < UNR; j++) {
+                if (j0 + j < len) {
+                    c[j] = cp[(j0 + j) * 32];
+                    v[j] = vp[(j0 + j) * 32];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < UNR; j++) {
+                if (j0 + j < len) {
+                    xs[j] = __ldg(s + c[j]);
+                    xr[j] = __ldg(r + c[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < UNR; j++)
+                if (j0 + j < len)
+                    acc = __fma_rn(v[j], __fma_rn(na, xs[j], xr[j]), acc);
+        }
+        return acc;
+    }
 };
 
 // Common tile loop.  No CTA-wide barrier per tile: each warp waits on the
@@ -1271,6 +1162,186 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
         }
         set_cond(c);
     }
+}
+
+// ---------------------------------------------------------------------------
+// BiCGStab passes, staged like the p-BiCGStab passes (Algorithm 1)
+// ---------------------------------------------------------------------------
+// last-CTA tails shared with the unstaged passes
+__device__ __forceinline__ void bicg_a_scalar(Ctl *c, double rs)
+{
+    c->rs = rs;
+    if (c->err) {
+        c->status = ST_TIMEOUT;
+    } else if (!fin(rs)) {
+        c->status = 3;
+    } else {
+        double a = __ddiv_rn(c->rho, rs);
+        if (!fin(a))
+            c->status = 2;
+        else
+            c->alpha = a;
+    }
+    if (c->status != ST_RUNNING)
+        set_cond(c);
+}
+
+__device__ __forceinline__ void bicg_b_scalar(Ctl *c, double qy, double yy)
+{
+    c->qy = qy;
+    c->yy = yy;
+    if (c->err) {
+        c->status = ST_TIMEOUT;
+        set_cond(c);
+    } else if (!fin(qy) || !fin(yy)) {
+        c->status = 3;
+        set_cond(c);
+    } else {
+        c->omega = (yy == 0.0) ? 0.0 : __ddiv_rn(qy, yy);
+    }
+}
+
+__device__ __forceinline__ void bicg_c_scalar(Ctl *c, double rho_new, double rr)
+{
+    c->rho_new = rho_new;
+    c->rr = rr;
+    c->phase = PH_ITER;
+    if (c->err) {
+        c->status = ST_TIMEOUT;
+    } else if (!fin(rho_new) || !fin(rr)) {
+        c->status = 3;
+    } else {
+        c->it += 1;
+        residual_step(c, rr);
+    }
+    set_cond(c);
+}
+
+// P(i), i >= 1: p = fma(beta, fma(-omega, s, p), r)
+static __global__ void __launch_bounds__(THREADS) k_bicg_p_tma(Mat A, Vecs V, Ctl *c, Work *)
+{
+    if (c->status != ST_RUNNING || c->it == 0)
+        return;
+    extern __shared__ __align__(128) uint8_t dsm[];
+    const double beta = c->beta, nomega = -c->omega;
+    const double *const src[3] = {V.s, V.p, V.r};
+    tile_loop<3, false>(A, src, 3, nullptr, c, dsm, [&](const TilePipe<3, false> &P, int k, int tile, int warp, int lane) {
+        const int sl = tile * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const int o = warp * 32 + lane;
+        if (sl < A.nslices && i < A.n)
+            V.p[i] = __fma_rn(beta, __fma_rn(nomega, P.vec(k, 0)[o], P.vec(k, 1)[o]), P.vec(k, 2)[o]);
+    });
+}
+
+// A(i): s = A p; dot (r0, s); alpha_i
+template <int MODE, bool MATS>
+__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+    k_bicg_a_tma(Mat A, Vecs V, Ctl *c, Work *wk)
+{
+    if (c->status != ST_RUNNING)
+        return;
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ Shm<1> sh;
+    shm_init<1, MODE>(sh);
+    DotSet<1, MODE> D;
+    D.init();
+    const double *const src[1] = {V.r0};
+    tile_loop<1, MATS>(A, src, 1, V.p, c, dsm, [&](const TilePipe<1, MATS> &P, int k, int tile, int warp, int lane) {
+        const int sl = tile * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const bool act = sl < A.nslices && i < A.n;
+        const int o = warp * 32 + lane;
+        double si = 0.0, r0i = 0.0;
+        if (sl < A.nslices) {
+            si = P.spmv(k, A, warp, lane, V.p);
+            r0i = P.vec(k, 0)[o];
+            if (act)
+                V.s[i] = si;
+        }
+        const Dec dr = decode(r0i), ds = decode(si);
+        D.template add2<false>(sh, 0, r0i, si, dr, ds, act);
+    });
+    if (!finalize<1, MODE>(D, sh, wk))
+        return;
+    if (threadIdx.x == 0)
+        bicg_a_scalar(c, sh.dv[0]);
+}
+
+// B(i): y = A q with q_j = fma(-alpha, s_j, r_j) formed for each gathered
+// entry (alpha is known only after pass A); dots (q,y), (y,y); omega_i
+template <int MODE, bool MATS>
+__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+    k_bicg_b_tma(Mat A, Vecs V, Ctl *c, Work *wk)
+{
+    if (c->status != ST_RUNNING)
+        return;
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ Shm<2> sh;
+    shm_init<2, MODE>(sh);
+    const double nalpha = -c->alpha;
+    DotSet<2, MODE> D;
+    D.init();
+    const double *const src[2] = {V.s, V.r};
+    tile_loop<2, MATS>(A, src, 2, nullptr, c, dsm, [&](const TilePipe<2, MATS> &P, int k, int tile, int warp, int lane) {
+        const int sl = tile * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const bool act = sl < A.nslices && i < A.n;
+        const int o = warp * 32 + lane;
+        double qi = 0.0, yi = 0.0;
+        if (sl < A.nslices) {
+            yi = P.spmv_axpy(k, A, warp, lane, nalpha, V.s, V.r);
+            qi = __fma_rn(nalpha, P.vec(k, 0)[o], P.vec(k, 1)[o]);
+            if (act)
+                V.y[i] = yi;
+        }
+        const Dec dq = decode(qi), dy = decode(yi);
+        D.template add2<false>(sh, 0, qi, yi, dq, dy, act);
+        D.template add2<true>(sh, 1, yi, yi, dy, dy, act);
+    });
+    if (!finalize<2, MODE>(D, sh, wk))
+        return;
+    if (threadIdx.x == 0)
+        bicg_b_scalar(c, sh.dv[0], sh.dv[1]);
+}
+
+// C(i): x, r updates; dots (r0,r), (r,r); beta_i, stop test
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+    k_bicg_c_tma(Mat A, Vecs V, Ctl *c, Work *wk)
+{
+    if (c->status != ST_RUNNING)
+        return;
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ Shm<2> sh;
+    shm_init<2, MODE>(sh);
+    const double alpha = c->alpha, omega = c->omega;
+    const double nalpha = -alpha, nomega = -omega;
+    DotSet<2, MODE> D;
+    D.init();
+    // stage slots: 0 s, 1 r, 2 p, 3 x, 4 y, 5 r0
+    const double *const src[6] = {V.s, V.r, V.p, V.x, V.y, V.r0};
+    tile_loop<6, false>(A, src, 6, nullptr, c, dsm, [&](const TilePipe<6, false> &P, int k, int tile, int warp, int lane) {
+        const int sl = tile * TILE_SLICES + warp;
+        const int i = sl * 32 + lane;
+        const bool act = sl < A.nslices && i < A.n;
+        const int o = warp * 32 + lane;
+        double rn = 0.0, r0i = 0.0;
+        if (act) {
+            const double q = __fma_rn(nalpha, P.vec(k, 0)[o], P.vec(k, 1)[o]);
+            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, P.vec(k, 2)[o], P.vec(k, 3)[o]));
+            rn = __fma_rn(nomega, P.vec(k, 4)[o], q);
+            V.r[i] = rn;
+            r0i = P.vec(k, 5)[o];
+        }
+        const Dec dr0 = decode(r0i), dr = decode(rn);
+        D.template add2<false>(sh, 0, r0i, rn, dr0, dr, act);
+        D.template add2<true>(sh, 1, rn, rn, dr, dr, act);
+    });
+    if (!finalize<2, MODE>(D, sh, wk))
+        return;
+    if (threadIdx.x == 0)
+        bicg_c_scalar(c, sh.dv[0], sh.dv[1]);
 }
 
 }  // namespace pbcg
