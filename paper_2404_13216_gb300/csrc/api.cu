@@ -60,7 +60,7 @@ struct pbcg_mat {
     int *ci;               // [padded], solver-order column indices
     double *va;            // [padded]
     int *perm;             // [n] solver row p holds caller row perm[p]; NULL when rows keep their order
-    int *lci;              // [padded] entry indices into a tile's staged gather blocks
+    uint16_t *lci;         // [padded] local column indices into a tile's staged gather blocks
     int *tmeta;            // [ntiles * TMETA] per tile: first and end entry, gather blocks (-1: none / too many)
     bool narrow;           // every 256-row tile spans at most MCAP SELL entries (staged in shared memory)
     std::vector<int32_t> h_rp, h_ci;   // host copy of the CSR (for per-batch layouts)
@@ -314,7 +314,8 @@ struct Sell {
     long long padded = 0;
     bool permuted = false;
     bool narrow = true;
-    std::vector<int> sl_off, rlen, ci, perm, lci, tmeta;
+    std::vector<int> sl_off, rlen, ci, perm, tmeta;
+    std::vector<uint16_t> lci;          // local column index into a tile's staged gather blocks
     std::vector<double> va;
 };
 
@@ -425,7 +426,7 @@ bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val,
         for (long long e = S.sl_off[sa]; e < S.sl_off[sb]; e++) {
             int b = S.ci[(size_t)e] / TILE_ROWS;
             int g = (int)(std::lower_bound(blocks.begin(), blocks.end(), b) - blocks.begin());
-            S.lci[(size_t)e] = g * TILE_ROWS + S.ci[(size_t)e] % TILE_ROWS;
+            S.lci[(size_t)e] = (uint16_t)(g * TILE_ROWS + S.ci[(size_t)e] % TILE_ROWS);
         }
     }
     return true;
@@ -1625,7 +1626,8 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     m->nnz = nnz;
     m->nslices = S.nslices;
     m->padded = S.padded;
-    m->sl_off = m->rlen = m->ci = m->perm = m->lci = m->tmeta = nullptr;
+    m->sl_off = m->rlen = m->ci = m->perm = m->tmeta = nullptr;
+    m->lci = nullptr;
     m->va = nullptr;
     m->narrow = S.narrow;
     m->bl = nullptr;
@@ -1643,11 +1645,11 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     if (e == cudaSuccess && S.permuted)
         e = cudaMalloc(&m->perm, sizeof(int) * (size_t)n);
     if (e == cudaSuccess)
-        e = cudaMalloc(&m->lci, sizeof(int) * P);
+        e = cudaMalloc(&m->lci, sizeof(uint16_t) * P);
     if (e == cudaSuccess)
         e = cudaMalloc(&m->tmeta, sizeof(int) * S.tmeta.size());
     if (e == cudaSuccess && S.padded)
-        e = cudaMemcpy(m->lci, S.lci.data(), sizeof(int) * (size_t)S.padded, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(m->lci, S.lci.data(), sizeof(uint16_t) * (size_t)S.padded, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(m->tmeta, S.tmeta.data(), sizeof(int) * S.tmeta.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)

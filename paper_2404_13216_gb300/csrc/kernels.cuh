@@ -79,7 +79,7 @@ struct Mat {
     const int *__restrict__ ci;          // padded column indices (solver order)
     const double *__restrict__ va;       // padded values
     const int *__restrict__ sl_w;        // [nslices] slice widths, or NULL: width = (sl_off[s+1] - sl_off[s]) / 32
-    const int *__restrict__ lci;         // padded local indices into a tile's staged blocks (or NULL)
+    const uint16_t *__restrict__ lci;    // padded local indices (< GMAX * 256) into a tile's staged blocks (or NULL)
     const int *__restrict__ tmeta;       // [ntiles * TMETA] per tile: first and end SELL entry, then the GMAX
                                          // 256-row blocks it gathers from (-1 pad; all -1: gathers from global)
 };
@@ -771,7 +771,7 @@ struct TilePipe {
         info[k].staged = staged;
         info[k].windowed = windowed;
         info[k].tile = tile;
-        uint32_t bytes = (uint32_t)nv * TILE_ROWS * 8 + L::RLEN + L::SLOFF + (staged ? (uint32_t)span * 12u : 0u) +
+        uint32_t bytes = (uint32_t)nv * TILE_ROWS * 8 + L::RLEN + L::SLOFF + (staged ? (uint32_t)span * (windowed ? 10u : 12u) : 0u) +
                          (uint32_t)nblk * TILE_ROWS * 8 + (tn >= 0 ? TMETA * 4u : 0u);
         fence_async_shared();
         mbar_arrive_expect_tx(&bar[k], bytes);
@@ -784,7 +784,10 @@ struct TilePipe {
         if (tn >= 0)
             bulk_g2s(tail + L::RLEN + L::SLOFF, A.tmeta + (size_t)tn * TMETA, TMETA * 4, &bar[k]);
         if (staged) {
-            bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA, (windowed ? A.lci : A.ci) + e0, (uint32_t)span * 4u, &bar[k]);
+            if (windowed)
+                bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA, A.lci + e0, (uint32_t)span * 2u, &bar[k]);
+            else
+                bulk_g2s(stage(k) + L::VEC + L::GWIN + L::VA, A.ci + e0, (uint32_t)span * 4u, &bar[k]);
             bulk_g2s(stage(k) + L::VEC + L::GWIN, A.va + e0, (uint32_t)span * 8u, &bar[k]);
         }
         if (windowed) {
@@ -809,13 +812,14 @@ struct TilePipe {
         const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
         const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
         double acc = 0.0;
-        if (info[k].windowed) {                         // gather from the staged blocks
+        if (info[k].windowed) {                         // gather from the staged blocks (16-bit local indices)
             const double *xw = gwin(k);
+            const uint16_t *lp = reinterpret_cast<const uint16_t *>(ci(k)) + (off - info[k].e0) + lane;
             for (int j0 = 0; j0 < width; j0 += UNR) {
 #pragma unroll
                 for (int j = 0; j < UNR; j++)
                     if (j0 + j < len)
-                        acc = __fma_rn(vp[(j0 + j) * 32], xw[cp[(j0 + j) * 32]], acc);
+                        acc = __fma_rn(vp[(j0 + j) * 32], xw[lp[(j0 + j) * 32]], acc);
             }
             return acc;
         }

@@ -87,7 +87,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 // Dynamic shared memory of a staged pass with NV input vectors:
 // NSTAGE stages of { vec[NV][256] f64, gwin[GMAX][256] f64 (if staged), va[MCAP] f64 (if staged),
-// ci[MCAP] i32 (if staged), rlen[256] i32, sl_off[16] i32, meta[TMETA] i32 }.
+// ci[MCAP] i32 or 16-bit local indices (if staged), rlen[256] i32, sl_off[16] i32, meta[TMETA] i32 }.
 // meta holds the record of the tile this stage takes next, so the warp that
 // refills the stage needs no global load.
 // When a tile's columns fall in at most GMAX 256-row blocks, those blocks of
