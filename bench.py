@@ -260,6 +260,9 @@ def run_ours(args):
     serving = None
     if not args.no_serving and ws == 1:
         serving = run_serving_leg(requests=args.serving_requests)
+        # the same stream thinned to an arrival rate below the measured capacity
+        sub = max(1.0, round(0.5 * serving["solves_per_s"]))
+        serving["sub_capacity"] = run_serving_leg(requests=max(50, int(12 * sub)), rate=sub)
     x_d.zero_()
     _, prof_e = ctx.profile_solve(M, b_d, x_d, TOL, MAXIT, pbcg.PIPELINED, pbcg.EXACT)
     x_d.zero_()
