@@ -263,6 +263,9 @@ def run_ours(args):
         # the same stream thinned to an arrival rate below the measured capacity
         sub = max(1.0, round(0.5 * serving["solves_per_s"]))
         serving["sub_capacity"] = run_serving_leg(requests=max(50, int(12 * sub)), rate=sub)
+        # the same stream solved with residual replacement every 50 iterations
+        from paper_2404_13216_gb300 import pbcg as _p
+        serving["residual_replacement"] = run_serving_leg(requests=args.serving_requests, alg=_p.PIPELINED_RR)
     x_d.zero_()
     _, prof_e = ctx.profile_solve(M, b_d, x_d, TOL, MAXIT, pbcg.PIPELINED, pbcg.EXACT)
     x_d.zero_()
@@ -468,7 +471,7 @@ def run_config_legs(ctx, pbcg, torch, dev, peak):
     return out
 
 
-def run_serving_leg(requests=1000, rate=2000.0, templates=64, K=8, maxit=2000):
+def run_serving_leg(requests=1000, rate=2000.0, templates=64, K=8, maxit=2000, alg=None):
     """Config 5: an open-loop Poisson stream of solves (2D/3D convection-diffusion,
     n log-uniform 4k..1M, tol 1e-8 or 1e-10, exact or plain dots) through two
     pools (exact, plain) with continuous batching; latency = arrival to result."""
@@ -476,10 +479,14 @@ def run_serving_leg(requests=1000, rate=2000.0, templates=64, K=8, maxit=2000):
     reqs = inputs.serving_requests(count=requests, rate=rate, seed=5)
     tmpl = serve.make_templates(reqs, templates)
     ce, cp = pbcg.Context(0), pbcg.Context(0)
-    pools = serve.make_pools(ce, cp, tmpl, 48 << 20, 384 << 20, 512, maxit, pbcg.PIPELINED)
+    alg = pbcg.PIPELINED if alg is None else alg
+    for c in (ce, cp):
+        c.set_option(pbcg.OPT_RR_PERIOD, 50)
+    pools = serve.make_pools(ce, cp, tmpl, 48 << 20, 384 << 20, 512, maxit, alg)
     out = serve.serve(reqs, tmpl, pools, K=K, maxit=maxit)
     summary = serve.summarize(reqs, tmpl, out, rate)
-    summary.update({"iters_per_step": K, "maxit_limit": maxit, "alg": "p-BiCGStab",
+    summary.update({"iters_per_step": K, "maxit_limit": maxit,
+                    "alg": "p-BiCGStab" if alg == pbcg.PIPELINED else "p-BiCGStabRR (k = 50)",
                     "pool": {"max_rows": 48 << 20, "max_entries": 384 << 20, "max_slots": 512}})
     for p in pools.values():
         p.close()
@@ -510,7 +517,7 @@ def run_ncu_case(args):
     with pbcg.Context(0) as ctx:
         M = ctx.upload_csr(A)
         x = np.zeros(A.n)
-        res, prof = ctx.profile_solve(M, b, x, 1e-300, args.ncu_iters, pbcg.PIPELINED, mode)
+        res, prof = ctx.profile_solve(M, b, x, 1e-300, args.ncu_iters, args.ncu_alg, mode)
         print(json.dumps({"case": args.ncu_case, "n": A.n, "iters": res.iters,
                           "kernels": {k: {"launches": c, "avg_us": 1e3 * t / c} for k, (t, c) in prof.items()}}))
     return 0
@@ -522,6 +529,7 @@ def main():
                     help="run a short fixed solve for a profiler and exit")
     ap.add_argument("--ncu-side", type=int, default=N_SIDE)
     ap.add_argument("--ncu-iters", type=int, default=12)
+    ap.add_argument("--ncu-alg", type=int, default=1, help="0 BiCGStab, 1 p-BiCGStab, 2 p-BiCGStabRR")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
