@@ -1040,9 +1040,9 @@ std::vector<BKernel> batch_body(int alg)
     }
     if (alg == PBCG_ALG_PIPELINED || alg == PBCG_ALG_PIPELINED_RR) {
         k.push_back({(void *)k_bstaged<MODE, BPipeX>, MODE ? "b_pipe_x_exact" : "b_pipe_x_plain",
-                     StageLayout<BPipeX::NV, true>::TOTAL});
+                     StageLayout<BPipeX::NV, true, false>::TOTAL});
         k.push_back({(void *)k_bstaged<MODE, BPipeY>, MODE ? "b_pipe_y_exact" : "b_pipe_y_plain",
-                     StageLayout<BPipeY::NV, true>::TOTAL});
+                     StageLayout<BPipeY::NV, true, false>::TOTAL});
     } else {
         k.push_back({(void *)k_batched<MODE, StepBicgP>, "b_bicg_p", 0});
         k.push_back({(void *)k_batched<MODE, StepBicgA>, MODE ? "b_bicg_a_exact" : "b_bicg_a_plain", 0});
@@ -1448,8 +1448,8 @@ std::vector<BKernel> pool_body(int alg)
         k.push_back({(void *)k_batched<MODE, StepBicgB>, "pool_bicg_b", 0});
         k.push_back({(void *)k_batched<MODE, StepBicgC>, "pool_bicg_c", 0});
     } else {
-        k.push_back({(void *)k_bstaged<MODE, BPipeX>, "pool_pipe_x", StageLayout<BPipeX::NV, true>::TOTAL});
-        k.push_back({(void *)k_bstaged<MODE, BPipeY>, "pool_pipe_y", StageLayout<BPipeY::NV, true>::TOTAL});
+        k.push_back({(void *)k_bstaged<MODE, BPipeX>, "pool_pipe_x", StageLayout<BPipeX::NV, true, false>::TOTAL});
+        k.push_back({(void *)k_bstaged<MODE, BPipeY>, "pool_pipe_y", StageLayout<BPipeY::NV, true, false>::TOTAL});
     }
     return k;
 }

@@ -381,10 +381,12 @@ struct StepPipeY {
 // flush group can close at any tile.  Row arithmetic and dots are those of
 // the generic steps (pipe_x_row / pipe_y_row), so results are bit-identical.
 // ---------------------------------------------------------------------------
-struct BTag {
-    int tile;        // -1: no more tiles for this CTA
-    int sys;
-    int first;       // pass X: the system's first iteration (no SpMV, t staged in p's slot)
+constexpr int BLIST = 512;     // tile positions of a CTA's chunk scheduled per round
+
+// one scheduled tile of a staged batched pass
+struct BEntry {
+    int tile, sys, first;        // first: pass X at the system's first iteration
+    int e0, e1;                  // the tile's SELL entry range
 };
 
 struct BPipeX : StepPipeX {
@@ -402,7 +404,7 @@ struct BPipeX : StepPipeX {
         gx = first ? nullptr : V.w;
     }
     template <int MODE>
-    static __device__ __forceinline__ void row(const TilePipe<NV, true> &P, int k, const Mat &A, const Vecs &V,
+    static __device__ __forceinline__ void row(const TilePipe<NV, true, false> &P, int k, const Mat &A, const Vecs &V,
                                                const Scal &S, int tile, int warp, int lane, DotSet<ND, MODE> &D,
                                                Shm<ND> &sh)
     {
@@ -448,7 +450,7 @@ struct BPipeY : StepPipeY {
         gx = V.z;
     }
     template <int MODE>
-    static __device__ __forceinline__ void row(const TilePipe<NV, true> &P, int k, const Mat &A, const Vecs &V,
+    static __device__ __forceinline__ void row(const TilePipe<NV, true, false> &P, int k, const Mat &A, const Vecs &V,
                                                const Scal &S, int tile, int warp, int lane, DotSet<ND, MODE> &D,
                                                Shm<ND> &sh)
     {
@@ -473,6 +475,18 @@ struct BPipeY : StepPipeY {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Staged batched passes (p-BiCGStab X and Y).
+//
+// Each CTA serves one contiguous chunk of the tile list.  A round first
+// schedules up to BLIST positions of the chunk in parallel: the tiles of the
+// systems this pass serves, in order, with their entry ranges, into a list
+// in shared memory.  The list is then run like the single-system tile loop:
+// bulk copies into two stages, each warp waiting on the stage's mbarrier for
+// its own data, the last warp out of a stage refilling it from the list.
+// Warps only meet at system boundaries, where the CTA closes the system's
+// flush group.  Row arithmetic and dots are those of the generic steps.
+// ---------------------------------------------------------------------------
 template <int MODE, class Step>
 __global__ void __launch_bounds__(THREADS, 2) k_bstaged(Mat A, Vecs V, Batch B)
 {
@@ -481,131 +495,148 @@ __global__ void __launch_bounds__(THREADS, 2) k_bstaged(Mat A, Vecs V, Batch B)
     __shared__ Shm<ND> sh;
     __shared__ uint64_t bar[NSTAGE];
     __shared__ StageInfo info[NSTAGE];
-    __shared__ BTag tag[NSTAGE];
+    __shared__ BEntry list[BLIST];
+    __shared__ int cnts[THREADS];
+    __shared__ int done_cnt[NSTAGE], uses[NSTAGE], nlist, tmo;
     shm_init<ND, MODE>(sh);
-    TilePipe<NV, true> P{dsm, bar, info};
+    TilePipe<NV, true, false> P{dsm, bar, info};
     DotSet<ND, MODE> D;
     D.init();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // thread 0: cursor over this CTA's contiguous chunk [q0, q1) of the tile
-    // list (the live list of a pool, else all tiles)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const bool listed = B.lv_n != nullptr;
     const int nq = listed ? B.lv_n[1] : B.ntiles;
+    const int q0 = (int)(((long long)nq * blockIdx.x) / gridDim.x);
     const int q1 = (int)(((long long)nq * (blockIdx.x + 1)) / gridDim.x);
-    int q = (int)(((long long)nq * blockIdx.x) / gridDim.x), j = 0, ls = -1, lf = 0;
-    bool lw = false;
-    if (threadIdx.x == 0 && listed && q < q1) {
-        int lo = 0, hi = B.lv_n[0] - 1;                // last live system with lv_pre[j] <= q
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (B.lv_pre[mid] <= q)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        j = lo;
-    }
-    // next tile this pass serves (thread 0); -1 when none is left
-    auto next_tile = [&](BTag &tg) {
-        tg.tile = -1;
-        while (q < q1) {
-            int t = q, qend;
-            if (listed) {
-                while (B.lv_pre[j + 1] <= q)
-                    j++;
-                t = B.lv_t0[j] + (q - B.lv_pre[j]);
-            }
-            const int sys = B.tile_sys[t];
-            if (sys >= 0) {
-                if (sys != ls) {
-                    ls = sys;
-                    lw = Step::wants(B.ctl + sys);
-                    lf = Step::flags(B.ctl + sys);
-                }
-                if (lw) {
-                    tg.tile = t;
-                    tg.sys = sys;
-                    tg.first = lf;
-                    q++;
-                    return;
-                }
-                qend = listed ? B.lv_pre[j + 1] : B.sys_t1[sys];    // skip the rest of this system
-            } else {
-                qend = q + 1;
-            }
-            q = max(q + 1, min(q1, qend));
-        }
-    };
-    auto issue = [&](int k, const BTag &tg) {
+    auto issue = [&](int k, const BEntry &e) {        // one lane
         const double *src[NV];
         const double *gx;
-        Step::srcs(V, tg.first, src, gx);
-        const int s0 = tg.tile * TILE_SLICES;
+        Step::srcs(V, e.first, src, gx);
         int rec[TMETA];
-        rec[0] = A.sl_off[s0];
-        rec[1] = A.sl_w ? A.sl_off[s0 + TILE_SLICES - 1] + 32 * A.sl_w[s0 + TILE_SLICES - 1] : A.sl_off[s0 + TILE_SLICES];
+        rec[0] = e.e0;
+        rec[1] = e.e1;
 #pragma unroll
         for (int g = 2; g < TMETA; g++)
             rec[g] = -1;
-        P.issue(k, tg.tile, rec, A, src, NV, gx, -1);
+        uses[k] += 1;
+        P.issue(k, e.tile, rec, A, src, NV, gx, -1);
     };
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < NSTAGE; k++)
+    if (tid == 0) {
+        for (int k = 0; k < NSTAGE; k++) {
             mbar_init(&bar[k], 1);
+            uses[k] = 0;
+        }
+        tmo = 0;
         fence_mbar_init();
         fence_async_shared();
-        for (int k = 0; k < NSTAGE; k++) {
-            next_tile(tag[k]);
-            if (tag[k].tile >= 0)
-                issue(k, tag[k]);
-        }
     }
     __syncthreads();
     int cur = -1, t_first = -1, cnt = 0;
-    bool tmo = false;
     typename Step::Scal S;
-    int c = 0;
-    for (;; c++) {
-        const int k = c % NSTAGE;
-        const BTag tg = tag[k];
-        if (tg.tile < 0)
-            break;
-        const bool ok = mbar_wait_bounded(&bar[k], (uint32_t)(c / NSTAGE) & 1u);
-        if (__syncthreads_or(!ok)) {
-            tmo = true;
-            break;
-        }
-        if (tg.sys != cur) {
-            if (cur >= 0 && cnt > 0) {
-                b_flush<ND, MODE, Step>(D, sh, B, cur, t_first, cnt, V);
-                D.init();
+    for (int qa = q0; qa < q1 && !*(volatile int *)&tmo; qa += BLIST) {
+        const int qb = min(q1, qa + BLIST);
+        // schedule positions [qa, qb): thread tid takes a contiguous piece, then an ordered compaction
+        const int per = (qb - qa + THREADS - 1) / THREADS;
+        const int pa = min(qb, qa + tid * per), pb = min(qb, pa + per);
+        BEntry mine[2];
+        int nm = 0;
+        for (int q = pa; q < pb; q++) {
+            int t = q;
+            if (listed) {
+                int lo = 0, hi = B.lv_n[0] - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (B.lv_pre[mid] <= q)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                t = B.lv_t0[lo] + (q - B.lv_pre[lo]);
             }
-            cur = tg.sys;
-            t_first = tg.tile;
-            cnt = 0;
-            S = Step::load(B.ctl + cur);
+            const int sys = B.tile_sys[t];
+            if (sys < 0 || !Step::wants(B.ctl + sys))
+                continue;
+            BEntry &e = mine[nm++];
+            e.tile = t;
+            e.sys = sys;
+            e.first = Step::flags(B.ctl + sys);
+            const int s0 = t * TILE_SLICES;
+            e.e0 = A.sl_off[s0];
+            e.e1 = A.sl_w ? A.sl_off[s0 + TILE_SLICES - 1] + 32 * A.sl_w[s0 + TILE_SLICES - 1]
+                          : A.sl_off[s0 + TILE_SLICES];
         }
-        if (MODE == 0 && threadIdx.x < ND)
-            B.part[(size_t)tg.tile * MAXD + threadIdx.x] = 0.0;
-        Step::template row<MODE>(P, k, A, V, S, tg.tile, warp, lane, D, sh);
-        cnt++;
-        __syncthreads();                       // stage k consumed by every warp
-        if (threadIdx.x == 0) {
-            next_tile(tag[k]);
-            if (tag[k].tile >= 0)
-                issue(k, tag[k]);
+        cnts[tid] = nm;
+        __syncthreads();
+        if (tid == 0) {
+            int run = 0;
+            for (int u = 0; u < THREADS; u++) {
+                const int cu = cnts[u];
+                cnts[u] = run;
+                run += cu;
+            }
+            nlist = run;
+            for (int k = 0; k < NSTAGE; k++)
+                done_cnt[k] = 0;
         }
-    }
-    if (tmo) {
-        // give up: wait (bounded) for this CTA's copies still in flight, flag the systems
-        if (threadIdx.x == 0) {
-            for (int cc = c; cc < c + NSTAGE; cc++) {
-                const BTag tg = tag[cc % NSTAGE];
-                if (tg.tile >= 0) {
-                    mbar_wait_bounded(&bar[cc % NSTAGE], (uint32_t)(cc / NSTAGE) & 1u);
-                    atomicOr(&B.ctl[tg.sys].err, 1);
+        __syncthreads();
+        for (int m = 0; m < nm; m++)
+            list[cnts[tid] + m] = mine[m];
+        __syncthreads();
+        const int n = nlist;
+        int base[NSTAGE];
+#pragma unroll
+        for (int k = 0; k < NSTAGE; k++)
+            base[k] = uses[k];                             // stage uses before this round
+        __syncthreads();
+        if (tid == 0)
+            for (int k = 0; k < NSTAGE && k < n; k++)
+                issue(k, list[k]);
+        __syncthreads();
+        for (int j = 0; j < n; j++) {
+            const int k = j % NSTAGE;
+            const BEntry e = list[j];
+            if (e.sys != cur) {                            // every warp reaches this entry: CTA-uniform
+                if (cur >= 0 && cnt > 0) {
+                    b_flush<ND, MODE, Step>(D, sh, B, cur, t_first, cnt, V);
+                    D.init();
+                }
+                cur = e.sys;
+                t_first = e.tile;
+                cnt = 0;
+                S = Step::load(B.ctl + cur);
+            }
+            // after an expired wait every warp keeps walking the list (so the
+            // CTA-wide flush points stay matched) but skips waits, rows and refills
+            if (!*(volatile int *)&tmo) {
+                const bool ok = __all_sync(0xffffffffu,
+                                           mbar_wait_bounded(&bar[k], (uint32_t)(base[k] + j / NSTAGE) & 1u));
+                if (!ok && lane == 0)
+                    tmo = 1;
+            }
+            if (__any_sync(0xffffffffu, *(volatile int *)&tmo))
+                continue;
+            if (MODE == 0 && warp == 0 && lane < ND)
+                B.part[(size_t)e.tile * MAXD + lane] = 0.0;
+            Step::template row<MODE>(P, k, A, V, S, e.tile, warp, lane, D, sh);
+            cnt++;
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&done_cnt[k], 1) == WARPS - 1) {   // last warp out refills the stage
+                    __threadfence_block();
+                    done_cnt[k] = 0;
+                    if (j + NSTAGE < n)
+                        issue(k, list[j + NSTAGE]);
                 }
             }
+        }
+        __syncthreads();
+    }
+    if (tmo) {
+        // give up: wait (bounded) for copies still in flight, flag the systems
+        if (tid == 0) {
+            for (int k = 0; k < NSTAGE; k++)
+                if (uses[k] > 0)
+                    mbar_wait_bounded(&bar[k], (uint32_t)(uses[k] - 1) & 1u);
             if (cur >= 0)
                 atomicOr(&B.ctl[cur].err, 1);
         }

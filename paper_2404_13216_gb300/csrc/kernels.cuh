@@ -713,9 +713,9 @@ static __global__ void __launch_bounds__(THREADS) k_rr4(Mat A, Vecs V, const Ctl
 // ---------------------------------------------------------------------------
 // staged passes: tiles of 256 rows double-buffered in shared memory by TMA
 // ---------------------------------------------------------------------------
-template <int NV, bool MATS>
+template <int NV, bool MATS, bool WIN = MATS>
 struct TilePipe {
-    using L = StageLayout<NV, MATS>;
+    using L = StageLayout<NV, MATS, WIN>;
     uint8_t *smem;
     uint64_t *bar;
     StageInfo *info;
@@ -760,7 +760,7 @@ struct TilePipe {
         const int s0 = tile * TILE_SLICES;
         const int e0 = rec[0], span = rec[1] - rec[0];
         const bool staged = MATS && span > 0 && span <= MCAP;
-        const bool windowed = staged && gx != nullptr && A.lci != nullptr && rec[2] >= 0;
+        const bool windowed = WIN && staged && gx != nullptr && A.lci != nullptr && rec[2] >= 0;
         int nblk = 0;
         if (windowed) {
 #pragma unroll
@@ -812,7 +812,7 @@ struct TilePipe {
         const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
         const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
         double acc = 0.0;
-        if (info[k].windowed) {                         // gather from the staged blocks (16-bit local indices)
+        if (WIN && info[k].windowed) {                  // gather from the staged blocks (16-bit local indices)
             const double *xw = gwin(k);
             const uint16_t *lp = reinterpret_cast<const uint16_t *>(ci(k)) + (off - info[k].e0) + lane;
             for (int j0 = 0; j0 < width; j0 += UNR) {

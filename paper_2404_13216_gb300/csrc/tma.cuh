@@ -86,16 +86,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 // Dynamic shared memory of a staged pass with NV input vectors:
-// NSTAGE stages of { vec[NV][256] f64, gwin[GMAX][256] f64 (if staged), va[MCAP] f64 (if staged),
+// NSTAGE stages of { vec[NV][256] f64, gwin[GMAX][256] f64 (if staged with windows), va[MCAP] f64 (if staged),
 // ci[MCAP] i32 or 16-bit local indices (if staged), rlen[256] i32, sl_off[16] i32, meta[TMETA] i32 }.
 // meta holds the record of the tile this stage takes next, so the warp that
 // refills the stage needs no global load.
 // When a tile's columns fall in at most GMAX 256-row blocks, those blocks of
 // the gathered vector are staged in gwin and ci holds local indices into it.
-template <int NV, bool MATS>
+template <int NV, bool MATS, bool WIN = MATS>
 struct StageLayout {
     static constexpr uint32_t VEC = NV * TILE_ROWS * 8;
-    static constexpr uint32_t GWIN = MATS ? GMAX * TILE_ROWS * 8 : 0;
+    static constexpr uint32_t GWIN = (MATS && WIN) ? GMAX * TILE_ROWS * 8 : 0;
     static constexpr uint32_t VA = MATS ? MCAP * 8 : 0;
     static constexpr uint32_t CI = MATS ? MCAP * 4 : 0;
     static constexpr uint32_t RLEN = TILE_ROWS * 4;
