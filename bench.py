@@ -254,6 +254,7 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = run_batched_leg(ctx, pbcg, torch, dev)
+        batched["residual_replacement"] = run_batched_rr(ctx, pbcg, torch, dev)
     configs = None
     if not args.no_configs:
         configs = run_config_legs(ctx, pbcg, torch, dev, peaks()[0])
@@ -359,6 +360,35 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_batched_rr(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, period=50):
+    """The config-4 batch solved with residual replacement every `period` iterations."""
+    import numpy as np
+    from paper_2404_13216_gb300 import inputs
+    B = inputs.batched_convdiff(nsys=nsys, seed=4)
+    b = inputs.rhs_ones(B.A)
+    M = ctx.upload_csr(B.A)
+    b_d = torch.from_numpy(b).to(dev)
+    x_d = torch.zeros(B.A.n, dtype=torch.float64, device=dev)
+    tols = np.full(nsys, tol)
+    ctx.set_option(pbcg.OPT_RR_PERIOD, period)
+    ctx.solve_batched(M, B.sys_row_ptr, b_d, x_d, tols, maxit, pbcg.PIPELINED_RR, 1)
+    stream = torch.cuda.current_stream(dev)
+    x_d.zero_()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = ctx.solve_batched(M, B.sys_row_ptr, b_d, x_d, tols, maxit, pbcg.PIPELINED_RR, 1)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) * 1e-3
+    M.free()
+    its = np.array([r.iters for r in res])
+    return {"period": period, "solves_per_s": nsys / t, "seconds": t,
+            "converged": int(sum(r.status == 0 for r in res)),
+            "max_true_relres": float(max(r.relres_true for r in res)),
+            "iters_mean": float(its.mean()), "iters_max": int(its.max())}
 
 
 def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, mode=1):
