@@ -279,39 +279,6 @@ struct StepPipeX {
     };
     static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->beta, c->omega, c->it == 0, rr_now(c)}; }
-    static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
-                               double (&a)[ND], double (&b)[ND])
-    {
-        double q = 0.0, y = 0.0, r0i = 0.0, si = 0.0, zi = 0.0;
-        if (sl < A.nslices) {
-            double ti = 0.0;
-            if (!S.first) {
-                RowRef R = row_ref(A, sl, lane);
-                ti = spmv_row(A, R, V.w);
-            }
-            if (act) {
-                const double ri = V.r[i], wi = V.w[i];
-                r0i = V.r0[i];
-                if (S.first)
-                    ti = V.t[i];
-                else
-                    V.t[i] = ti;
-                const XRow X = S.first ? pipe_x_row(true, false, -S.alpha, S.beta, -S.omega, ri, wi, ti, 0.0, 0.0, 0.0, 0.0)
-                                       : pipe_x_row(false, S.rr, -S.alpha, S.beta, -S.omega, ri, wi, ti, V.p[i],
-                                                    V.s[i], V.z[i], V.v[i]);
-                si = X.s;
-                zi = X.z;
-                q = X.q;
-                y = X.y;
-                V.p[i] = X.p;
-                V.s[i] = X.s;
-                V.z[i] = X.z;
-                V.q[i] = q;
-                V.y[i] = y;
-            }
-        }
-        a[0] = q, b[0] = y, a[1] = y, b[1] = y, a[2] = r0i, b[2] = si, a[3] = r0i, b[3] = zi;
-    }
     static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
     {
         double qy = dv[0], yy = dv[1];
@@ -334,27 +301,6 @@ struct StepPipeY {
     };
     static __device__ bool wants(const Ctl *c) { const int st = c->status; return st == ST_RUNNING; }
     static __device__ Scal load(const Ctl *c) { return Scal{c->alpha, c->omega}; }
-    static __device__ void row(const Mat &A, const Vecs &V, const Scal &S, int sl, int lane, int i, bool act,
-                               double (&a)[ND], double (&b)[ND])
-    {
-        double rn = 0.0, wn = 0.0, r0i = 0.0;
-        if (sl < A.nslices) {
-            RowRef R = row_ref(A, sl, lane);
-            const double vi = spmv_row(A, R, V.z);
-            if (act) {
-                const YRow Yr = pipe_y_row(S.alpha, S.omega, -S.alpha, -S.omega, V.q[i], V.y[i], V.p[i], V.x[i],
-                                           V.t[i], vi);
-                V.x[i] = Yr.x;
-                rn = Yr.r;
-                wn = Yr.w;
-                r0i = V.r0[i];
-                V.v[i] = vi;
-                V.r[i] = rn;
-                V.w[i] = wn;
-            }
-        }
-        a[0] = r0i, b[0] = rn, a[1] = r0i, b[1] = wn, a[2] = rn, b[2] = rn;
-    }
     static __device__ void fin(Ctl *c, const double *dv, const Vecs &)
     {
         double rho_new = dv[0], rw = dv[1], rr = dv[2];

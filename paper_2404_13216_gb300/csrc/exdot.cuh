@@ -48,34 +48,6 @@ struct Prod {
     bool nonfinite;              // an operand is Inf or NaN
 };
 
-__device__ __forceinline__ Prod exact_product(double a, double b)
-{
-    Prod p;
-    unsigned long long ba = (unsigned long long)__double_as_longlong(a);
-    unsigned long long bb = (unsigned long long)__double_as_longlong(b);
-    uint32_t ahi = (uint32_t)(ba >> 32), alo = (uint32_t)ba;
-    uint32_t bhi = (uint32_t)(bb >> 32), blo = (uint32_t)bb;
-    uint32_t ea = (ahi >> 20) & 0x7ffu, eb = (bhi >> 20) & 0x7ffu;
-    p.nonfinite = (ea == 0x7ffu) | (eb == 0x7ffu);
-    p.neg = (ahi ^ bhi) >> 31;
-    uint32_t ma = (ahi & 0xfffffu) | (ea ? 0x100000u : 0u);   // high 21 mantissa bits
-    uint32_t mb = (bhi & 0xfffffu) | (eb ? 0x100000u : 0u);
-    bool zero = ((ma | alo) == 0u) | ((mb | blo) == 0u);
-    // (ma:alo) * (mb:blo), 53 x 53 -> 106 bits
-    unsigned long long p0 = (unsigned long long)alo * blo;
-    unsigned long long m = (unsigned long long)ma * blo + (p0 >> 32);
-    m = (unsigned long long)alo * mb + m;
-    unsigned long long h = (unsigned long long)ma * mb + (m >> 32);
-    p.w0 = (uint32_t)p0;
-    p.w1 = (uint32_t)m;
-    p.w2 = (uint32_t)h;
-    p.w3 = (uint32_t)(h >> 32);
-    // LSB exponent of a double: max(e,1) - 1075; offset above 2^-2148
-    int eea = ea ? (int)ea : 1, eeb = eb ? (int)eb : 1;
-    p.off = (zero | p.nonfinite) ? -1 : (eea + eeb - 2);
-    return p;
-}
-
 // signed product words shifted left by r (0..31): u0..u4, u4 carrying the sign
 struct Shifted {
     uint32_t u0, u1, u2, u3, u4, sgn;
@@ -129,21 +101,6 @@ __device__ __forceinline__ void cta_touch(CtaAcc<ND> &c, int d, int k0, int k1)
 {
     atomicMin(&c.kmin[d], k0);
     atomicMax(&c.kmax[d], k1);
-}
-
-// slow path: one lane adds one product straight into the CTA digits
-template <int ND>
-__device__ __noinline__ void cta_add_product(CtaAcc<ND> &c, int d, const Prod &p)
-{
-    int k = p.off >> 5;
-    Shifted s = signed_shift(p, (uint32_t)(p.off & 31));
-    unsigned long long *g = c.dig[d];
-    atomicAdd(&g[k + 0], (unsigned long long)s.u0);
-    atomicAdd(&g[k + 1], (unsigned long long)s.u1);
-    atomicAdd(&g[k + 2], (unsigned long long)s.u2);
-    atomicAdd(&g[k + 3], (unsigned long long)s.u3);
-    atomicAdd(&g[k + 4], (unsigned long long)(long long)(int)s.u4);
-    cta_touch(c, d, k, k + 4);
 }
 
 // ---------------------------------------------------------------------------
