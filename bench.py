@@ -535,13 +535,14 @@ def source_sha() -> str:
 
 
 def run_ncu_case(args):
-    """Small fixed run for profilers: the 128^3 system, host-driven launches (no
-    CUDA graph), a fixed number of iterations; prints the per-kernel event times."""
+    """Small fixed run for profilers: the 128^3 system (or the power-law matrix),
+    host-driven launches (no CUDA graph), a fixed number of iterations; prints
+    the per-kernel event times."""
     import numpy as np
     from paper_2404_13216_gb300 import build, inputs
     build.build_library()
     from paper_2404_13216_gb300 import pbcg
-    A = inputs.convdiff3d(args.ncu_side, PECLET, WIND)
+    A = inputs.powerlaw() if args.ncu_matrix == "powerlaw" else inputs.convdiff3d(args.ncu_side, PECLET, WIND)
     b = inputs.rhs_ones(A)
     mode = pbcg.EXACT if args.ncu_case == "exact" else pbcg.PLAIN
     with pbcg.Context(0) as ctx:
@@ -560,6 +561,7 @@ def main():
     ap.add_argument("--ncu-side", type=int, default=N_SIDE)
     ap.add_argument("--ncu-iters", type=int, default=12)
     ap.add_argument("--ncu-alg", type=int, default=1, help="0 BiCGStab, 1 p-BiCGStab, 2 p-BiCGStabRR")
+    ap.add_argument("--ncu-matrix", choices=["convdiff", "powerlaw"], default="convdiff")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

@@ -34,6 +34,10 @@ namespace pbcg {
 #ifndef PBCG_MINB_EXACT
 #define PBCG_MINB_EXACT 2               // same, exact passes
 #endif
+#ifndef PBCG_MINB_WIDE
+#define PBCG_MINB_WIDE 2                // same, passes over matrices whose tiles are too wide to stage
+#endif
+#define PBCG_MINB(MODE, MATS) ((MATS) ? ((MODE) ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN) : PBCG_MINB_WIDE)
 #ifndef PBCG_INTERLEAVE
 #define PBCG_INTERLEAVE 1               // 1: warp w takes slices w, w + W, ...; 0: one contiguous run per warp
 #endif
@@ -1030,7 +1034,7 @@ __device__ __forceinline__ YRow pipe_y_row(double alpha, double omega, double na
 
 // X(i) staged: t_i = A w_i (i >= 1), p, s, z, q, y; dots (q,y), (y,y), (r0,s), (r0,z); omega_i
 template <int MODE, bool MATS>
-__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+__global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_pipe_x_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
@@ -1109,7 +1113,7 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
 
 // Y(i) staged: v_i = A z_i, x_{i+1}, r_{i+1}, w_{i+1}; dots (r0,r), (r0,w), (r,r); beta, alpha, stop test
 template <int MODE, bool MATS>
-__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+__global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_pipe_y_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
@@ -1240,7 +1244,7 @@ static __global__ void __launch_bounds__(THREADS) k_bicg_p_tma(Mat A, Vecs V, Ct
 
 // A(i): s = A p; dot (r0, s); alpha_i
 template <int MODE, bool MATS>
-__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+__global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_bicg_a_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)
@@ -1275,7 +1279,7 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
 // B(i): y = A q with q_j = fma(-alpha, s_j, r_j) formed for each gathered
 // entry (alpha is known only after pass A); dots (q,y), (y,y); omega_i
 template <int MODE, bool MATS>
-__global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
+__global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_bicg_b_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     if (c->status != ST_RUNNING)

@@ -230,3 +230,31 @@ def test_pool_invalid_arguments(ctx):
     with pytest.raises(pbcg.PbcgError):
         pool.step(0)
     pool.close()
+
+
+def test_pool_and_batch_irregular_rows(ctx, orc):
+    """Random power-law rows (some wider than a tile can stage) in a pool and in
+    a batched solve: each system equals the oracle bit for bit (exact)."""
+    from paper_2404_13216_gb300 import pbcg
+    syst = [inputs.powerlaw(n=n, mean_len=12.0, max_len=300, seed=s) for n, s in ((700, 1), (1500, 2), (300, 3))]
+    syst.append(inputs.convdiff3d(9, 40.0))
+    refs = [orc.solve(A.row_ptr, A.col_idx, A.vals, inputs.rhs_ones(A), tol=1e-10, maxit=400, alg=1, mode=1)
+            for A in syst]
+    pool = pbcg.Pool(ctx, max_rows=16 * 256, max_entries=1 << 20, max_slots=4, maxit=400)
+    live, got = {}, {}
+    for k, A in enumerate(syst):
+        live[pool.admit(A, inputs.rhs_ones(A), tol=1e-10, maxit=400)] = k
+    drain(pool, live, got, 5)
+    pool.close()
+    for k, ref in enumerate(refs):
+        x, r, _ = got[k]
+        assert r.status == ref.status and r.iters == ref.iters and same(x, ref.x), k
+    A, srp = inputs.block_diag(syst)
+    b = inputs.rhs_ones(A)
+    M = ctx.upload_csr(A)
+    x = np.zeros(A.n)
+    res = ctx.solve_batched(M, srp, b, x, np.full(len(syst), 1e-10), 400, 1, 1)
+    M.free()
+    for k, ref in enumerate(refs):
+        assert res[k].status == ref.status and res[k].iters == ref.iters, k
+        assert same(x[srp[k]:srp[k + 1]], ref.x), k
