@@ -495,6 +495,11 @@ def run_config_legs(ctx, pbcg, torch, dev, peak):
     A = inputs.powerlaw()
     for mode, mn in ((pbcg.EXACT, "exact"), (pbcg.PLAIN, "plain")):
         out[f"powerlaw_pbicgstab_{mn}"] = leg(A, pbcg.PIPELINED, mode, 1e-300, 100, 1, 23)
+    # to tolerance, unpreconditioned and with right Jacobi preconditioning
+    out["powerlaw_pbicgstab_exact_to_tol"] = leg(A, pbcg.PIPELINED, pbcg.EXACT, TOL, 400, 1, 23)
+    ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_JACOBI)
+    out["powerlaw_pbicgstab_jacobi_exact_to_tol"] = leg(A, pbcg.PIPELINED, pbcg.EXACT, TOL, 400, 1, 23)
+    ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_NONE)
     out["notes"] = ("us_per_iter = solve time / iterations (setup and the true-residual check included); "
                     "bytes_per_iter = 2M + 23V (p-BiCGStab) or 2M + 17V (BiCGStab); the 64^2 system is "
                     "L2-resident, so its GB/s is not an HBM figure; tol 1e-300 runs exactly maxit iterations")

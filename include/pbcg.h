@@ -258,9 +258,20 @@ int pbcg_pool_room(const pbcg_pool *pool, int32_t *free_slots, int64_t *free_row
  *     of every iteration i > 0 with i mod k == 0: r = b - A x, w = A r, p by
  *     its recurrence from the new r, s = A p, z = A s (t = A w follows in the
  *     same iteration); the scalars are kept.
+ *   PBCG_OPT_PRECOND: PBCG_PRECOND_NONE (default) or PBCG_PRECOND_JACOBI.
+ *     Section 2 notes that real implementations add a preconditioner M (its
+ *     experiments use none).  With PBCG_PRECOND_JACOBI, pbcg_solve runs
+ *     Algorithm 1 or 2 on the right-preconditioned system A M^{-1} y = b with
+ *     M = diag(A), then returns x = M^{-1} y; a diagonal M is applied as
+ *     scaled matrix entries, so no iteration does extra work.  Fixed forms:
+ *     d_i = sum, in stored order, of row i's entries in column i (zero,
+ *     non-finite or absent: INVALID); entries v / d_col (one IEEE division);
+ *     y0 = x0 * d; x = y / d.  Residual histories and relres_* are those of
+ *     the scaled system.  pbcg_solve_batched rejects the option (INVALID).
  * Returns 0, or INVALID for an unknown option or value.
  */
-enum { PBCG_OPT_RR_PERIOD = 1 };
+enum { PBCG_OPT_RR_PERIOD = 1, PBCG_OPT_PRECOND = 3 };
+enum { PBCG_PRECOND_NONE = 0, PBCG_PRECOND_JACOBI = 1 };
 int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value);
 
 /*

@@ -66,6 +66,9 @@ def _load():
     lib.orc_solve.restype = ctypes.c_int
     lib.orc_solve.argtypes = [i32, P, P, P, P, P, d, i32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                               P, i32, P, P, i32, P, P, P]
+    lib.orc_solve_jacobi.restype = ctypes.c_int
+    lib.orc_solve_jacobi.argtypes = [i32, P, P, P, P, P, d, i32, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32,
+                                     P, i32, P, P, i32, P, P, P]
     lib.orc_solve_rr.restype = ctypes.c_int
     lib.orc_solve_rr.argtypes = [i32, P, P, P, P, P, d, i32, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32,
                                  P, i32, P, P, i32, P, P, P]
@@ -139,9 +142,10 @@ class Result:
 
 
 def solve(row_ptr, col_idx, vals, b, x0=None, tol=1e-8, maxit=1000, alg=PIPELINED, mode=EXACT,
-          nthreads: int = 1, trace: bool = False, rr_period: int = 0) -> Result:
+          nthreads: int = 1, trace: bool = False, rr_period: int = 0, jacobi: bool = False) -> Result:
     """Run Algorithm 1 (alg=BICGSTAB) or Algorithm 2 (alg=PIPELINED) from x0;
-    rr_period > 0 adds residual replacement every rr_period iterations (Algorithm 2)."""
+    rr_period > 0 adds residual replacement every rr_period iterations (Algorithm 2);
+    jacobi=True solves with right Jacobi preconditioning (orc_solve_jacobi)."""
     rp, ci, v, b = _i32(row_ptr), _i32(col_idx), _f64(vals), _f64(b)
     n = rp.size - 1
     x = np.zeros(n) if x0 is None else _f64(x0).copy()
@@ -150,7 +154,8 @@ def solve(row_ptr, col_idx, vals, b, x0=None, tol=1e-8, maxit=1000, alg=PIPELINE
     tr = np.full((max(int(maxit), 1), 4), np.nan) if trace else None
     hl, it = ctypes.c_int32(0), ctypes.c_int32(0)
     rr, rt = ctypes.c_double(0), ctypes.c_double(0)
-    st = _load().orc_solve_rr(n, _p(rp), _p(ci), _p(v), _p(b), _p(x), float(tol), int(maxit), int(alg),
+    fn = _load().orc_solve_jacobi if jacobi else _load().orc_solve_rr
+    st = fn(n, _p(rp), _p(ci), _p(v), _p(b), _p(x), float(tol), int(maxit), int(alg),
                            int(mode), int(nthreads), int(rr_period), _p(hist), cap, ctypes.byref(hl),
                            _p(tr) if trace else None, tr.shape[0] if trace else 0,
                            ctypes.byref(it), ctypes.byref(rr), ctypes.byref(rt))

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -33,6 +34,7 @@ struct LoopGraph {
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle handle = 0;
     int alg = -1, mode = -1, n = -1;
+    bool jac = false;                  // built on the Jacobi-scaled entries
     const void *mat = nullptr;
 };
 
@@ -63,6 +65,8 @@ struct pbcg_mat {
     uint16_t *lci;         // [padded] local column indices into a tile's staged gather blocks
     int *tmeta;            // [ntiles * TMETA] per tile: first and end entry, gather blocks (-1: none / too many)
     bool narrow;           // every 256-row tile spans at most MCAP SELL entries (staged in shared memory)
+    double *diag = nullptr;    // [n] solver-order diagonal for Jacobi preconditioning (built on first use)
+    double *va_jac = nullptr;  // [padded] entries of A M^-1, M = diag(A)
     std::vector<int32_t> h_rp, h_ci;   // host copy of the CSR (for per-batch layouts)
     std::vector<double> h_va;
     struct BatchLayout *bl;            // tile-aligned layout of the last batched solve, or NULL
@@ -92,6 +96,7 @@ struct pbcg_ctx {
     Ctl *h_ctl = nullptr;              // pinned mirror of the control block
     std::map<const void *, int> occ;   // resident CTAs per SM of each kernel
     int rr_period = 50;                // residual replacement period of PBCG_ALG_PIPELINED_RR
+    int precond = PBCG_PRECOND_NONE;   // preconditioner of pbcg_solve
     // batched solves
     struct {
         long long n_cap = 0;
@@ -177,6 +182,8 @@ void mat_release(pbcg_mat *m)
     cudaFree(m->perm);
     cudaFree(m->lci);
     cudaFree(m->tmeta);
+    cudaFree(m->diag);
+    cudaFree(m->va_jac);
     delete m;
 }
 
@@ -516,10 +523,10 @@ int launch_kernel(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, in
 }
 
 // build (or reuse) the WHILE-node loop graph for this matrix / algorithm / mode
-int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, LoopGraph **out)
+int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, LoopGraph **out)
 {
     LoopGraph &L = ctx->ws.loop;
-    if (L.exec && L.mat == m && L.alg == alg && L.mode == mode && L.n == m->n) {
+    if (L.exec && L.mat == m && L.alg == alg && L.mode == mode && L.n == m->n && L.jac == jac) {
         *out = &L;
         return 0;
     }
@@ -536,6 +543,8 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, LoopGraph **ou
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     // kernel parameter values are copied into the nodes when they are added
     Mat A = mat_of(m);
+    if (jac)
+        A.va = m->va_jac;
     Vecs V = vecs_of(ctx->ws);
     Ctl *c = ctx->ws.ctl;
     Work *wk = ctx->ws.wk;
@@ -557,6 +566,7 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, LoopGraph **ou
     CK(cudaGraphInstantiate(&L.exec, L.graph, 0));
     L.alg = alg;
     L.mode = mode;
+    L.jac = jac;
     L.mat = m;
     L.n = m->n;
     *out = &L;
@@ -632,6 +642,60 @@ struct Launcher {
 };
 
 // caller-order vector (host or device) -> solver-order device vector
+// Jacobi preconditioning data of a matrix: d_i = sum, in stored order, of row
+// i's entries in column i (zero, non-finite or absent: INVALID), in solver
+// order, and the entries of A M^-1 (v / d_col, one IEEE division each)
+int ensure_jacobi(pbcg_ctx *ctx, pbcg_mat *m)
+{
+    if (m->va_jac)
+        return 0;
+    const int n = m->n;
+    std::vector<double> d((size_t)n, 0.0);
+    for (int i = 0; i < n; i++) {
+        bool found = false;
+        double s = 0.0;
+        for (int k = m->h_rp[i]; k < m->h_rp[i + 1]; k++)
+            if (m->h_ci[k] == i) {
+                s = found ? s + m->h_va[k] : m->h_va[k];
+                found = true;
+            }
+        if (!found || s == 0.0 || !std::isfinite(s))
+            return fail(ctx, PBCG_ERR_INVALID, "Jacobi preconditioning needs a finite nonzero diagonal (row %d)", i);
+        d[(size_t)i] = s;
+    }
+    std::vector<int> perm;
+    if (m->perm) {
+        perm.resize((size_t)n);
+        CK(cudaMemcpy(perm.data(), m->perm, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost));
+    }
+    std::vector<double> ds((size_t)n);
+    for (int p = 0; p < n; p++)
+        ds[(size_t)p] = d[(size_t)(m->perm ? perm[(size_t)p] : p)];
+    const size_t P = (size_t)(m->padded ? m->padded : 1);
+    CK(cudaMalloc(&m->diag, sizeof(double) * (size_t)n));
+    CK(cudaMalloc(&m->va_jac, sizeof(double) * P));
+    CK(cudaMemcpy(m->diag, ds.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+    long long ne = m->padded;
+    const int *ci = m->ci;
+    const double *va = m->va, *dd = m->diag;
+    double *vs = m->va_jac;
+    void *args[5] = {&ne, (void *)&ci, (void *)&va, (void *)&dd, &vs};
+    CK(cudaLaunchKernel((void *)k_jacobi_scale, dim3(ctx->num_sms * 8), dim3(256), args, 0, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return 0;
+}
+
+// y = x * d or x = y / d on a solver-order device vector
+int jacobi_vec(pbcg_ctx *ctx, const pbcg_mat *m, double *x, bool to_scaled)
+{
+    int n = m->n;
+    const double *dd = m->diag;
+    void *args[3] = {&n, (void *)&dd, &x};
+    CK(cudaLaunchKernel(to_scaled ? (void *)k_vmul : (void *)k_vdiv, dim3(ctx->num_sms * 4), dim3(256), args, 0,
+                        ctx->stream));
+    return 0;
+}
+
 int vec_in(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst)
 {
     size_t bytes = sizeof(double) * (size_t)m->n;
@@ -689,7 +753,12 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     if (rc)
         return rc;
     Workspace &ws = ctx->ws;
+    const bool jac = ctx->precond == PBCG_PRECOND_JACOBI;
+    if (jac && (rc = ensure_jacobi(ctx, const_cast<pbcg_mat *>(m))))
+        return rc;
     if ((rc = vec_in(ctx, m, b, ws.vec[V_B])) || (rc = vec_in(ctx, m, x, ws.vec[V_X])))
+        return rc;
+    if (jac && (rc = jacobi_vec(ctx, m, ws.vec[V_X], true)))     // y0 = d x0
         return rc;
     Ctl h;
     memset(&h, 0, sizeof h);
@@ -708,6 +777,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     CK(cudaMemcpyAsync(ws.ctl, ctx->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
 
     Mat A = mat_of(m);
+    if (jac)
+        A.va = m->va_jac;                                         // A M^-1
     Vecs V = vecs_of(ws);
     Launcher L{ctx, prof, 0, {}};
     if (alg != PBCG_ALG_BICGSTAB) {
@@ -749,7 +820,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
                     return rc;
         } else {
             LoopGraph *G = nullptr;
-            if ((rc = get_loop(ctx, m, alg, mode, &G)))
+            if ((rc = get_loop(ctx, m, alg, mode, jac, &G)))
                 return rc;
             if (!cond_on) {
                 int one = 1;
@@ -788,6 +859,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     Ctl fin_ctl = *ctx->h_ctl;
     if (fin_ctl.err || fin_ctl.status == ST_TIMEOUT)
         return fail(ctx, PBCG_ERR_TIMEOUT, "a bounded device wait expired (bulk copy did not complete)");
+    if (jac && (rc = jacobi_vec(ctx, m, ws.vec[V_X], false)))    // x = y / d
+        return rc;
     if ((rc = vec_out(ctx, m, ws.vec[V_X], x)))
         return rc;
     int hl = fin_ctl.it + 1;
@@ -814,10 +887,14 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
 // ---------------------------------------------------------------------------
 // batched solves
 // ---------------------------------------------------------------------------
+void free_batch_graph(pbcg_ctx *ctx);
+
 int build_layout(pbcg_ctx *ctx, pbcg_mat *m, const std::vector<int32_t> &srp)
 {
     if (m->bl && m->bl->key == srp)
         return 0;
+    if (m->bl && ctx->b.g_layout == (const void *)m->bl)
+        free_batch_graph(ctx);             // its nodes point into the layout being replaced
     layout_release(m->bl);
     m->bl = nullptr;
     const int nsys = (int)srp.size() - 1;
@@ -1075,6 +1152,8 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
     if (nsys < 1 || !sys_row_ptr || !b || !x || !tol || !out)
         return fail(ctx, PBCG_ERR_INVALID, "bad batched arguments");
+    if (ctx->precond != PBCG_PRECOND_NONE)
+        return fail(ctx, PBCG_ERR_INVALID, "preconditioning applies to pbcg_solve only");
     if (maxit < 0)
         return fail(ctx, PBCG_ERR_INVALID, "maxit must be >= 0");
     if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED && alg != PBCG_ALG_PIPELINED_RR)
@@ -1684,6 +1763,8 @@ int pbcg_mat_free(pbcg_ctx *ctx, pbcg_mat *m)
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ws.loop.mat == m)
         free_loop(ctx->ws.loop);
+    if (m->bl && ctx->b.g_layout == (const void *)m->bl)
+        free_batch_graph(ctx);             // its nodes point into this matrix's layout
     ctx->mats.erase(m);
     mat_release(m);
     return 0;
@@ -1727,6 +1808,12 @@ int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value)
         if (value < 1 || value > INT32_MAX)
             return fail(ctx, PBCG_ERR_INVALID, "residual replacement period must be >= 1");
         ctx->rr_period = (int)value;
+        return 0;
+    }
+    if (option == PBCG_OPT_PRECOND) {
+        if (value != PBCG_PRECOND_NONE && value != PBCG_PRECOND_JACOBI)
+            return fail(ctx, PBCG_ERR_INVALID, "unknown preconditioner %lld", (long long)value);
+        ctx->precond = (int)value;
         return 0;
     }
     return fail(ctx, PBCG_ERR_INVALID, "unknown option %d", option);

@@ -592,6 +592,29 @@ static __global__ void __launch_bounds__(THREADS) k_true_res(Mat A, Vecs V, Ctl 
 }
 
 // ---------------------------------------------------------------------------
+// right Jacobi preconditioning: A M^-1 with M = diag(A) as scaled entries,
+// y0 = d x0 before the solve and x = y / d after it (one rounding each)
+// ---------------------------------------------------------------------------
+static __global__ void k_jacobi_scale(long long ne, const int *__restrict__ ci, const double *__restrict__ va,
+                                      const double *__restrict__ d, double *vs)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
+        vs[e] = __ddiv_rn(va[e], d[ci[e]]);
+}
+
+static __global__ void k_vmul(int n, const double *__restrict__ d, double *x)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] = __dmul_rn(x[i], d[i]);
+}
+
+static __global__ void k_vdiv(int n, const double *__restrict__ d, double *x)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] = __ddiv_rn(x[i], d[i]);
+}
+
+// ---------------------------------------------------------------------------
 // standalone kernels: dot, SpMV, permutation gather/scatter
 // ---------------------------------------------------------------------------
 template <int MODE>

@@ -325,3 +325,67 @@ def test_residual_replacement_vs_oracle(ctx, orc, mode, k):
         assert same(hist, ref.history) and same(x, ref.x)
     else:
         assert res.status == 0 and res.relres_true <= tol
+
+
+@pytest.mark.parametrize("alg", [0, 1, 2], ids=["bicgstab", "pbicgstab", "pbicgstab_rr"])
+@pytest.mark.parametrize("sysname", ["2d_scaled", "powerlaw"])
+def test_jacobi_exact_bitwise(ctx, orc, sysname, alg):
+    """Right Jacobi preconditioning: the exact solve equals the oracle's bit for
+    bit (a convection-diffusion matrix with a varied diagonal, and power-law
+    rows, which the library reorders by length)."""
+    from paper_2404_13216_gb300 import pbcg
+    if sysname == "2d_scaled":
+        A = inputs.convdiff2d(30, 25.0)
+        rng = np.random.default_rng(3)
+        v = A.vals.copy()
+        for i in range(A.n):
+            for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                if A.col_idx[k] == i:
+                    v[k] *= 10.0 ** rng.uniform(-2, 2)
+        A = inputs.CSR(A.n, A.row_ptr, A.col_idx, v)
+    else:
+        A = inputs.powerlaw(n=20000, mean_len=20, max_len=400, seed=8)
+    b = inputs.rhs_ones(A)
+    x0 = np.full(A.n, 0.25)
+    rr = 9 if alg == 2 else 0
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, x0=x0, tol=1e-10, maxit=600, alg=min(alg, 1), mode=1,
+                    nthreads=8, rr_period=rr, jacobi=True)
+    ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_JACOBI)
+    if alg == 2:
+        ctx.set_option(pbcg.OPT_RR_PERIOD, rr)
+    try:
+        M = ctx.upload_csr(A)
+        x = x0.copy()
+        res = ctx.solve(M, b, x, 1e-10, 600, alg, 1)
+        hist = ctx.history()
+        M.free()
+    finally:
+        ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_NONE)
+        ctx.set_option(pbcg.OPT_RR_PERIOD, 50)
+    assert res.status == ref.status and res.iters == ref.iters, (res, ref.status, ref.iters)
+    assert same(hist, ref.history) and same(x, ref.x)
+    assert same([res.relres_true], [ref.relres_true])
+
+
+def test_jacobi_rejections(ctx):
+    from paper_2404_13216_gb300 import pbcg
+    A = inputs.convdiff2d(6, 2.0)
+    v = A.vals.copy()
+    v[A.row_ptr[4]:A.row_ptr[5]][A.col_idx[A.row_ptr[4]:A.row_ptr[5]] == 4] = 0.0
+    Z = inputs.CSR(A.n, A.row_ptr, A.col_idx, v)
+    ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_JACOBI)
+    try:
+        M = ctx.upload_csr(Z)
+        with pytest.raises(pbcg.PbcgError):
+            ctx.solve(M, inputs.rhs_ones(A), np.zeros(A.n), 1e-8, 10, 1, 1)     # zero diagonal
+        M.free()
+        systems = [inputs.convdiff2d(6, 2.0), inputs.convdiff2d(5, 2.0)]
+        Bm, srp = inputs.block_diag(systems)
+        M = ctx.upload_csr(Bm)
+        with pytest.raises(pbcg.PbcgError):
+            ctx.solve_batched(M, srp, inputs.rhs_ones(Bm), np.zeros(Bm.n), np.full(2, 1e-8), 10)
+        M.free()
+    finally:
+        ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_NONE)
+    with pytest.raises(pbcg.PbcgError):
+        ctx.set_option(pbcg.OPT_PRECOND, 7)

@@ -247,3 +247,80 @@ def test_rr_period_zero_is_algorithm_2(orc):
     r0 = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=300, alg=1, mode=1)
     r1 = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=300, alg=1, mode=1, rr_period=0)
     assert np.array_equal(r0.history, r1.history) and np.array_equal(r0.x, r1.x)
+
+
+# ---------------------------------------------------------------------------
+# right Jacobi preconditioning (orc_solve_jacobi)
+# ---------------------------------------------------------------------------
+def _scaled_columns(A, d):
+    """A with column j multiplied by 1/d_j, computed exactly for powers of two."""
+    v = A.vals.astype(np.float64).copy()
+    for i in range(A.n):
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            v[k] = math.ldexp(v[k], -int(math.log2(abs(d[A.col_idx[k]]))))
+            if d[A.col_idx[k]] < 0:
+                v[k] = -v[k]
+    return v
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_jacobi_with_unit_diagonal_is_the_plain_solve(orc, alg):
+    A = inputs.convdiff2d(10, 20.0)
+    diag = np.zeros(A.n)
+    for i in range(A.n):
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            if A.col_idx[k] == i:
+                diag[i] = A.vals[k]
+    # divide every row by its diagonal entry (exact for this test's purpose: a new matrix with unit diagonal)
+    v = A.vals / np.repeat(diag, np.diff(A.row_ptr))
+    U = inputs.CSR(A.n, A.row_ptr, A.col_idx, v)
+    b = inputs.rhs_ones(U)
+    x0 = np.linspace(-1.0, 1.0, A.n)
+    ref = orc.solve(U.row_ptr, U.col_idx, U.vals, b, x0=x0, tol=1e-10, maxit=300, alg=alg, mode=1)
+    got = orc.solve(U.row_ptr, U.col_idx, U.vals, b, x0=x0, tol=1e-10, maxit=300, alg=alg, mode=1, jacobi=True)
+    assert got.status == ref.status and got.iters == ref.iters
+    assert np.array_equal(got.x.view(np.int64), ref.x.view(np.int64))
+    assert np.array_equal(got.history.view(np.int64), ref.history.view(np.int64))
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_jacobi_is_the_solve_of_the_column_scaled_system(orc, alg):
+    """Diagonal entries +-2^k: A M^-1 and the unscaling are exact, so the
+    preconditioned solve must equal, bit for bit, the plain solve of the
+    column-scaled matrix from y0 = d x0, followed by x = y / d."""
+    rng = np.random.default_rng(4)
+    A = inputs.convdiff2d(9, 15.0)
+    n = A.n
+    d = np.ldexp(1.0, rng.integers(-6, 7, n)) * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    v = A.vals.copy()
+    for i in range(n):                       # put d on the diagonal, keep the off-diagonals
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            if A.col_idx[k] == i:
+                v[k] = d[i]
+    B = inputs.CSR(n, A.row_ptr, A.col_idx, v)
+    b = rng.standard_normal(n)
+    x0 = rng.standard_normal(n)
+    got = orc.solve(B.row_ptr, B.col_idx, B.vals, b, x0=x0, tol=1e-9, maxit=400, alg=alg, mode=1, jacobi=True)
+    vs = _scaled_columns(B, d)
+    ref = orc.solve(B.row_ptr, B.col_idx, vs, b, x0=x0 * d, tol=1e-9, maxit=400, alg=alg, mode=1)
+    assert got.status == ref.status and got.iters == ref.iters
+    assert np.array_equal(got.history.view(np.int64), ref.history.view(np.int64))
+    assert np.array_equal(got.x.view(np.int64), (ref.x / d).view(np.int64))
+
+
+def test_jacobi_helps_a_badly_scaled_matrix(orc):
+    A = inputs.powerlaw(n=600, mean_len=8.0, max_len=60, seed=9)
+    b = inputs.rhs_ones(A)
+    plain = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=600, alg=1, mode=1)
+    jac = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=600, alg=1, mode=1, jacobi=True)
+    assert jac.status == 0 and jac.iters < plain.iters
+    r = b - orc.spmv(A.row_ptr, A.col_idx, A.vals, jac.x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
+
+
+def test_jacobi_rejects_a_missing_or_zero_diagonal(orc):
+    A = inputs.convdiff2d(5, 1.0)
+    v = A.vals.copy()
+    v[A.row_ptr[3]:A.row_ptr[4]][A.col_idx[A.row_ptr[3]:A.row_ptr[4]] == 3] = 0.0
+    with pytest.raises(ValueError):
+        orc.solve(A.row_ptr, A.col_idx, v, inputs.rhs_ones(A), tol=1e-8, maxit=10, jacobi=True)
