@@ -267,7 +267,8 @@ int pbcg_pool_room(const pbcg_pool *pool, int32_t *free_slots, int64_t *free_row
  *     d_i = sum, in stored order, of row i's entries in column i (zero,
  *     non-finite or absent: INVALID); entries v / d_col (one IEEE division);
  *     y0 = x0 * d; x = y / d.  Residual histories and relres_* are those of
- *     the scaled system.  pbcg_solve_batched rejects the option (INVALID).
+ *     the scaled system.  pbcg_solve_batched applies it to every system (a
+ *     block-diagonal M); pools do not (their systems run unpreconditioned).
  * Returns 0, or INVALID for an unknown option or value.
  */
 enum { PBCG_OPT_RR_PERIOD = 1, PBCG_OPT_PRECOND = 3 };

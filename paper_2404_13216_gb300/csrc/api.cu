@@ -80,6 +80,8 @@ struct BatchLayout {
     double *va = nullptr;
     int *map = nullptr;                // [n_int] caller row of each internal row, -1 for padding
     int *tile_sys = nullptr, *sys_t0 = nullptr;
+    bool jac = false;                  // entries of A M^-1 (Jacobi)
+    double *diag = nullptr;            // [n_int] internal-order diagonal when jac (1 on padding rows)
 };
 
 struct pbcg_ctx {
@@ -645,12 +647,10 @@ struct Launcher {
 // Jacobi preconditioning data of a matrix: d_i = sum, in stored order, of row
 // i's entries in column i (zero, non-finite or absent: INVALID), in solver
 // order, and the entries of A M^-1 (v / d_col, one IEEE division each)
-int ensure_jacobi(pbcg_ctx *ctx, pbcg_mat *m)
+int host_diagonal(pbcg_ctx *ctx, const pbcg_mat *m, std::vector<double> &d)
 {
-    if (m->va_jac)
-        return 0;
     const int n = m->n;
-    std::vector<double> d((size_t)n, 0.0);
+    d.assign((size_t)n, 0.0);
     for (int i = 0; i < n; i++) {
         bool found = false;
         double s = 0.0;
@@ -663,6 +663,17 @@ int ensure_jacobi(pbcg_ctx *ctx, pbcg_mat *m)
             return fail(ctx, PBCG_ERR_INVALID, "Jacobi preconditioning needs a finite nonzero diagonal (row %d)", i);
         d[(size_t)i] = s;
     }
+    return 0;
+}
+
+int ensure_jacobi(pbcg_ctx *ctx, pbcg_mat *m)
+{
+    if (m->va_jac)
+        return 0;
+    const int n = m->n;
+    std::vector<double> d;
+    if (int rc = host_diagonal(ctx, m, d))
+        return rc;
     std::vector<int> perm;
     if (m->perm) {
         perm.resize((size_t)n);
@@ -889,9 +900,9 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
 // ---------------------------------------------------------------------------
 void free_batch_graph(pbcg_ctx *ctx);
 
-int build_layout(pbcg_ctx *ctx, pbcg_mat *m, const std::vector<int32_t> &srp)
+int build_layout(pbcg_ctx *ctx, pbcg_mat *m, const std::vector<int32_t> &srp, const std::vector<double> *dj)
 {
-    if (m->bl && m->bl->key == srp)
+    if (m->bl && m->bl->key == srp && m->bl->jac == (dj != nullptr))
         return 0;
     if (m->bl && ctx->b.g_layout == (const void *)m->bl)
         free_batch_graph(ctx);             // its nodes point into the layout being replaced
@@ -945,12 +956,14 @@ int build_layout(pbcg_ctx *ctx, pbcg_mat *m, const std::vector<int32_t> &srp)
             int j0 = m->h_rp[i];
             for (int e = 0; e < len[p]; e++) {
                 ci[(size_t)(base + 32ll * e)] = ib[k] + (m->h_ci[j0 + e] - srp[k]);
-                va[(size_t)(base + 32ll * e)] = m->h_va[j0 + e];
+                va[(size_t)(base + 32ll * e)] =
+                    dj ? m->h_va[j0 + e] / (*dj)[(size_t)m->h_ci[j0 + e]] : m->h_va[j0 + e];   // A M^-1
             }
         }
     }
     BatchLayout *L = new BatchLayout();
     L->key = srp;
+    L->jac = dj != nullptr;
     L->nsys = nsys;
     L->n_int = n_int;
     L->nslices = ns;
@@ -969,6 +982,15 @@ int build_layout(pbcg_ctx *ctx, pbcg_mat *m, const std::vector<int32_t> &srp)
     if (e == cudaSuccess) e = cudaMemcpy(L->map, map.data(), sizeof(int) * (size_t)n_int, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L->tile_sys, tile_sys.data(), sizeof(int) * (size_t)ntiles, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L->sys_t0, t0.data(), sizeof(int) * (size_t)(nsys + 1), cudaMemcpyHostToDevice);
+    if (dj && e == cudaSuccess) {
+        std::vector<double> dl((size_t)n_int, 1.0);          // padding rows keep x = 0
+        for (int p = 0; p < n_int; p++)
+            if (map[(size_t)p] >= 0)
+                dl[(size_t)p] = (*dj)[(size_t)map[(size_t)p]];
+        e = cudaMalloc(&L->diag, sizeof(double) * (size_t)n_int);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(L->diag, dl.data(), sizeof(double) * (size_t)n_int, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         layout_release(L);
         return fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "batched layout: %s",
@@ -1152,8 +1174,6 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
     if (nsys < 1 || !sys_row_ptr || !b || !x || !tol || !out)
         return fail(ctx, PBCG_ERR_INVALID, "bad batched arguments");
-    if (ctx->precond != PBCG_PRECOND_NONE)
-        return fail(ctx, PBCG_ERR_INVALID, "preconditioning applies to pbcg_solve only");
     if (maxit < 0)
         return fail(ctx, PBCG_ERR_INVALID, "maxit must be >= 0");
     if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED && alg != PBCG_ALG_PIPELINED_RR)
@@ -1173,8 +1193,12 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         if (!(htol[k] > 0.0))
             return fail(ctx, PBCG_ERR_INVALID, "tol[%d] must be > 0", k);
     }
-    int rc = build_layout(ctx, m, srp);
+    const bool jac = ctx->precond == PBCG_PRECOND_JACOBI;
+    std::vector<double> dj;
+    int rc = jac ? host_diagonal(ctx, m, dj) : 0;
     if (rc)
+        return rc;
+    if ((rc = build_layout(ctx, m, srp, jac ? &dj : nullptr)))
         return rc;
     const BatchLayout *L = m->bl;
     if ((rc = ensure_batch_ws(ctx, L, m->n, maxit)))
@@ -1194,6 +1218,11 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         dst = V.x;
         void *a2[4] = {(void *)&np, &mp, &src, &dst};
         CK(cudaLaunchKernel((void *)k_bgather, dim3(ctx->num_sms * 4), dim3(256), a2, 0, ctx->stream));
+        if (jac) {                                            // y0 = d x0
+            const double *dd = L->diag;
+            void *a4[3] = {(void *)&np, (void *)&dd, &dst};
+            CK(cudaLaunchKernel((void *)k_vmul, dim3(ctx->num_sms * 4), dim3(256), a4, 0, ctx->stream));
+        }
     }
     std::vector<Ctl> hc((size_t)nsys);
     for (int k = 0; k < nsys; k++) {
@@ -1288,6 +1317,11 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
     {
         int *mp = L->map;
         double *src = V.x, *dst = BW.io;
+        if (jac) {                                            // x = y / d
+            const double *dd = L->diag;
+            void *a4[3] = {(void *)&np, (void *)&dd, &src};
+            CK(cudaLaunchKernel((void *)k_vdiv, dim3(ctx->num_sms * 4), dim3(256), a4, 0, ctx->stream));
+        }
         void *a3[4] = {(void *)&np, &mp, &src, &dst};
         CK(cudaLaunchKernel((void *)k_bscatter, dim3(ctx->num_sms * 4), dim3(256), a3, 0, ctx->stream));
         CK(cudaMemcpyAsync(x, BW.io, sizeof(double) * (size_t)m->n, cudaMemcpyDefault, ctx->stream));

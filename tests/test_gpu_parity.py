@@ -379,13 +379,42 @@ def test_jacobi_rejections(ctx):
         with pytest.raises(pbcg.PbcgError):
             ctx.solve(M, inputs.rhs_ones(A), np.zeros(A.n), 1e-8, 10, 1, 1)     # zero diagonal
         M.free()
-        systems = [inputs.convdiff2d(6, 2.0), inputs.convdiff2d(5, 2.0)]
-        Bm, srp = inputs.block_diag(systems)
-        M = ctx.upload_csr(Bm)
-        with pytest.raises(pbcg.PbcgError):
-            ctx.solve_batched(M, srp, inputs.rhs_ones(Bm), np.zeros(Bm.n), np.full(2, 1e-8), 10)
-        M.free()
     finally:
         ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_NONE)
     with pytest.raises(pbcg.PbcgError):
         ctx.set_option(pbcg.OPT_PRECOND, 7)
+
+
+def test_jacobi_batched_bitwise(ctx, orc):
+    """Jacobi in a batched solve is Jacobi on every block: each system equals
+    the oracle's preconditioned solve bit for bit; switching it off again gives
+    the unpreconditioned results (the cached layout is rebuilt)."""
+    from paper_2404_13216_gb300 import pbcg
+    rng = np.random.default_rng(12)
+    systems = []
+    for side in (14, 21, 9):
+        A = inputs.convdiff2d(side, float(rng.uniform(5, 60)))
+        v = A.vals.copy()
+        for i in range(A.n):
+            for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                if A.col_idx[k] == i:
+                    v[k] *= 10.0 ** rng.uniform(-1.5, 1.5)
+        systems.append(inputs.CSR(A.n, A.row_ptr, A.col_idx, v))
+    systems.append(inputs.powerlaw(n=900, mean_len=10, max_len=120, seed=4))
+    Bm, srp = inputs.block_diag(systems)
+    b = inputs.rhs_ones(Bm)
+    M = ctx.upload_csr(Bm)
+    for jac in (True, False, True):
+        ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_JACOBI if jac else pbcg.PRECOND_NONE)
+        try:
+            x = np.full(Bm.n, 0.5)
+            res = ctx.solve_batched(M, srp, b, x, np.full(len(systems), 1e-10), 800, 1, 1)
+        finally:
+            ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_NONE)
+        for k, S in enumerate(systems):
+            r0, r1 = srp[k], srp[k + 1]
+            ref = orc.solve(S.row_ptr, S.col_idx, S.vals, b[r0:r1], x0=np.full(S.n, 0.5), tol=1e-10, maxit=800,
+                            alg=1, mode=1, jacobi=jac)
+            assert res[k].status == ref.status and res[k].iters == ref.iters, (jac, k)
+            assert same(x[r0:r1], ref.x), (jac, k)
+    M.free()
