@@ -554,8 +554,7 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, Loop
     for (auto &bk : body_kernels(alg, mode, m->narrow)) {
         void *args4[4] = {&A, &V, &c, &wk};
         void *args3[3] = {&A, &V, &c};
-        cudaKernelNodeParams kp;
-        memset(&kp, 0, sizeof kp);
+        cudaKernelNodeParams kp{};
         kp.func = bk.fn;
         kp.gridDim = dim3(grid_for(ctx, bk.fn, A.nslices, bk.smem));
         kp.blockDim = dim3(THREADS);
@@ -1280,8 +1279,7 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         cudaGraphNode_t prev = nullptr;
         for (auto &bk : body) {
             void *args[3] = {&A, &V, &B};
-            cudaKernelNodeParams kp;
-            memset(&kp, 0, sizeof kp);
+            cudaKernelNodeParams kp{};
             kp.func = bk.fn;
             kp.gridDim = dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem));
             kp.blockDim = dim3(THREADS);
@@ -1294,8 +1292,7 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         unsigned long long hv = (unsigned long long)h;
         int one = 1;
         void *cargs[3] = {&B, &hv, &one};
-        cudaKernelNodeParams kp;
-        memset(&kp, 0, sizeof kp);
+        cudaKernelNodeParams kp{};
         kp.func = (void *)k_batch_ctl;
         kp.gridDim = dim3(1);
         kp.blockDim = dim3(1024);
@@ -1583,8 +1580,7 @@ int pool_build_graph(pbcg_ctx *ctx, pbcg_pool *P)
     auto ctl_node = [&](cudaGraph_t g, cudaGraphNode_t *dep, int first, cudaGraphNode_t *node) -> int {
         int f = first;
         void *cargs[] = {&B, &lvn, &lvp, &lvt, &left, &hv, &f};
-        cudaKernelNodeParams kp;
-        memset(&kp, 0, sizeof kp);
+        cudaKernelNodeParams kp{};
         kp.func = (void *)k_pool_ctl;
         kp.gridDim = dim3(1);
         kp.blockDim = dim3(1024);
@@ -1608,8 +1604,7 @@ int pool_build_graph(pbcg_ctx *ctx, pbcg_pool *P)
     cudaGraphNode_t prev = nullptr;
     for (auto &bk : body) {
         void *args[3] = {&A, &V, &B};
-        cudaKernelNodeParams kp;
-        memset(&kp, 0, sizeof kp);
+        cudaKernelNodeParams kp{};
         kp.func = bk.fn;
         kp.gridDim = dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem));
         kp.blockDim = dim3(THREADS);
