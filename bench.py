@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "p-BiCGStab iters/s & HBM GB/s, exact vs plain dots; batched solves/s & p99"
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth, for context beside the measured peak
 N_SIDE, PECLET, WIND, TOL, MAXIT = 128, 50.0, (1.0, 0.5, 0.25), 1e-10, 1000
 WORKLOAD = ("3D convection-diffusion 7-point upwind 128^3 (n=2097152, nnz=14581760), wind (1,0.5,0.25), "
             "Peclet 50, FP64 CSR, b=A*ones, x0=0, rel tol 1e-10, p-BiCGStab")
@@ -280,6 +281,7 @@ def run_ours(args):
 
     peak, peak_kind = peaks()
     iter_bytes = 2 * M_bytes + 23 * V_bytes
+    min_bytes = 2 * M_bytes + 17 * V_bytes     # every vector read once
     kern_bytes = {"pipe_x": M_bytes + 11 * V_bytes, "pipe_y": M_bytes + 12 * V_bytes}
 
     def kernel_table(prof):
@@ -341,7 +343,13 @@ def run_ours(args):
         "exact_over_plain_time_per_iter": us_it_e / us_it_p,
         "iteration_roofline": {"bytes_per_iter": iter_bytes, "frac_exact": iter_bytes / (us_it_e * 1e-6) / 1e9 / peak,
                                "frac_plain": iter_bytes / (us_it_p * 1e-6) / 1e9 / peak, "peak_gbs": peak,
-                               "peak_kind": peak_kind},
+                               "peak_kind": peak_kind,
+                               "frac_exact_of_nominal": iter_bytes / (us_it_e * 1e-6) / 1e9 / NOMINAL_HBM_GBS,
+                               "frac_plain_of_nominal": iter_bytes / (us_it_p * 1e-6) / 1e9 / NOMINAL_HBM_GBS,
+                               "nominal_gbs": NOMINAL_HBM_GBS,
+                               "bytes_per_iter_min": min_bytes,
+                               "frac_exact_min_bytes": min_bytes / (us_it_e * 1e-6) / 1e9 / peak,
+                               "frac_plain_min_bytes": min_bytes / (us_it_p * 1e-6) / 1e9 / peak},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "traffic": traffic, "algorithmic_bytes_per_launch": kern_bytes.get(dom_base),
                      "peak_kind": peak_kind},

@@ -48,31 +48,6 @@ struct Prod {
     bool nonfinite;              // an operand is Inf or NaN
 };
 
-// signed product words shifted left by r (0..31): u0..u4, u4 carrying the sign
-struct Shifted {
-    uint32_t u0, u1, u2, u3, u4, sgn;
-};
-
-__device__ __forceinline__ Shifted signed_shift(const Prod &p, uint32_t r)
-{
-    uint32_t mask = 0u - p.neg;
-    uint32_t w0 = p.w0 ^ mask, w1 = p.w1 ^ mask, w2 = p.w2 ^ mask, w3 = p.w3 ^ mask;
-    asm("add.cc.u32 %0, %0, %4;\n\t"
-        "addc.cc.u32 %1, %1, 0;\n\t"
-        "addc.cc.u32 %2, %2, 0;\n\t"
-        "addc.u32 %3, %3, 0;"
-        : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
-        : "r"(p.neg));
-    Shifted s;
-    s.sgn = mask;
-    s.u0 = w0 << r;
-    s.u1 = __funnelshift_l(w0, w1, r);
-    s.u2 = __funnelshift_l(w1, w2, r);
-    s.u3 = __funnelshift_l(w2, w3, r);
-    s.u4 = __funnelshift_l(w3, mask, r);
-    return s;
-}
-
 // ---------------------------------------------------------------------------
 // CTA accumulator (shared memory) for ND dots
 // ---------------------------------------------------------------------------
@@ -136,25 +111,6 @@ __device__ __forceinline__ void add256(uint32_t (&a)[WIN_WORDS], const uint32_t 
         "addc.u32 %7, %7, %15;"
         : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7])
         : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]));
-}
-
-// add the shifted product s (sh = 32 q + r already applied for r) at word offset q (0..3)
-__device__ __forceinline__ void win_place(uint32_t (&acc)[WIN_WORDS], const Shifted &s, uint32_t q)
-{
-    const bool q1 = q & 1u, q2 = q & 2u;
-    // word t of the shifted product: u[t-q] for t-q in 0..4, the sign word above, 0 below
-    const uint32_t v0 = q1 ? 0u : s.u0, v1 = q1 ? s.u0 : s.u1, v2 = q1 ? s.u1 : s.u2;
-    const uint32_t v3 = q1 ? s.u2 : s.u3, v4 = q1 ? s.u3 : s.u4, v5 = q1 ? s.u4 : s.sgn;
-    uint32_t x[WIN_WORDS];
-    x[0] = q2 ? 0u : v0;
-    x[1] = q2 ? 0u : v1;
-    x[2] = q2 ? v0 : v2;
-    x[3] = q2 ? v1 : v3;
-    x[4] = q2 ? v2 : v4;
-    x[5] = q2 ? v3 : v5;
-    x[6] = q2 ? v4 : s.sgn;
-    x[7] = q2 ? v5 : s.sgn;
-    add256(acc, x);
 }
 
 // Sum the windows of the warp (all lanes call) and add the total, anchored at
@@ -247,8 +203,13 @@ __device__ __forceinline__ Prod dec_product(const Dec &a, const Dec &b)
 {
     Prod p;
     unsigned long long p0 = (unsigned long long)a.lo * b.lo;
-    unsigned long long m = (unsigned long long)a.hi * b.lo + (p0 >> 32);
-    m = (unsigned long long)a.lo * b.hi + m;
+    unsigned long long m;
+    if (SQUARE) {      // a == b: the two cross terms are equal (each < 2^53)
+        m = (((unsigned long long)a.hi * b.lo) << 1) + (p0 >> 32);
+    } else {
+        m = (unsigned long long)a.hi * b.lo + (p0 >> 32);
+        m = (unsigned long long)a.lo * b.hi + m;
+    }
     unsigned long long h = (unsigned long long)a.hi * b.hi + (m >> 32);
     p.w0 = (uint32_t)p0;
     p.w1 = (uint32_t)m;
@@ -260,24 +221,48 @@ __device__ __forceinline__ Prod dec_product(const Dec &a, const Dec &b)
     return p;
 }
 
-// positive product words shifted left by r (0..31) (squares need no sign handling)
-__device__ __forceinline__ Shifted unsigned_shift(const Prod &p, uint32_t r)
-{
-    Shifted s;
-    s.sgn = 0u;
-    s.u0 = p.w0 << r;
-    s.u1 = __funnelshift_l(p.w0, p.w1, r);
-    s.u2 = __funnelshift_l(p.w1, p.w2, r);
-    s.u3 = __funnelshift_l(p.w2, p.w3, r);
-    s.u4 = __funnelshift_l(p.w3, 0u, r);
-    return s;
-}
-
+// acc += (-1)^neg |p| 2^sh for 0 <= sh <= WIN_SMAX.  A negative term is added
+// as its 256-bit one's complement plus one: the words of |p| << sh and the
+// words around them are XORed with the sign mask, and the +1 enters as the
+// carry into word 0, so no separate negation chain is needed.
 template <bool SQUARE>
 __device__ __forceinline__ void place_product(uint32_t (&acc)[WIN_WORDS], const Prod &p, int sh)
 {
-    Shifted s = SQUARE ? unsigned_shift(p, (uint32_t)(sh & 31)) : signed_shift(p, (uint32_t)(sh & 31));
-    win_place(acc, s, (uint32_t)sh >> 5);
+    const uint32_t r = (uint32_t)sh & 31u, q = (uint32_t)sh >> 5;
+    const uint32_t m = SQUARE ? 0u : 0u - p.neg;
+    const uint32_t u0 = (p.w0 << r) ^ m, u1 = __funnelshift_l(p.w0, p.w1, r) ^ m;
+    const uint32_t u2 = __funnelshift_l(p.w1, p.w2, r) ^ m, u3 = __funnelshift_l(p.w2, p.w3, r) ^ m;
+    const uint32_t u4 = __funnelshift_l(p.w3, 0u, r) ^ m;
+    const bool q1 = q & 1u, q2 = q & 2u;
+    // word t of the term: u[t-q] for t-q in 0..4, the mask elsewhere
+    const uint32_t v0 = q1 ? m : u0, v1 = q1 ? u0 : u1, v2 = q1 ? u1 : u2;
+    const uint32_t v3 = q1 ? u2 : u3, v4 = q1 ? u3 : u4, v5 = q1 ? u4 : m;
+    uint32_t x[WIN_WORDS];
+    x[0] = q2 ? m : v0;
+    x[1] = q2 ? m : v1;
+    x[2] = q2 ? v0 : v2;
+    x[3] = q2 ? v1 : v3;
+    x[4] = q2 ? v2 : v4;
+    x[5] = q2 ? v3 : v5;
+    x[6] = q2 ? v4 : m;
+    x[7] = q2 ? v5 : m;
+    if (SQUARE) {
+        add256(acc, x);
+    } else {
+        uint32_t cf;
+        asm("add.cc.u32 %8, %16, 0xffffffff;\n\t"      // carry = neg
+            "addc.cc.u32 %0, %0, %9;\n\t"
+            "addc.cc.u32 %1, %1, %10;\n\t"
+            "addc.cc.u32 %2, %2, %11;\n\t"
+            "addc.cc.u32 %3, %3, %12;\n\t"
+            "addc.cc.u32 %4, %4, %13;\n\t"
+            "addc.cc.u32 %5, %5, %14;\n\t"
+            "addc.cc.u32 %6, %6, %15;\n\t"
+            "addc.u32 %7, %7, %17;"
+            : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5]), "+r"(acc[6]),
+              "+r"(acc[7]), "=r"(cf)
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(p.neg), "r"(x[7]));
+    }
 }
 
 // Products below the warp's window: deposit them together into a temporary
@@ -312,20 +297,27 @@ __device__ __forceinline__ void win_add(Win &w, CtaAcc<ND> &c, int d, const Dec 
 {
     nf |= act && (a.nf || b.nf);
     const int off = act ? a.e + b.e - 2 : -1;        // negative for zero operands and inactive lanes
-    const bool high = off >= 0 && (w.anchor < 0 || off - w.anchor > WIN_SMAX);
-    if (__any_sync(0xffffffffu, high)) {             // warp-uniform and rare
-        int m = __reduce_max_sync(0xffffffffu, off);
-        if (w.anchor >= 0)
-            win_flush_reset<ND>(w, c, d);
-        w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
-    }
-    const int sh = off - w.anchor;                   // <= WIN_SMAX for every lane with off >= 0
     const Prod p = dec_product<SQUARE>(a, b);
-    const bool low = off >= 0 && sh < 0;
-    if (off >= 0 && sh >= 0)
+    int sh = off - w.anchor;
+    // one vote covers the common case: every term lands inside the current window
+    const bool odd = off >= 0 && (w.anchor < 0 || sh > WIN_SMAX || sh < 0);
+    if (__any_sync(0xffffffffu, odd)) {
+        const bool high = off >= 0 && (w.anchor < 0 || sh > WIN_SMAX);
+        if (__any_sync(0xffffffffu, high)) {         // re-anchor at the warp maximum
+            const int m = __reduce_max_sync(0xffffffffu, off);
+            if (w.anchor >= 0)
+                win_flush_reset<ND>(w, c, d);
+            w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
+            sh = off - w.anchor;                     // <= WIN_SMAX for every lane with off >= 0
+        }
+        const bool low = off >= 0 && sh < 0;
+        if (off >= 0 && sh >= 0)
+            place_product<SQUARE>(w.a, p, sh);
+        if (__any_sync(0xffffffffu, low))
+            win_low<ND, SQUARE>(c, d, p, low ? off : -1);
+    } else if (off >= 0) {
         place_product<SQUARE>(w.a, p, sh);
-    if (__any_sync(0xffffffffu, low))
-        win_low<ND, SQUARE>(c, d, p, low ? off : -1);
+    }
 }
 
 // Deposit a*b.  Must be called by all 32 lanes of the warp together (the
