@@ -37,6 +37,7 @@ constexpr int NDIG = 136;        // 32-bit digits; 136*32 = 4352 bits cover 2^-2
 constexpr int WIN_WORDS = 8;     // per-lane window: 256-bit two's complement
 constexpr int WIN_SMAX = 120;    // largest left shift of a 106-bit product inside the window (3 words + 24 bits)
 constexpr int WIN_ROOM = 32;     // bits of room left above the warp maximum when anchoring
+constexpr int WIN_UNSET = -(1 << 24);   // anchor of an empty window: every term is above it
 
 // ---------------------------------------------------------------------------
 // decode and exact product
@@ -88,7 +89,7 @@ __device__ __forceinline__ void cta_touch(CtaAcc<ND> &c, int d, int k0, int k1)
 // ---------------------------------------------------------------------------
 struct Win {
     uint32_t a[WIN_WORDS];
-    int anchor;      // -1 while unset
+    int anchor;      // WIN_UNSET while unset
 };
 
 __device__ __forceinline__ void win_init(Win &w)
@@ -96,7 +97,7 @@ __device__ __forceinline__ void win_init(Win &w)
 #pragma unroll
     for (int t = 0; t < WIN_WORDS; t++)
         w.a[t] = 0u;
-    w.anchor = -1;
+    w.anchor = WIN_UNSET;
 }
 
 __device__ __forceinline__ void add256(uint32_t (&a)[WIN_WORDS], const uint32_t (&x)[WIN_WORDS])
@@ -287,37 +288,67 @@ __device__ __noinline__ void win_low(CtaAcc<ND> &c, int d, Prod p, int rem)
     }
 }
 
+// A term a*b prepared for a window: its exact product, LSB offset (negative
+// for zero operands and inactive lanes) and shift above the window's anchor;
+// `odd` when it does not land inside the window (also while it is unset).
+struct WinTerm {
+    Prod p;
+    int off, sh;
+    bool odd;
+};
+
+template <bool SQUARE>
+__device__ __forceinline__ WinTerm win_term(const Win &w, const Dec &a, const Dec &b, bool act, bool &nf)
+{
+    WinTerm t;
+    nf |= act && (a.nf || b.nf);
+    t.off = act ? a.e + b.e - 2 : -1;
+    t.p = dec_product<SQUARE>(a, b);
+    t.sh = t.off - w.anchor;
+    t.odd = t.off >= 0 && (uint32_t)t.sh > (uint32_t)WIN_SMAX;
+    return t;
+}
+
+// The common case, known warp-wide: every lane's term lands inside the window.
+template <bool SQUARE>
+__device__ __forceinline__ void win_put(Win &w, const WinTerm &t)
+{
+    if (t.off >= 0)
+        place_product<SQUARE>(w.a, t.p, t.sh);
+}
+
+// Deposit a prepared term.  All 32 lanes of the warp call together.  The
+// anchor is kept warp-uniform: a vote finds lanes whose term would not fit
+// the top of the window; only then is the window flushed and re-anchored at
+// the warp maximum.  Terms below the window take win_low.
+template <int ND, bool SQUARE>
+__device__ __forceinline__ void win_settle(Win &w, CtaAcc<ND> &c, int d, WinTerm t)
+{
+    if (!__any_sync(0xffffffffu, t.odd)) {
+        win_put<SQUARE>(w, t);
+        return;
+    }
+    const bool high = t.off >= 0 && t.sh > WIN_SMAX;
+    if (__any_sync(0xffffffffu, high)) {             // re-anchor at the warp maximum
+        const int m = __reduce_max_sync(0xffffffffu, t.off);
+        if (w.anchor >= 0)
+            win_flush_reset<ND>(w, c, d);
+        w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
+        t.sh = t.off - w.anchor;                     // <= WIN_SMAX for every lane with off >= 0
+    }
+    const bool low = t.off >= 0 && t.sh < 0;
+    if (t.off >= 0 && t.sh >= 0)
+        place_product<SQUARE>(w.a, t.p, t.sh);
+    if (__any_sync(0xffffffffu, low))
+        win_low<ND, SQUARE>(c, d, t.p, low ? t.off : -1);
+}
+
 // Deposit a*b for decoded operands.  All 32 lanes of the warp call together.
-// The anchor is kept warp-uniform: a vote finds lanes whose product would not
-// fit the top of the window; only then is the window flushed and re-anchored
-// at the warp maximum.  Products below the window take win_low.
 template <int ND, bool SQUARE>
 __device__ __forceinline__ void win_add(Win &w, CtaAcc<ND> &c, int d, const Dec &a, const Dec &b, bool act,
                                         bool &nf)
 {
-    nf |= act && (a.nf || b.nf);
-    const int off = act ? a.e + b.e - 2 : -1;        // negative for zero operands and inactive lanes
-    const Prod p = dec_product<SQUARE>(a, b);
-    int sh = off - w.anchor;
-    // one vote covers the common case: every term lands inside the current window
-    const bool odd = off >= 0 && (w.anchor < 0 || sh > WIN_SMAX || sh < 0);
-    if (__any_sync(0xffffffffu, odd)) {
-        const bool high = off >= 0 && (w.anchor < 0 || sh > WIN_SMAX);
-        if (__any_sync(0xffffffffu, high)) {         // re-anchor at the warp maximum
-            const int m = __reduce_max_sync(0xffffffffu, off);
-            if (w.anchor >= 0)
-                win_flush_reset<ND>(w, c, d);
-            w.anchor = max(m - WIN_SMAX + WIN_ROOM, 0);
-            sh = off - w.anchor;                     // <= WIN_SMAX for every lane with off >= 0
-        }
-        const bool low = off >= 0 && sh < 0;
-        if (off >= 0 && sh >= 0)
-            place_product<SQUARE>(w.a, p, sh);
-        if (__any_sync(0xffffffffu, low))
-            win_low<ND, SQUARE>(c, d, p, low ? off : -1);
-    } else if (off >= 0) {
-        place_product<SQUARE>(w.a, p, sh);
-    }
+    win_settle<ND, SQUARE>(w, c, d, win_term<SQUARE>(w, a, b, act, nf));
 }
 
 // Deposit a*b.  Must be called by all 32 lanes of the warp together (the

@@ -1108,6 +1108,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
                 V.y[i] = y;
             }
         }
+        // (one vote for all four terms, as in pass Y, needs more registers than pass X has: spills)
         const Dec dq = decode(q), dy = decode(y), dr = decode(r0i), ds = decode(si), dz = decode(zi);
         D.template add2<false>(sh, 0, q, y, dq, dy, act);
         D.template add2<true>(sh, 1, y, y, dy, dy, act);
@@ -1170,10 +1171,26 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
                 V.w[i] = wn;
             }
         }
-        const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
-        D.template add2<false>(sh, 0, r0i, rn, dr0, dr, act);
-        D.template add2<false>(sh, 1, r0i, wn, dr0, dw, act);
-        D.template add2<true>(sh, 2, rn, rn, dr, dr, act);
+        if constexpr (MODE == 1) {
+            // one vote for the common case in which all three terms land in their windows
+            const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
+            const WinTerm t0 = win_term<false>(D.win[0], dr0, dr, act, D.nf[0]);
+            const WinTerm t1 = win_term<false>(D.win[1], dr0, dw, act, D.nf[1]);
+            const WinTerm t2 = win_term<true>(D.win[2], dr, dr, act, D.nf[2]);
+            if (__any_sync(0xffffffffu, t0.odd || t1.odd || t2.odd)) {
+                win_settle<3, false>(D.win[0], sh.acc, 0, t0);
+                win_settle<3, false>(D.win[1], sh.acc, 1, t1);
+                win_settle<3, true>(D.win[2], sh.acc, 2, t2);
+            } else {
+                win_put<false>(D.win[0], t0);
+                win_put<false>(D.win[1], t1);
+                win_put<true>(D.win[2], t2);
+            }
+        } else {
+            D.add(sh, 0, r0i, rn, act);
+            D.add(sh, 1, r0i, wn, act);
+            D.add(sh, 2, rn, rn, act);
+        }
     });
     if (!finalize<3, MODE>(D, sh, wk))
         return;
