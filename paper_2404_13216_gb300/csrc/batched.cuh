@@ -415,9 +415,7 @@ struct BPipeY : StepPipeY {
         }
         const double r0 = act ? P.vec(k, 5)[o] : 0.0, rn = act ? Yr.r : 0.0, wn = act ? Yr.w : 0.0;
         const Dec dr0 = decode(r0), dr = decode(rn), dw = decode(wn);
-        D.template add2<false>(sh, 0, r0, rn, dr0, dr, act);
-        D.template add2<false>(sh, 1, r0, wn, dr0, dw, act);
-        D.template add2<true>(sh, 2, rn, rn, dr, dr, act);
+        D.template add_row<3, false, false, true>(sh, act, r0, rn, dr0, dr, r0, wn, dr0, dw, rn, rn, &dr, &dr);
     }
 };
 

@@ -245,6 +245,41 @@ struct DotSet {
             s[d] = __fma_rn(a, b, s[d]);
         }
     }
+    // Dots 0 and 1 (and 2 when K == 3) of one row, each a (value, decoded)
+    // operand pair; SQk when dot k is a square.  Exact mode takes one vote for
+    // the common case in which every term lands in its window.
+    template <int K, bool SQ0, bool SQ1, bool SQ2 = false>
+    __device__ __forceinline__ void add_row(Shm<ND> &sh, bool act, double a0, double b0, const Dec &da0,
+                                            const Dec &db0, double a1, double b1, const Dec &da1, const Dec &db1,
+                                            double a2 = 0.0, double b2 = 0.0, const Dec *da2 = nullptr,
+                                            const Dec *db2 = nullptr)
+    {
+        static_assert(K == 2 || K == 3, "two or three terms");
+        if constexpr (MODE == 1) {
+            const WinTerm t0 = win_term<SQ0>(win[0], da0, db0, act, nf[0]);
+            const WinTerm t1 = win_term<SQ1>(win[1], da1, db1, act, nf[1]);
+            WinTerm t2;
+            if constexpr (K == 3)
+                t2 = win_term<SQ2>(win[2], *da2, *db2, act, nf[2]);
+            const bool odd = t0.odd || t1.odd || (K == 3 && t2.odd);
+            if (__any_sync(0xffffffffu, odd)) {
+                win_settle<ND, SQ0>(win[0], sh.acc, 0, t0);
+                win_settle<ND, SQ1>(win[1], sh.acc, 1, t1);
+                if constexpr (K == 3)
+                    win_settle<ND, SQ2>(win[2], sh.acc, 2, t2);
+            } else {
+                win_put<SQ0>(win[0], t0);
+                win_put<SQ1>(win[1], t1);
+                if constexpr (K == 3)
+                    win_put<SQ2>(win[2], t2);
+            }
+        } else if (act) {
+            s[0] = __fma_rn(a0, b0, s[0]);
+            s[1] = __fma_rn(a1, b1, s[1]);
+            if constexpr (K == 3)
+                s[2] = __fma_rn(a2, b2, s[2]);
+        }
+    }
 };
 
 template <int ND, int MODE>
@@ -1108,7 +1143,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
                 V.y[i] = y;
             }
         }
-        // (one vote for all four terms, as in pass Y, needs more registers than pass X has: spills)
+        // (one vote for all four terms, as add_row does, needs more registers than pass X has: spills)
         const Dec dq = decode(q), dy = decode(y), dr = decode(r0i), ds = decode(si), dz = decode(zi);
         D.template add2<false>(sh, 0, q, y, dq, dy, act);
         D.template add2<true>(sh, 1, y, y, dy, dy, act);
@@ -1171,26 +1206,8 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
                 V.w[i] = wn;
             }
         }
-        if constexpr (MODE == 1) {
-            // one vote for the common case in which all three terms land in their windows
-            const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
-            const WinTerm t0 = win_term<false>(D.win[0], dr0, dr, act, D.nf[0]);
-            const WinTerm t1 = win_term<false>(D.win[1], dr0, dw, act, D.nf[1]);
-            const WinTerm t2 = win_term<true>(D.win[2], dr, dr, act, D.nf[2]);
-            if (__any_sync(0xffffffffu, t0.odd || t1.odd || t2.odd)) {
-                win_settle<3, false>(D.win[0], sh.acc, 0, t0);
-                win_settle<3, false>(D.win[1], sh.acc, 1, t1);
-                win_settle<3, true>(D.win[2], sh.acc, 2, t2);
-            } else {
-                win_put<false>(D.win[0], t0);
-                win_put<false>(D.win[1], t1);
-                win_put<true>(D.win[2], t2);
-            }
-        } else {
-            D.add(sh, 0, r0i, rn, act);
-            D.add(sh, 1, r0i, wn, act);
-            D.add(sh, 2, rn, rn, act);
-        }
+        const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
+        D.template add_row<3, false, false, true>(sh, act, r0i, rn, dr0, dr, r0i, wn, dr0, dw, rn, rn, &dr, &dr);
     });
     if (!finalize<3, MODE>(D, sh, wk))
         return;
@@ -1344,8 +1361,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
                 V.y[i] = yi;
         }
         const Dec dq = decode(qi), dy = decode(yi);
-        D.template add2<false>(sh, 0, qi, yi, dq, dy, act);
-        D.template add2<true>(sh, 1, yi, yi, dy, dy, act);
+        D.template add_row<2, false, true>(sh, act, qi, yi, dq, dy, yi, yi, dy, dy);
     });
     if (!finalize<2, MODE>(D, sh, wk))
         return;
@@ -1383,8 +1399,7 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
             r0i = P.vec(k, 5)[o];
         }
         const Dec dr0 = decode(r0i), dr = decode(rn);
-        D.template add2<false>(sh, 0, r0i, rn, dr0, dr, act);
-        D.template add2<true>(sh, 1, rn, rn, dr, dr, act);
+        D.template add_row<2, false, true>(sh, act, r0i, rn, dr0, dr, rn, rn, dr, dr);
     });
     if (!finalize<2, MODE>(D, sh, wk))
         return;
