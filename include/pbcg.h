@@ -269,9 +269,17 @@ int pbcg_pool_room(const pbcg_pool *pool, int32_t *free_slots, int64_t *free_row
  *     y0 = x0 * d; x = y / d.  Residual histories and relres_* are those of
  *     the scaled system.  pbcg_solve_batched applies it to every system (a
  *     block-diagonal M); pools do not (their systems run unpreconditioned).
+ *   PBCG_OPT_SMALL_CLUSTER: 1 (default) or 0.  With 1, pbcg_solve runs the
+ *     iterations of Algorithm 2 (PBCG_ALG_PIPELINED) on a system of at most
+ *     16384 rows as one launch over one thread-block cluster of up to 16 CTAs
+ *     per stop test, the two reduction points of every iteration becoming
+ *     cluster barriers; with 0 it uses the two-pass launch graph whatever the
+ *     size.  Exact-mode results are bit-identical either way; plain-mode dots
+ *     sum their partials over fewer CTAs.  pbcg_profile_solve always runs the
+ *     passes.
  * Returns 0, or INVALID for an unknown option or value.
  */
-enum { PBCG_OPT_RR_PERIOD = 1, PBCG_OPT_PRECOND = 3 };
+enum { PBCG_OPT_RR_PERIOD = 1, PBCG_OPT_PRECOND = 3, PBCG_OPT_SMALL_CLUSTER = 4 };
 enum { PBCG_PRECOND_NONE = 0, PBCG_PRECOND_JACOBI = 1 };
 int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value);
 

@@ -22,6 +22,7 @@
 
 #include "../../include/pbcg.h"
 #include "batched.cuh"
+#include "cluster.cuh"
 
 using namespace pbcg;
 
@@ -68,6 +69,7 @@ struct pbcg_mat {
     double *diag = nullptr;    // [n] solver-order diagonal for Jacobi preconditioning (built on first use)
     double *va_jac = nullptr;  // [padded] entries of A M^-1, M = diag(A)
     std::vector<int32_t> h_rp, h_ci;   // host copy of the CSR (for per-batch layouts)
+    std::vector<int> h_sloff;          // [nslices + 1] host copy of sl_off
     std::vector<double> h_va;
     struct BatchLayout *bl;            // tile-aligned layout of the last batched solve, or NULL
 };
@@ -99,6 +101,8 @@ struct pbcg_ctx {
     std::map<const void *, int> occ;   // resident CTAs per SM of each kernel
     int rr_period = 50;                // residual replacement period of PBCG_ALG_PIPELINED_RR
     int precond = PBCG_PRECOND_NONE;   // preconditioner of pbcg_solve
+    int small_cluster = 1;             // Algorithm 2 on small systems as one cluster launch
+    std::map<long long, bool> cl_ok;   // cluster shapes (mode, CTAs, shared memory) that can be resident
     // batched solves
     struct {
         long long n_cap = 0;
@@ -739,6 +743,96 @@ int vec_out(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst)
     return 0;
 }
 
+// Launch shape of k_pipe_cluster for a small system.
+struct ClusterShape {
+    int ctas, rpt, lg, emax;
+    size_t smem;
+};
+
+cudaLaunchConfig_t cluster_config(pbcg_ctx *ctx, const ClusterShape &S, cudaLaunchAttribute *at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(S.ctas);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = S.smem;
+    cfg.stream = ctx->stream;
+    *at = cudaLaunchAttribute{};
+    at->id = cudaLaunchAttributeClusterDimension;
+    at->val.clusterDim.x = S.ctas;
+    at->val.clusterDim.y = 1;
+    at->val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// The cluster shape of a small system: the fewest rows per thread (1, 2 or 4)
+// that fit the system in one cluster of at most 16 CTAs, with every CTA's
+// rows of the vectors and matrix in its shared memory; false when there is
+// none (too many rows, rows too wide, or no such cluster can be resident).
+bool cluster_shape(pbcg_ctx *ctx, const pbcg_mat *m, int mode, ClusterShape *out)
+{
+    const void *fn = mode ? (const void *)k_pipe_cluster<1> : (const void *)k_pipe_cluster<0>;
+    if (m->n < 1 || m->h_sloff.size() != (size_t)m->nslices + 1)
+        return false;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    for (int rpt = 1; rpt <= CLUSTER_MAX_RPT; rpt *= 2) {
+        const int rows = rpt * THREADS, nsl = rows / 32;
+        const long long ctas = ((long long)m->n + rows - 1) / rows;
+        if (ctas > CLUSTER_MAX_CTAS)
+            continue;
+        int emax = 0;
+        for (long long b = 0; b < ctas; b++) {
+            const int s0 = (int)std::min<long long>(b * nsl, m->nslices);
+            const int s1 = (int)std::min<long long>(b * nsl + nsl, m->nslices);
+            emax = std::max(emax, m->h_sloff[(size_t)s1] - m->h_sloff[(size_t)s0]);
+        }
+        ClusterShape S{(int)ctas, rpt, 31 - __builtin_clz((unsigned)rows), emax, cluster_smem_bytes(rows, emax)};
+        if (S.smem + fa.sharedSizeBytes > (size_t)optin)
+            return false;                                   // more rows per thread only needs more
+        const long long key = ((long long)mode << 60) | ((long long)S.ctas << 48) | (long long)S.smem;
+        auto it = ctx->cl_ok.find(key);
+        bool ok;
+        if (it != ctx->cl_ok.end()) {
+            ok = it->second;
+        } else {
+            ok = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+                 cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem) == cudaSuccess;
+            if (ok) {
+                cudaLaunchAttribute at;
+                cudaLaunchConfig_t cfg = cluster_config(ctx, S, &at);
+                int num = 0;
+                ok = cudaOccupancyMaxActiveClusters(&num, fn, &cfg) == cudaSuccess && num >= 1;
+            }
+            cudaGetLastError();
+            ctx->cl_ok[key] = ok;
+        }
+        if (!ok)
+            return false;
+        *out = S;
+        return true;
+    }
+    return false;
+}
+
+int launch_cluster(pbcg_ctx *ctx, int mode, Mat &A, Vecs &V, Ctl *c, const ClusterShape &S)
+{
+    const void *fn = mode ? (const void *)k_pipe_cluster<1> : (const void *)k_pipe_cluster<0>;
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
+    cudaLaunchAttribute at;
+    cudaLaunchConfig_t cfg = cluster_config(ctx, S, &at);
+    int rpt = S.rpt, lg = S.lg, emax = S.emax;
+    void *args[6] = {&A, &V, &c, &rpt, &lg, &emax};
+    CK(cudaLaunchKernelExC(&cfg, fn, args));
+    return 0;
+}
+
 int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, double tol, int32_t maxit, int alg,
                int mode, pbcg_result *out, Prof *prof)
 {
@@ -823,11 +917,17 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         if (st != ST_RUNNING)
             break;
         true_done = false;
+        ClusterShape cs;
         if (prof) {
             // host-driven iteration, one kernel at a time
             for (auto &bk : body)
                 if ((rc = L.go(bk.name, bk.fn, A, V, ws.ctl, ws.wk, bk.has_work, bk.smem)))
                     return rc;
+        } else if (alg == PBCG_ALG_PIPELINED && ctx->small_cluster && cluster_shape(ctx, m, mode, &cs)) {
+            // small system: every iteration up to the next stop in one cluster launch
+            if ((rc = launch_cluster(ctx, mode, A, V, ws.ctl, cs)))
+                return rc;
+            L.launches += 1;
         } else {
             LoopGraph *G = nullptr;
             if ((rc = get_loop(ctx, m, alg, mode, jac, &G)))
@@ -1739,6 +1839,7 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     m->va = nullptr;
     m->narrow = S.narrow;
     m->bl = nullptr;
+    m->h_sloff.assign(S.sl_off.begin(), S.sl_off.begin() + (S.nslices + 1));
     m->h_rp = std::move(hrp);
     m->h_ci = std::move(hci);
     m->h_va = std::move(hva);
@@ -1837,6 +1938,12 @@ int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value)
         if (value < 1 || value > INT32_MAX)
             return fail(ctx, PBCG_ERR_INVALID, "residual replacement period must be >= 1");
         ctx->rr_period = (int)value;
+        return 0;
+    }
+    if (option == PBCG_OPT_SMALL_CLUSTER) {
+        if (value != 0 && value != 1)
+            return fail(ctx, PBCG_ERR_INVALID, "PBCG_OPT_SMALL_CLUSTER takes 0 or 1");
+        ctx->small_cluster = (int)value;
         return 0;
     }
     if (option == PBCG_OPT_PRECOND) {

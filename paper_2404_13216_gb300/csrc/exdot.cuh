@@ -442,9 +442,12 @@ static __device__ double round_digits(const unsigned long long *dig, int k0, int
         return 0.0;
     int h = hk * 32 + 31 - __clz(scratch[hk]);
     int lsb = max(h - 52, 1074);
-    unsigned long long m = 0ull;
-    for (int i = h; i >= lsb; i--)
-        m = (m << 1) | bit_at(scratch, k0, top, i);
+    // m = bits lsb..h (at most 53): the three words from lsb's word up hold
+    // them, and every bit above h is 0
+    auto word = [&](int k) -> unsigned long long { return (k >= k0 && k <= top) ? scratch[k] : 0u; };
+    const int kl = lsb >> 5, sl = lsb & 31;
+    const unsigned long long lo64 = word(kl) | (word(kl + 1) << 32);
+    unsigned long long m = sl ? (lo64 >> sl) | (word(kl + 2) << (64 - sl)) : lo64;
     uint32_t rb = bit_at(scratch, k0, top, lsb - 1);
     uint32_t st = 0u;
     int sk = (lsb - 1) >> 5;

@@ -261,7 +261,9 @@ struct DotSet {
             WinTerm t2;
             if constexpr (K == 3)
                 t2 = win_term<SQ2>(win[2], *da2, *db2, act, nf[2]);
-            const bool odd = t0.odd || t1.odd || (K == 3 && t2.odd);
+            bool odd = t0.odd || t1.odd;
+            if constexpr (K == 3)
+                odd = odd || t2.odd;
             if (__any_sync(0xffffffffu, odd)) {
                 win_settle<ND, SQ0>(win[0], sh.acc, 0, t0);
                 win_settle<ND, SQ1>(win[1], sh.acc, 1, t1);
@@ -337,10 +339,11 @@ __device__ __forceinline__ void warp_sum_plain(const double (&s)[ND], double (&o
     }
 }
 
-// Merge the CTA's dots grid-wide.  Returns true in the last CTA, whose
-// sh.dv[] then holds the finished dot values.  Called by every thread.
+// First half of a merge: the CTA's windows (exact) or plain partials are
+// summed within the CTA and published in global memory (wk->g digits or
+// wk->part[d][blockIdx.x]).  Called by every thread.
 template <int ND, int MODE>
-__device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
+__device__ __forceinline__ void merge_publish(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (MODE == 1) {
@@ -369,14 +372,15 @@ __device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
         wk->part[threadIdx.x * wk->maxgrid + blockIdx.x] = v;
     }
     __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int t = atomicAdd(&wk->ticket, 1u);
-        sh.last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!sh.last)
-        return false;
+}
+
+// Second half, in one CTA once every CTA has published: round the exact
+// accumulators (and reset them) or sum the plain partials in CTA order, into
+// sh.dv.  Called by every thread of that CTA.
+template <int ND, int MODE>
+__device__ __forceinline__ void merge_finish(Shm<ND> &sh, Work *wk)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __threadfence();
     if (MODE == 1) {
         gacc_round_reset_cta<ND>(wk->g, sh.acc, sh.scratch, sh.dv);
@@ -391,6 +395,23 @@ __device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
         if (lane == 0)
             sh.dv[warp] = v;
     }
+}
+
+// Merge the CTA's dots grid-wide.  Returns true in the last CTA, whose
+// sh.dv[] then holds the finished dot values.  Called by every thread.
+template <int ND, int MODE>
+__device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
+{
+    merge_publish<ND, MODE>(D, sh, wk);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(&wk->ticket, 1u);
+        sh.last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!sh.last)
+        return false;
+    merge_finish<ND, MODE>(sh, wk);
     if (threadIdx.x == 0)
         wk->ticket = 0u;
     __syncthreads();
@@ -1045,6 +1066,46 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
     }
 }
 
+// Scalar tails of the p-BiCGStab passes (one thread, after the merge):
+// pass X stores (q,y), (y,y), (r0,s), (r0,z) and forms omega_i; pass Y stores
+// (r0,r), (r0,w), (r,r), counts the iteration and takes the stop test, beta
+// and alpha.
+static __device__ void pipe_x_tail(Ctl *c, const double *dv)
+{
+    double qy = dv[0], yy = dv[1];
+    c->qy = qy;
+    c->yy = yy;
+    c->rs = dv[2];
+    c->rz = dv[3];
+    if (c->err) {
+        c->status = ST_TIMEOUT;
+        set_cond(c);
+    } else if (!fin(qy) || !fin(yy)) {
+        c->status = 3;
+        set_cond(c);
+    } else {
+        c->omega = (yy == 0.0) ? 0.0 : __ddiv_rn(qy, yy);
+    }
+}
+
+static __device__ void pipe_y_tail(Ctl *c, const double *dv)
+{
+    double rho_new = dv[0], rw = dv[1], rr = dv[2];
+    c->rho_new = rho_new;
+    c->rw = rw;
+    c->rr = rr;
+    c->phase = PH_ITER;
+    if (c->err) {
+        c->status = ST_TIMEOUT;
+    } else if (!fin(rho_new) || !fin(rw) || !fin(c->rs) || !fin(c->rz) || !fin(rr)) {
+        c->status = 3;
+    } else {
+        c->it += 1;
+        residual_step(c, rr);
+    }
+    set_cond(c);
+}
+
 // Row arithmetic of the p-BiCGStab passes (Algorithm 2), shared by the
 // single-system and batched passes so that both round identically.
 // Pass X: p, s, z (bit copies of r, w, t at i = 0; kept as they are right
@@ -1152,22 +1213,8 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     });
     if (!finalize<4, MODE>(D, sh, wk))
         return;
-    if (threadIdx.x == 0) {
-        double qy = sh.dv[0], yy = sh.dv[1];
-        c->qy = qy;
-        c->yy = yy;
-        c->rs = sh.dv[2];
-        c->rz = sh.dv[3];
-        if (c->err) {
-            c->status = ST_TIMEOUT;
-            set_cond(c);
-        } else if (!fin(qy) || !fin(yy)) {
-            c->status = 3;
-            set_cond(c);
-        } else {
-            c->omega = (yy == 0.0) ? 0.0 : __ddiv_rn(qy, yy);
-        }
-    }
+    if (threadIdx.x == 0)
+        pipe_x_tail(c, sh.dv);
 }
 
 // Y(i) staged: v_i = A z_i, x_{i+1}, r_{i+1}, w_{i+1}; dots (r0,r), (r0,w), (r,r); beta, alpha, stop test
@@ -1211,22 +1258,8 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     });
     if (!finalize<3, MODE>(D, sh, wk))
         return;
-    if (threadIdx.x == 0) {
-        double rho_new = sh.dv[0], rw = sh.dv[1], rr = sh.dv[2];
-        c->rho_new = rho_new;
-        c->rw = rw;
-        c->rr = rr;
-        c->phase = PH_ITER;
-        if (c->err) {
-            c->status = ST_TIMEOUT;
-        } else if (!fin(rho_new) || !fin(rw) || !fin(c->rs) || !fin(c->rz) || !fin(rr)) {
-            c->status = 3;
-        } else {
-            c->it += 1;
-            residual_step(c, rr);
-        }
-        set_cond(c);
-    }
+    if (threadIdx.x == 0)
+        pipe_y_tail(c, sh.dv);
 }
 
 // ---------------------------------------------------------------------------
