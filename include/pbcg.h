@@ -270,13 +270,13 @@ int pbcg_pool_room(const pbcg_pool *pool, int32_t *free_slots, int64_t *free_row
  *     the scaled system.  pbcg_solve_batched applies it to every system (a
  *     block-diagonal M); pools do not (their systems run unpreconditioned).
  *   PBCG_OPT_SMALL_CLUSTER: 1 (default) or 0.  With 1, pbcg_solve runs the
- *     iterations of Algorithm 2 (PBCG_ALG_PIPELINED) on a system of at most
- *     16384 rows as one launch over one thread-block cluster of up to 16 CTAs
- *     per stop test, the two reduction points of every iteration becoming
- *     cluster barriers; with 0 it uses the two-pass launch graph whatever the
- *     size.  Exact-mode results are bit-identical either way; plain-mode dots
- *     sum their partials over fewer CTAs.  pbcg_profile_solve always runs the
- *     passes.
+ *     iterations of Algorithm 1 or 2 (not PBCG_ALG_PIPELINED_RR) on a system
+ *     of at most 16384 rows whose rows fit in shared memory as one launch
+ *     over one thread-block cluster of up to 16 CTAs per stop test, the
+ *     reduction points of every iteration becoming cluster barriers; with 0
+ *     it uses the launch graph of passes whatever the size.  Exact-mode
+ *     results are bit-identical either way; plain-mode dots sum their
+ *     partials over fewer CTAs.  pbcg_profile_solve always runs the passes.
  * Returns 0, or INVALID for an unknown option or value.
  */
 enum { PBCG_OPT_RR_PERIOD = 1, PBCG_OPT_PRECOND = 3, PBCG_OPT_SMALL_CLUSTER = 4 };

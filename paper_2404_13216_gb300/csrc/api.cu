@@ -102,7 +102,7 @@ struct pbcg_ctx {
     int rr_period = 50;                // residual replacement period of PBCG_ALG_PIPELINED_RR
     int precond = PBCG_PRECOND_NONE;   // preconditioner of pbcg_solve
     int small_cluster = 1;             // Algorithm 2 on small systems as one cluster launch
-    std::map<long long, bool> cl_ok;   // cluster shapes (mode, CTAs, shared memory) that can be resident
+    std::map<long long, bool> cl_ok;   // cluster shapes (kernel, CTAs, shared memory) that can be resident
     // batched solves
     struct {
         long long n_cap = 0;
@@ -770,9 +770,16 @@ cudaLaunchConfig_t cluster_config(pbcg_ctx *ctx, const ClusterShape &S, cudaLaun
 // that fit the system in one cluster of at most 16 CTAs, with every CTA's
 // rows of the vectors and matrix in its shared memory; false when there is
 // none (too many rows, rows too wide, or no such cluster can be resident).
-bool cluster_shape(pbcg_ctx *ctx, const pbcg_mat *m, int mode, ClusterShape *out)
+const void *cluster_fn(int alg, int mode)
 {
-    const void *fn = mode ? (const void *)k_pipe_cluster<1> : (const void *)k_pipe_cluster<0>;
+    if (alg == PBCG_ALG_BICGSTAB)
+        return mode ? (const void *)k_bicg_cluster<1> : (const void *)k_bicg_cluster<0>;
+    return mode ? (const void *)k_pipe_cluster<1> : (const void *)k_pipe_cluster<0>;
+}
+
+bool cluster_shape(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, ClusterShape *out)
+{
+    const void *fn = cluster_fn(alg, mode);
     if (m->n < 1 || m->h_sloff.size() != (size_t)m->nslices + 1)
         return false;
     cudaFuncAttributes fa;
@@ -796,7 +803,7 @@ bool cluster_shape(pbcg_ctx *ctx, const pbcg_mat *m, int mode, ClusterShape *out
         ClusterShape S{(int)ctas, rpt, 31 - __builtin_clz((unsigned)rows), emax, cluster_smem_bytes(rows, emax)};
         if (S.smem + fa.sharedSizeBytes > (size_t)optin)
             return false;                                   // more rows per thread only needs more
-        const long long key = ((long long)mode << 60) | ((long long)S.ctas << 48) | (long long)S.smem;
+        const long long key = ((long long)(alg * 2 + mode) << 56) | ((long long)S.ctas << 48) | (long long)S.smem;
         auto it = ctx->cl_ok.find(key);
         bool ok;
         if (it != ctx->cl_ok.end()) {
@@ -821,9 +828,9 @@ bool cluster_shape(pbcg_ctx *ctx, const pbcg_mat *m, int mode, ClusterShape *out
     return false;
 }
 
-int launch_cluster(pbcg_ctx *ctx, int mode, Mat &A, Vecs &V, Ctl *c, const ClusterShape &S)
+int launch_cluster(pbcg_ctx *ctx, int alg, int mode, Mat &A, Vecs &V, Ctl *c, const ClusterShape &S)
 {
-    const void *fn = mode ? (const void *)k_pipe_cluster<1> : (const void *)k_pipe_cluster<0>;
+    const void *fn = cluster_fn(alg, mode);
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     cudaLaunchAttribute at;
     cudaLaunchConfig_t cfg = cluster_config(ctx, S, &at);
@@ -923,9 +930,9 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
             for (auto &bk : body)
                 if ((rc = L.go(bk.name, bk.fn, A, V, ws.ctl, ws.wk, bk.has_work, bk.smem)))
                     return rc;
-        } else if (alg == PBCG_ALG_PIPELINED && ctx->small_cluster && cluster_shape(ctx, m, mode, &cs)) {
+        } else if (alg != PBCG_ALG_PIPELINED_RR && ctx->small_cluster && cluster_shape(ctx, m, alg, mode, &cs)) {
             // small system: every iteration up to the next stop in one cluster launch
-            if ((rc = launch_cluster(ctx, mode, A, V, ws.ctl, cs)))
+            if ((rc = launch_cluster(ctx, alg, mode, A, V, ws.ctl, cs)))
                 return rc;
             L.launches += 1;
         } else {

@@ -1,5 +1,6 @@
-// cluster.cuh -- the whole p-BiCGStab iteration loop (Algorithm 2) of a small
-// system in one launch over one thread-block cluster, held in shared memory.
+// cluster.cuh -- the whole iteration loop of a small system (Algorithm 2, and
+// Algorithm 1 beside it) in one launch over one thread-block cluster, held in
+// shared memory.
 //
 // A system of a few thousand rows leaves the multi-pass launch graph bound by
 // latency: every iteration pays two kernel launches, two grid-wide merges
@@ -8,8 +9,9 @@
 // runs the iterations inside one kernel:
 //   - each CTA keeps its rows of the 11 solver vectors and of the SELL-32
 //     matrix in its own shared memory for the whole launch;
-//   - the SpMV gathers w (pass X) and z (pass Y) from the owning CTA's shared
-//     memory through distributed shared memory;
+//   - the SpMV gathers its operand (w and z in Algorithm 2, p and s, r in
+//     Algorithm 1) from the owning CTA's shared memory through distributed
+//     shared memory;
 //   - each reduction point is a cluster merge: every CTA adds its exact
 //     accumulator digits (or writes its plain partial) into CTA 0's shared
 //     memory, the cluster syncs (a hardware barrier), CTA 0 rounds (exact) or
@@ -79,6 +81,126 @@ __device__ __forceinline__ double spmv_cluster(const double *mva, const uint32_t
                 acc = __fma_rn(v[j], xv[j], acc);
     }
     return acc;
+}
+
+// same, with the gathered operand formed as fma(na, s[col], r[col]) (pass B of Algorithm 1)
+__device__ __forceinline__ double spmv_cluster_axpy(const double *mva, const uint32_t *mcode, int soff, int width,
+                                                    int len, int lane, double na, const double *const *gs,
+                                                    const double *const *gr)
+{
+    double acc = 0.0;
+    for (int j0 = 0; j0 < width; j0 += UNR) {
+        double v[UNR], xs[UNR], xr[UNR];
+        uint32_t cd[UNR];
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            if (j0 + j < len) {
+                const int e = soff + (j0 + j) * 32 + lane;
+                cd[j] = mcode[e];
+                v[j] = mva[e];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < UNR; j++) {
+            if (j0 + j < len) {
+                xs[j] = gs[cd[j] >> 16][cd[j] & 0xffffu];
+                xr[j] = gr[cd[j] >> 16][cd[j] & 0xffffu];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < UNR; j++)
+            if (j0 + j < len)
+                acc = __fma_rn(v[j], __fma_rn(na, xs[j], xr[j]), acc);
+    }
+    return acc;
+}
+
+// This CTA's rows in shared memory (dynamic): CL_NV vectors of `rows`
+// entries, the SELL entries of its slices (value and owner/local code), the
+// row lengths and the slices' local entry offsets.  gv[k][b] is vector k of
+// CTA b through distributed shared memory.
+struct ClusterRows {
+    double *vec, *mva;
+    uint32_t *mcode;
+    int *mlen, *msoff;
+    int rows, nsl, row0;
+    __device__ __forceinline__ double *v(int k) const { return vec + (size_t)k * rows; }
+    __device__ __forceinline__ int soff(int ls) const { return msoff[ls]; }
+    __device__ __forceinline__ int width(int ls) const { return (msoff[ls + 1] - msoff[ls]) >> 5; }
+};
+
+struct ClusterGather {
+    const double *gv[CL_NV][CLUSTER_MAX_CTAS];
+};
+
+// Fill this CTA's rows from global memory, CTA 0's hub from the control
+// block, the gather tables; ends with a cluster barrier.
+__device__ __forceinline__ ClusterRows cluster_load(const Mat &A, const Vecs &V, const Ctl *c, int rpt, int lg,
+                                                    int emax, uint8_t *dsm, ClusterHub &hub, ClusterGather &G,
+                                                    cooperative_groups::cluster_group &cl)
+{
+    ClusterRows R;
+    R.rows = rpt * THREADS;
+    R.nsl = R.rows / 32;
+    R.row0 = (int)blockIdx.x * R.rows;
+    R.vec = reinterpret_cast<double *>(dsm);
+    R.mva = R.vec + (size_t)CL_NV * R.rows;
+    R.mcode = reinterpret_cast<uint32_t *>(R.mva + emax);
+    R.mlen = reinterpret_cast<int *>(R.mcode + emax);
+    R.msoff = R.mlen + R.rows;
+    const int gs0 = min((int)blockIdx.x * R.nsl, A.nslices), gs1 = min(gs0 + R.nsl, A.nslices);
+    const int e0 = A.sl_off[gs0], ne = A.sl_off[gs1] - e0;
+    for (int t = threadIdx.x; t <= R.nsl; t += THREADS)
+        R.msoff[t] = A.sl_off[min(gs0 + t, gs1)] - e0;
+    for (int e = threadIdx.x; e < ne; e += THREADS) {
+        const int col = A.ci[e0 + e];
+        R.mva[e] = A.va[e0 + e];
+        R.mcode[e] = ((uint32_t)(col >> lg) << 16) | (uint32_t)(col & (R.rows - 1));
+    }
+    const double *const gsrc[CL_NV] = {V.x, V.r, V.w, V.t, V.p, V.s, V.z, V.v, V.q, V.y, V.r0};
+    for (int r = threadIdx.x; r < R.rows; r += THREADS) {
+        const int i = R.row0 + r;
+        R.mlen[r] = (i < A.nslices * 32) ? A.rlen[i] : 0;
+#pragma unroll
+        for (int k = 0; k < CL_NV; k++)
+            R.vec[(size_t)k * R.rows + r] = (i < A.n) ? gsrc[k][i] : 0.0;
+    }
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            hub.ctl = *c;
+            for (int d = 0; d < 4; d++) {
+                hub.kmin[d] = NDIG;
+                hub.kmax[d] = -1;
+                hub.nf[d] = 0;
+            }
+        }
+        for (int k = threadIdx.x; k < 4 * NDIG; k += THREADS)
+            (&hub.dig[0][0])[k] = 0ull;
+    }
+    for (int t = threadIdx.x; t < CL_NV * (int)gridDim.x; t += THREADS)
+        G.gv[t / gridDim.x][t % gridDim.x] = cl.map_shared_rank(R.v(t / gridDim.x), t % gridDim.x);
+    cl.sync();
+    return R;
+}
+
+// Write this CTA's rows of the vectors (all but r0) and CTA 0's control block
+// back to global memory; the final barrier keeps every CTA's shared memory
+// alive until no other CTA reads it.
+__device__ __forceinline__ void cluster_store(const Mat &A, const Vecs &V, Ctl *c, const ClusterRows &R,
+                                              const ClusterHub &hub, cooperative_groups::cluster_group &cl)
+{
+    double *const gdst[CL_NV - 1] = {V.x, V.r, V.w, V.t, V.p, V.s, V.z, V.v, V.q, V.y};
+    for (int r = threadIdx.x; r < R.rows; r += THREADS) {
+        const int i = R.row0 + r;
+        if (i < A.n) {
+#pragma unroll
+            for (int k = 0; k < CL_NV - 1; k++)
+                gdst[k][i] = R.vec[(size_t)k * R.rows + r];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *c = hub.ctl;
+    cl.sync();
 }
 
 // Merge the cluster's ND dots into dv (valid in CTA 0).  Every thread of every CTA calls.
@@ -175,56 +297,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     __shared__ Shm<4> sx;
     __shared__ Shm<3> sy;
     __shared__ ClusterHub hub;
-    __shared__ const double *gw[CLUSTER_MAX_CTAS], *gz[CLUSTER_MAX_CTAS];
-    const int rows = rpt * THREADS, nsl = rows / 32, me = (int)blockIdx.x, row0 = me * rows;
-    double *vec = reinterpret_cast<double *>(dsm);               // [CL_NV][rows]
-    double *mva = vec + (size_t)CL_NV * rows;                    // [emax]
-    uint32_t *mcode = reinterpret_cast<uint32_t *>(mva + emax);  // [emax]
-    int *mlen = reinterpret_cast<int *>(mcode + emax);           // [rows]
-    int *msoff = mlen + rows;                                    // [nsl + 1]
-    double *const Vx = vec + CV_X * rows, *const Vr = vec + CV_R * rows, *const Vw = vec + CV_W * rows;
-    double *const Vt = vec + CV_T * rows, *const Vp = vec + CV_P * rows, *const Vs = vec + CV_S * rows;
-    double *const Vz = vec + CV_Z * rows, *const Vv = vec + CV_V * rows, *const Vq = vec + CV_Q * rows;
-    double *const Vy = vec + CV_Y * rows, *const Vr0 = vec + CV_R0 * rows;
-
-    // ---- load this CTA's rows: matrix slices, row lengths, vectors
-    const int gs0 = min(me * nsl, A.nslices), gs1 = min(gs0 + nsl, A.nslices);
-    const int e0 = A.sl_off[gs0], ne = A.sl_off[gs1] - e0;
-    for (int t = threadIdx.x; t <= nsl; t += THREADS)
-        msoff[t] = A.sl_off[min(gs0 + t, gs1)] - e0;
-    for (int e = threadIdx.x; e < ne; e += THREADS) {
-        const int col = A.ci[e0 + e];
-        mva[e] = A.va[e0 + e];
-        mcode[e] = ((uint32_t)(col >> lg) << 16) | (uint32_t)(col & (rows - 1));
-    }
-    double *const gsrc[CL_NV] = {V.x, V.r, V.w, V.t, V.p, V.s, V.z, V.v, V.q, V.y, V.r0};
-    for (int r = threadIdx.x; r < rows; r += THREADS) {
-        const int i = row0 + r;
-        mlen[r] = (i < A.nslices * 32) ? A.rlen[i] : 0;
-#pragma unroll
-        for (int v = 0; v < CL_NV; v++)
-            vec[v * rows + r] = (i < A.n) ? gsrc[v][i] : 0.0;
-    }
-    if (me == 0 && threadIdx.x == 0) {
-        hub.ctl = *c;
-        for (int d = 0; d < 4; d++) {
-            hub.kmin[d] = NDIG;
-            hub.kmax[d] = -1;
-            hub.nf[d] = 0;
-        }
-    }
-    if (me == 0)
-        for (int k = threadIdx.x; k < 4 * NDIG; k += THREADS)
-            (&hub.dig[0][0])[k] = 0ull;
-    if (threadIdx.x < gridDim.x) {
-        gw[threadIdx.x] = cl.map_shared_rank(Vw, threadIdx.x);
-        gz[threadIdx.x] = cl.map_shared_rank(Vz, threadIdx.x);
-    }
+    __shared__ ClusterGather G;
+    const ClusterRows R = cluster_load(A, V, c, rpt, lg, emax, dsm, hub, G, cl);
     ClusterHub *const hub0 = cl.map_shared_rank(&hub, 0);
     const volatile Ctl *const c0 = &hub0->ctl;     // read after each cluster barrier
-    cl.sync();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int me = (int)blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *const Vx = R.v(CV_X), *const Vr = R.v(CV_R), *const Vw = R.v(CV_W), *const Vt = R.v(CV_T);
+    double *const Vp = R.v(CV_P), *const Vs = R.v(CV_S), *const Vz = R.v(CV_Z), *const Vv = R.v(CV_V);
+    double *const Vq = R.v(CV_Q), *const Vy = R.v(CV_Y), *const Vr0 = R.v(CV_R0);
     for (;;) {
         if (c0->status != ST_RUNNING)
             break;
@@ -238,7 +318,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             D.init();
             for (int k = 0; k < rpt; k++) {
                 const int r = k * THREADS + (int)threadIdx.x, ls = k * WARPS + warp;
-                const bool act = row0 + r < A.n;
+                const bool act = R.row0 + r < A.n;
                 double q = 0.0, y = 0.0, r0i = 0.0, si = 0.0, zi = 0.0;
                 if (act) {
                     const double ri = Vr[r], wi = Vw[r];
@@ -247,7 +327,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (first) {
                         ti = Vt[r];
                     } else {
-                        ti = spmv_cluster(mva, mcode, msoff[ls], (msoff[ls + 1] - msoff[ls]) >> 5, mlen[r], lane, gw);
+                        ti = spmv_cluster(R.mva, R.mcode, R.soff(ls), R.width(ls), R.mlen[r], lane, G.gv[CV_W]);
                         pold = Vp[r];
                         sold = Vs[r];
                         zold = Vz[r];
@@ -288,11 +368,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             D.init();
             for (int k = 0; k < rpt; k++) {
                 const int r = k * THREADS + (int)threadIdx.x, ls = k * WARPS + warp;
-                const bool act = row0 + r < A.n;
+                const bool act = R.row0 + r < A.n;
                 double rn = 0.0, wn = 0.0, r0i = 0.0;
                 if (act) {
-                    const double vi = spmv_cluster(mva, mcode, msoff[ls], (msoff[ls + 1] - msoff[ls]) >> 5, mlen[r],
-                                                   lane, gz);
+                    const double vi = spmv_cluster(R.mva, R.mcode, R.soff(ls), R.width(ls), R.mlen[r], lane, G.gv[CV_Z]);
                     const YRow Yr = pipe_y_row(alpha, omega, nalpha, nomega, Vq[r], Vy[r], Vp[r], Vx[r], Vt[r], vi);
                     Vx[r] = Yr.x;
                     Vv[r] = vi;
@@ -312,19 +391,123 @@ __global__ void __launch_bounds__(THREADS, 1)
             cl.sync();
         }
     }
+    cluster_store(A, V, c, R, hub, cl);
+}
 
-    // ---- write back: the vectors of this CTA's rows and the control block
-    for (int r = threadIdx.x; r < rows; r += THREADS) {
-        const int i = row0 + r;
-        if (i < A.n) {
-#pragma unroll
-            for (int v = 0; v < CL_NV - 1; v++)          // r0 is never written
-                gsrc[v][i] = vec[v * rows + r];
+// Iterations of Algorithm 1 (BiCGStab) in the same form: the passes P, A, B
+// and C of the launch graph become phases separated by cluster barriers
+// (after P) and cluster merges (after A, B and C).
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_bicg_cluster(Mat A, Vecs V, Ctl *c, int rpt, int lg, int emax)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ Shm<1> sa;
+    __shared__ Shm<2> sb;
+    __shared__ ClusterHub hub;
+    __shared__ ClusterGather G;
+    const ClusterRows R = cluster_load(A, V, c, rpt, lg, emax, dsm, hub, G, cl);
+    ClusterHub *const hub0 = cl.map_shared_rank(&hub, 0);
+    const volatile Ctl *const c0 = &hub0->ctl;
+    const int me = (int)blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *const Vx = R.v(CV_X), *const Vr = R.v(CV_R), *const Vp = R.v(CV_P), *const Vs = R.v(CV_S);
+    double *const Vy = R.v(CV_Y), *const Vr0 = R.v(CV_R0);
+    for (;;) {
+        if (c0->status != ST_RUNNING)
+            break;
+        if (c0->it > 0) {
+            // P: p = fma(beta, fma(-omega, s, p), r)
+            const double beta = c0->beta, nomega = -c0->omega;
+            for (int k = 0; k < rpt; k++) {
+                const int r = k * THREADS + (int)threadIdx.x;
+                if (R.row0 + r < A.n)
+                    Vp[r] = __fma_rn(beta, __fma_rn(nomega, Vs[r], Vp[r]), Vr[r]);
+            }
+            cl.sync();
+        }
+        {
+            // A: s = A p; dot (r0, s); alpha
+            shm_init<1, MODE>(sa);
+            __syncthreads();
+            DotSet<1, MODE> D;
+            D.init();
+            for (int k = 0; k < rpt; k++) {
+                const int r = k * THREADS + (int)threadIdx.x, ls = k * WARPS + warp;
+                const bool act = R.row0 + r < A.n;
+                double si = 0.0, r0i = 0.0;
+                if (act) {
+                    si = spmv_cluster(R.mva, R.mcode, R.soff(ls), R.width(ls), R.mlen[r], lane, G.gv[CV_P]);
+                    Vs[r] = si;
+                    r0i = Vr0[r];
+                }
+                const Dec dr = decode(r0i), ds = decode(si);
+                D.template add2<false>(sa, 0, r0i, si, dr, ds, act);
+            }
+            cluster_merge<1, MODE>(D, sa, hub, hub0, cl);
+            if (me == 0 && threadIdx.x == 0)
+                bicg_a_scalar(&hub.ctl, sa.dv[0]);
+            cl.sync();
+        }
+        if (c0->status != ST_RUNNING)
+            break;
+        {
+            // B: y = A q with q_j = fma(-alpha, s_j, r_j); dots (q,y), (y,y); omega
+            const double nalpha = -c0->alpha;
+            shm_init<2, MODE>(sb);
+            __syncthreads();
+            DotSet<2, MODE> D;
+            D.init();
+            for (int k = 0; k < rpt; k++) {
+                const int r = k * THREADS + (int)threadIdx.x, ls = k * WARPS + warp;
+                const bool act = R.row0 + r < A.n;
+                double qi = 0.0, yi = 0.0;
+                if (act) {
+                    yi = spmv_cluster_axpy(R.mva, R.mcode, R.soff(ls), R.width(ls), R.mlen[r], lane, nalpha,
+                                           G.gv[CV_S], G.gv[CV_R]);
+                    qi = __fma_rn(nalpha, Vs[r], Vr[r]);
+                    Vy[r] = yi;
+                }
+                const Dec dq = decode(qi), dy = decode(yi);
+                D.template add_row<2, false, true>(sb, act, qi, yi, dq, dy, yi, yi, dy, dy);
+            }
+            cluster_merge<2, MODE>(D, sb, hub, hub0, cl);
+            if (me == 0 && threadIdx.x == 0)
+                bicg_b_scalar(&hub.ctl, sb.dv[0], sb.dv[1]);
+            cl.sync();
+        }
+        if (c0->status != ST_RUNNING)
+            break;
+        {
+            // C: x, r updates; dots (r0,r), (r,r); beta, stop test
+            const double alpha = c0->alpha, omega = c0->omega;
+            const double nalpha = -alpha, nomega = -omega;
+            shm_init<2, MODE>(sb);
+            __syncthreads();
+            DotSet<2, MODE> D;
+            D.init();
+            for (int k = 0; k < rpt; k++) {
+                const int r = k * THREADS + (int)threadIdx.x;
+                const bool act = R.row0 + r < A.n;
+                double rn = 0.0, r0i = 0.0;
+                if (act) {
+                    const double q = __fma_rn(nalpha, Vs[r], Vr[r]);
+                    Vx[r] = __fma_rn(omega, q, __fma_rn(alpha, Vp[r], Vx[r]));
+                    rn = __fma_rn(nomega, Vy[r], q);
+                    Vr[r] = rn;
+                    r0i = Vr0[r];
+                }
+                const Dec dr0 = decode(r0i), dr = decode(rn);
+                D.template add_row<2, false, true>(sb, act, r0i, rn, dr0, dr, rn, rn, dr, dr);
+            }
+            cluster_merge<2, MODE>(D, sb, hub, hub0, cl);
+            if (me == 0 && threadIdx.x == 0)
+                bicg_c_scalar(&hub.ctl, sb.dv[0], sb.dv[1]);
+            cl.sync();
         }
     }
-    if (me == 0 && threadIdx.x == 0)
-        *c = hub.ctl;
-    cl.sync();       // no CTA leaves while another may still read its shared memory
+    cluster_store(A, V, c, R, hub, cl);
 }
 
 }  // namespace pbcg

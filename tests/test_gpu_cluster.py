@@ -1,9 +1,10 @@
-"""Small systems through the one-launch cluster loop of Algorithm 2.
+"""Small systems through the one-launch cluster loops of Algorithms 1 and 2.
 
-pbcg_solve runs p-BiCGStab on a system of at most 16384 rows as one launch
-over a thread-block cluster (PBCG_OPT_SMALL_CLUSTER, on by default).  Exact
-mode must be bit-identical to the oracle and to the two-pass launch graph
-(the option off); plain mode must meet the same tolerance bars as the passes.
+pbcg_solve runs BiCGStab and p-BiCGStab on a system of at most 16384 rows as
+one launch over a thread-block cluster (PBCG_OPT_SMALL_CLUSTER, on by
+default).  Exact mode must be bit-identical to the oracle and to the launch
+graph of passes (the option off); plain mode must meet the same tolerance
+bars as the passes.
 """
 import numpy as np
 import pytest
@@ -30,13 +31,13 @@ def same(a, b):
     return np.array_equal(np.asarray(a).view(np.int64), np.asarray(b).view(np.int64))
 
 
-def solve(ctx, A, b, tol, maxit, mode, cluster, x0=None):
+def solve(ctx, A, b, tol, maxit, mode, cluster, x0=None, alg=1):
     from paper_2404_13216_gb300 import pbcg
     ctx.set_option(pbcg.OPT_SMALL_CLUSTER, 1 if cluster else 0)
     try:
         M = ctx.upload_csr(A)
         x = np.zeros(A.n) if x0 is None else np.array(x0, dtype=np.float64)
-        r = ctx.solve(M, b, x, tol, maxit, pbcg.PIPELINED, mode)
+        r = ctx.solve(M, b, x, tol, maxit, alg, mode)
         h = ctx.history()
         M.free()
     finally:
@@ -55,13 +56,14 @@ SYSTEMS = {
 }
 
 
+@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
 @pytest.mark.parametrize("name", list(SYSTEMS))
-def test_cluster_exact_bitwise_vs_oracle_and_passes(ctx, orc, name):
+def test_cluster_exact_bitwise_vs_oracle_and_passes(ctx, orc, name, alg):
     A = SYSTEMS[name]()
     b = inputs.rhs_ones(A)
-    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=600, alg=1, mode=1, nthreads=8)
-    rc, xc, hc = solve(ctx, A, b, 1e-10, 600, 1, True)
-    rp, xp, hp = solve(ctx, A, b, 1e-10, 600, 1, False)
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=600, alg=alg, mode=1, nthreads=8)
+    rc, xc, hc = solve(ctx, A, b, 1e-10, 600, 1, True, alg=alg)
+    rp, xp, hp = solve(ctx, A, b, 1e-10, 600, 1, False, alg=alg)
     assert rc.status == ref.status and rc.iters == ref.iters, (rc, ref.status, ref.iters)
     assert same(hc, ref.history) and same(xc, ref.x)
     assert same([rc.relres_true], [ref.relres_true])
@@ -91,12 +93,13 @@ def test_cluster_limit_and_past_it(ctx, orc):
         assert (r.launches <= 8) == expect_cluster, r.launches
 
 
-def test_cluster_plain(ctx, orc):
+@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
+def test_cluster_plain(ctx, orc, alg):
     A = SYSTEMS["2d64"]()
     b = inputs.rhs_ones(A)
     tol = 1e-8
-    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=tol, maxit=2000, alg=1, mode=0, nthreads=1)
-    r, x, h = solve(ctx, A, b, tol, 2000, 0, True)
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=tol, maxit=2000, alg=alg, mode=0, nthreads=1)
+    r, x, h = solve(ctx, A, b, tol, 2000, 0, True, alg=alg)
     assert r.status == 0 and r.relres_true <= tol
     k = min(21, h.size, ref.history.size)
     rel = np.abs(h[:k] - ref.history[:k]) / np.abs(ref.history[:k])
