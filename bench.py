@@ -555,12 +555,23 @@ def run_ncu_case(args):
     from paper_2404_13216_gb300 import build, inputs
     build.build_library()
     from paper_2404_13216_gb300 import pbcg
-    A = inputs.powerlaw() if args.ncu_matrix == "powerlaw" else inputs.convdiff3d(args.ncu_side, PECLET, WIND)
+    if args.ncu_matrix == "powerlaw":
+        A = inputs.powerlaw()
+    elif args.ncu_matrix == "convdiff2d":
+        A = inputs.convdiff2d(args.ncu_side, 10.0)
+    else:
+        A = inputs.convdiff3d(args.ncu_side, PECLET, WIND)
     b = inputs.rhs_ones(A)
     mode = pbcg.EXACT if args.ncu_case == "exact" else pbcg.PLAIN
     with pbcg.Context(0) as ctx:
         M = ctx.upload_csr(A)
         x = np.zeros(A.n)
+        if args.ncu_solve:
+            # the solve a user runs (launch graph, or one cluster launch for a small system), to tol 1e-8
+            res = ctx.solve(M, b, x, 1e-8, args.ncu_iters, args.ncu_alg, mode)
+            print(json.dumps({"case": args.ncu_case, "n": A.n, "iters": res.iters, "status": res.status,
+                              "launches": res.launches}))
+            return 0
         res, prof = ctx.profile_solve(M, b, x, 1e-300, args.ncu_iters, args.ncu_alg, mode)
         print(json.dumps({"case": args.ncu_case, "n": A.n, "iters": res.iters,
                           "kernels": {k: {"launches": c, "avg_us": 1e3 * t / c} for k, (t, c) in prof.items()}}))
@@ -574,7 +585,11 @@ def main():
     ap.add_argument("--ncu-side", type=int, default=N_SIDE)
     ap.add_argument("--ncu-iters", type=int, default=12)
     ap.add_argument("--ncu-alg", type=int, default=1, help="0 BiCGStab, 1 p-BiCGStab, 2 p-BiCGStabRR")
-    ap.add_argument("--ncu-matrix", choices=["convdiff", "powerlaw"], default="convdiff")
+    ap.add_argument("--ncu-matrix", choices=["convdiff", "convdiff2d", "powerlaw"], default="convdiff",
+                    help="3D convection-diffusion (side --ncu-side), 2D (Pe 10), or the power-law matrix")
+    ap.add_argument("--ncu-solve", action="store_true",
+                    help="with --ncu-case: run pbcg_solve to tol 1e-8 with maxit --ncu-iters instead of the "
+                         "host-driven per-kernel solve")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

@@ -121,6 +121,13 @@ int pbcg_mat_free(pbcg_ctx *ctx, pbcg_mat *mat);
  * step converged, BREAKDOWN.  The residual history (res_0 .. res_iters) is
  * kept for pbcg_residual_history.
  *
+ * Reproducibility: exact-mode results are bit-identical whatever the grid,
+ * schedule or batch.  Plain-mode dots sum per-CTA partials; on a matrix whose
+ * 256-row tiles exceed the shared-memory stage (more than 7 stored entries
+ * per row on average, e.g. power-law rows) the passes hand tiles out
+ * dynamically, so plain results there may differ in the last bits from run
+ * to run.
+ *
  * Returns the status (also in out->status) or a negative error.
  */
 int pbcg_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double *x, double tol, int32_t maxit,

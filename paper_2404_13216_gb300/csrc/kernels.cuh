@@ -70,6 +70,7 @@ struct Ctl {
 struct Work {
     GAcc g[MAXD];
     unsigned int ticket;
+    unsigned int tile_next;              // next tile to claim in a pass that schedules tiles dynamically
     int maxgrid;
     double *part;                        // plain partials [MAXD][maxgrid]
 };
@@ -412,8 +413,10 @@ __device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
     if (!sh.last)
         return false;
     merge_finish<ND, MODE>(sh, wk);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         wk->ticket = 0u;
+        wk->tile_next = 0u;          // every CTA has left its tile loop
+    }
     __syncthreads();
     return true;
 }
@@ -976,9 +979,18 @@ struct TilePipe {
 // Every wait is bounded; a warp that gives up raises a flag that stops the
 // others, and before the CTA returns one thread waits (bounded) for copies
 // still in flight.
+//
+// Tiles go to CTAs round-robin (CTA b takes b, b + grid, ...), or, with dyn
+// (a grid-wide counter that the pass's last CTA resets), in claim order: the
+// thread that refills a stage claims the next tile.  A matrix with wide rows
+// keeps its rows sorted by length, so claiming hands out the heaviest tiles
+// first and lets the light ones fill in around them (round-robin leaves the
+// CTA holding the heaviest tile of every round with the most work).  When the
+// counter is exhausted the refilling thread completes the stage's phase with
+// no data and a tile of -1, which ends every warp's loop at that stage.
 template <int NV, bool MATS, class Body>
 __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&src)[NV], int nv, const double *gx,
-                                          Ctl *c, uint8_t *dsm, Body body)
+                                          Ctl *c, uint8_t *dsm, Body body, unsigned int *dyn = nullptr)
 {
     __shared__ uint64_t bar[NSTAGE];
     __shared__ StageInfo info[NSTAGE];
@@ -1003,6 +1015,19 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
                 rec[q] = -1;
         }
     };
+    // dynamic: claim a tile into stage k (or end the stage's sequence)
+    auto claim_issue = [&](int k) {
+        const unsigned int t = atomicAdd(dyn, 1u);
+        if (t < (unsigned int)ntiles) {
+            int rec[TMETA];
+            record((int)t, rec);
+            nissued[k] += 1;
+            P.issue(k, (int)t, rec, A, src, nv, gx, -1);
+        } else {
+            info[k].tile = -1;
+            mbar_arrive(&bar[k]);
+        }
+    };
     if (threadIdx.x == 0) {
         for (int k = 0; k < NSTAGE; k++) {
             mbar_init(&bar[k], 1);
@@ -1012,16 +1037,20 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
         tmo = 0;
         fence_mbar_init();
         fence_async_shared();
-        for (int k = 0; k < NSTAGE && k < my; k++) {
-            int rec[TMETA];
-            record(tile_of(k), rec);
-            nissued[k] += 1;
-            P.issue(k, tile_of(k), rec, A, src, nv, gx, recs ? tile_of(k + NSTAGE) : -1);
+        for (int k = 0; k < NSTAGE; k++) {
+            if (dyn) {
+                claim_issue(k);
+            } else if (k < my) {
+                int rec[TMETA];
+                record(tile_of(k), rec);
+                nissued[k] += 1;
+                P.issue(k, tile_of(k), rec, A, src, nv, gx, recs ? tile_of(k + NSTAGE) : -1);
+            }
         }
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = 0; j < my; j++) {
+    for (int j = 0; dyn != nullptr || j < my; j++) {
         const int k = j % NSTAGE;
         const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[k], (uint32_t)(j / NSTAGE) & 1u));
         if (!ok || *(volatile int *)&tmo) {
@@ -1029,7 +1058,10 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
                 tmo = 1;
             break;
         }
-        body(P, k, tile_of(j), warp, lane);
+        const int tile = dyn ? *(volatile int *)&info[k].tile : tile_of(j);
+        if (tile < 0)
+            break;                                // dynamic: no tiles left (the same for every warp)
+        body(P, k, tile, warp, lane);
         __syncwarp();
         if (lane == 0) {
             __threadfence_block();
@@ -1037,19 +1069,23 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
                 // last warp out of this stage: every warp has read it
                 __threadfence_block();
                 done_cnt[k] = 0;
-                const int jn = j + NSTAGE;
-                if (jn < my) {
-                    int rec[TMETA];
-                    if (recs) {
-                        const int *m = P.meta(k);
+                if (dyn) {
+                    claim_issue(k);
+                } else {
+                    const int jn = j + NSTAGE;
+                    if (jn < my) {
+                        int rec[TMETA];
+                        if (recs) {
+                            const int *m = P.meta(k);
 #pragma unroll
-                        for (int q = 0; q < TMETA; q++)
-                            rec[q] = m[q];
-                    } else {
-                        record(tile_of(jn), rec);
+                            for (int q = 0; q < TMETA; q++)
+                                rec[q] = m[q];
+                        } else {
+                            record(tile_of(jn), rec);
+                        }
+                        nissued[k] += 1;
+                        P.issue(k, tile_of(jn), rec, A, src, nv, gx, recs ? tile_of(jn + NSTAGE) : -1);
                     }
-                    nissued[k] += 1;
-                    P.issue(k, tile_of(jn), rec, A, src, nv, gx, recs ? tile_of(jn + NSTAGE) : -1);
                 }
             }
         }
@@ -1210,7 +1246,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         D.template add2<true>(sh, 1, y, y, dy, dy, act);
         D.template add2<false>(sh, 2, r0i, si, dr, ds, act);
         D.template add2<false>(sh, 3, r0i, zi, dr, dz, act);
-    });
+    }, MATS ? nullptr : &wk->tile_next);
     if (!finalize<4, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1255,7 +1291,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
         D.template add_row<3, false, false, true>(sh, act, r0i, rn, dr0, dr, r0i, wn, dr0, dw, rn, rn, &dr, &dr);
-    });
+    }, MATS ? nullptr : &wk->tile_next);
     if (!finalize<3, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1359,7 +1395,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dr = decode(r0i), ds = decode(si);
         D.template add2<false>(sh, 0, r0i, si, dr, ds, act);
-    });
+    }, MATS ? nullptr : &wk->tile_next);
     if (!finalize<1, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1395,7 +1431,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dq = decode(qi), dy = decode(yi);
         D.template add_row<2, false, true>(sh, act, qi, yi, dq, dy, yi, yi, dy, dy);
-    });
+    }, MATS ? nullptr : &wk->tile_next);
     if (!finalize<2, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)

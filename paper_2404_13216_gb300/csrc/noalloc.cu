@@ -52,6 +52,7 @@ __global__ void k_noalloc_init(unsigned char *base)
     }
     if (threadIdx.x == 0) {
         wk->ticket = 0u;
+        wk->tile_next = 0u;
         wk->maxgrid = NOALLOC_MAXGRID;
         wk->part = reinterpret_cast<double *>(base + NOALLOC_PART_OFF);
     }

@@ -179,9 +179,18 @@ def test_golden_fixture_exact(ctx):
 
 
 # --------------------------------------------------------------------------- edge cases
+@pytest.fixture(params=[1, 0], ids=["cluster", "passes"])
+def small_path(ctx, request):
+    """Small systems run as one cluster launch by default; 0 keeps the passes."""
+    from paper_2404_13216_gb300 import pbcg
+    ctx.set_option(pbcg.OPT_SMALL_CLUSTER, request.param)
+    yield request.param
+    ctx.set_option(pbcg.OPT_SMALL_CLUSTER, 1)
+
+
 @pytest.mark.parametrize("alg", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_edge_cases(ctx, orc, alg, mode):
+def test_edge_cases(ctx, orc, alg, mode, small_path):
     # one unknown
     A = inputs.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]))
     ref, res, x, hist = run_both(ctx, orc, A, np.array([6.0]), 1e-12, 10, alg, mode)
@@ -277,7 +286,9 @@ def test_powerlaw_exact_bitwise(ctx, orc, alg):
 
 def test_mixed_window_tiles_exact_bitwise(ctx, orc):
     """A stencil matrix with a few long random rows: some tiles gather from
-    staged blocks, others from global memory, in the same pass."""
+    staged blocks, others from global memory, in the same pass (the passes are
+    forced: 8000 rows would otherwise run as one cluster launch)."""
+    from paper_2404_13216_gb300 import pbcg
     A = inputs.convdiff3d(20, 30.0)
     rng = np.random.default_rng(9)
     rows = []
@@ -299,7 +310,11 @@ def test_mixed_window_tiles_exact_bitwise(ctx, orc):
     B = inputs.CSR(A.n, rp, np.concatenate([c for c, _ in rows]).astype(np.int32),
                    np.concatenate([v for _, v in rows]))
     b = inputs.rhs_ones(B)
-    ref, res, x, hist = run_both(ctx, orc, B, b, 1e-10, 600, 1, 1)
+    ctx.set_option(pbcg.OPT_SMALL_CLUSTER, 0)
+    try:
+        ref, res, x, hist = run_both(ctx, orc, B, b, 1e-10, 600, 1, 1)
+    finally:
+        ctx.set_option(pbcg.OPT_SMALL_CLUSTER, 1)
     assert res.status == ref.status and res.iters == ref.iters
     assert same(hist, ref.history) and same(x, ref.x)
 
