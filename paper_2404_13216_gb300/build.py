@@ -62,7 +62,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([_nvcc(), ARCH, "-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    r = subprocess.run([_nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-ldl"], capture_output=True, text=True)
     for o in objs:
         os.remove(o)
     if r.returncode != 0:

@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
 #include "../../include/pbcg.h"
 #include "batched.cuh"
 #include "cluster.cuh"
@@ -52,6 +53,15 @@ struct Workspace {
 };
 
 }  // namespace
+
+// NVTX range around a public call or a host-driven launch (a no-op unless a
+// profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct pbcg_mat {
     int n;
@@ -615,6 +625,7 @@ struct Launcher {
 
     int go(const char *name, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work, size_t smem = 0)
     {
+        NvtxRange trace(name);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (prof) {
             CK(cudaEventCreate(&e0));
@@ -1910,6 +1921,7 @@ int pbcg_mat_free(pbcg_ctx *ctx, pbcg_mat *m)
 int pbcg_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double *x, double tol, int32_t maxit, int alg,
                int dot_mode, pbcg_result *out)
 {
+    NvtxRange trace("pbcg_solve");
     return solve_impl(ctx, A, b, x, tol, maxit, alg, dot_mode, out, nullptr);
 }
 
@@ -1917,6 +1929,7 @@ int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double
                        int alg, int dot_mode, pbcg_result *out, char (*names)[32], double *ms, int32_t *launches,
                        int32_t cap, int32_t *count)
 {
+    NvtxRange trace("pbcg_profile_solve");
     Prof prof;
     int rc = solve_impl(ctx, A, b, x, tol, maxit, alg, dot_mode, out, &prof);
     if (rc < 0)
@@ -2058,6 +2071,7 @@ int pbcg_spmv(pbcg_ctx *ctx, const pbcg_mat *m, const double *x, double *y)
 int pbcg_solve_batched(pbcg_ctx *ctx, const pbcg_mat *A, int32_t nsys, const int32_t *sys_row_ptr, const double *b,
                        double *x, const double *tol, int32_t maxit, int alg, int dot_mode, pbcg_result *out)
 {
+    NvtxRange trace("pbcg_solve_batched");
     return solve_batched_impl(ctx, A, nsys, sys_row_ptr, b, x, tol, maxit, alg, dot_mode, out);
 }
 
@@ -2195,6 +2209,7 @@ void pbcg_pool_destroy(pbcg_pool *P)
 int pbcg_pool_admit(pbcg_pool *P, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                     const double *vals, const double *b, const double *x0, double tol, int32_t maxit, int32_t *slot)
 {
+    NvtxRange trace("pbcg_pool_admit");
     if (!P)
         return PBCG_ERR_INVALID;
     pbcg_ctx *ctx = P->ctx;
@@ -2331,6 +2346,7 @@ int pbcg_pool_admit(pbcg_pool *P, int32_t n, int64_t nnz, const int32_t *row_ptr
 
 int pbcg_pool_step(pbcg_pool *P, int32_t iters)
 {
+    NvtxRange trace("pbcg_pool_step");
     if (!P)
         return PBCG_ERR_INVALID;
     pbcg_ctx *ctx = P->ctx;
