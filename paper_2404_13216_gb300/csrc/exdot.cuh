@@ -44,9 +44,7 @@ constexpr int WIN_UNSET = -(1 << 24);   // anchor of an empty window: every term
 // ---------------------------------------------------------------------------
 struct Prod {
     uint32_t w0, w1, w2, w3;     // |a*b| mantissa product (< 2^106)
-    int off;                     // bit offset of its LSB above 2^-2148, or -1 for a zero product
     uint32_t neg;                // 1 if a*b < 0
-    bool nonfinite;              // an operand is Inf or NaN
 };
 
 // ---------------------------------------------------------------------------
@@ -198,7 +196,8 @@ __device__ __forceinline__ Dec decode(double a)
     return d;
 }
 
-// exact product of two decoded operands (|a*b| words, sign, LSB offset)
+// exact product of two decoded operands (|a*b| words and sign; its LSB lies
+// a.e + b.e - 2 bits above 2^-2148)
 template <bool SQUARE>
 __device__ __forceinline__ Prod dec_product(const Dec &a, const Dec &b)
 {
@@ -217,8 +216,6 @@ __device__ __forceinline__ Prod dec_product(const Dec &a, const Dec &b)
     p.w2 = (uint32_t)h;
     p.w3 = (uint32_t)(h >> 32);
     p.neg = SQUARE ? 0u : (a.s ^ b.s);
-    p.off = a.e + b.e - 2;
-    p.nonfinite = false;
     return p;
 }
 
