@@ -300,6 +300,19 @@ int pbcg_dot(pbcg_ctx *ctx, int64_t n, const double *a, const double *b, int dot
 int pbcg_spmv(pbcg_ctx *ctx, const pbcg_mat *A, const double *x, double *y);
 
 /*
+ * Failure-detection check of the bounded device wait the staged passes use
+ * on their shared-memory barriers: one CTA waits, with the passes' wait
+ * function limited to `probes` attempts (1 .. 2^22; the passes use 2^18,
+ * about one second on GB300), on
+ * a barrier phase that nothing completes.  *expired receives 1 when the wait
+ * gave up and reported it (the expected outcome; a pass then ends its solve
+ * with PBCG_ERR_TIMEOUT), 0 if the phase completed; *seconds the time the
+ * wait took, measured on the device.  The context stays usable.  Returns 0,
+ * INVALID for a bad argument, or CUDA.
+ */
+int pbcg_check_wait(pbcg_ctx *ctx, int32_t probes, int32_t *expired, double *seconds);
+
+/*
  * Time the solver's kernels: run the solve of pbcg_solve with a host-driven
  * launch loop (no CUDA graph) and CUDA events around every launch, on the
  * context's stream.  names receives up to cap kernel names (a

@@ -2043,6 +2043,37 @@ int pbcg_dot(pbcg_ctx *ctx, int64_t n, const double *a, const double *b, int dot
     return 0;
 }
 
+int pbcg_check_wait(pbcg_ctx *ctx, int32_t probes, int32_t *expired, double *seconds)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (probes < 1 || (unsigned)probes > MBAR_CHECK_MAX || !expired || !seconds)
+        return fail(ctx, PBCG_ERR_INVALID, "pbcg_check_wait: probes must be in 1 .. 2^22 and outputs non-NULL");
+    CK(cudaSetDevice(ctx->device));
+    unsigned *d = nullptr;
+    CK(cudaMalloc(&d, 3 * sizeof(unsigned)));
+    unsigned h[3] = {0u, 0u, 0u};
+    cudaError_t e = cudaMemsetAsync(d, 0, 3 * sizeof(unsigned), ctx->stream);
+    if (e == cudaSuccess) {
+        unsigned pr = (unsigned)probes;
+        void *args[2] = {&pr, &d};
+        e = cudaLaunchKernel((void *)k_check_wait, dim3(1), dim3(32), args, 0, ctx->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return fail(ctx, PBCG_ERR_CUDA, "pbcg_check_wait: %s", cudaGetErrorString(e));
+    int clk = 0;
+    cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, ctx->device);     // kHz
+    const unsigned long long cyc = ((unsigned long long)h[2] << 32) | h[1];
+    *expired = (int32_t)h[0];
+    *seconds = clk > 0 ? (double)cyc / ((double)clk * 1e3) : 0.0;
+    return 0;
+}
+
 int pbcg_spmv(pbcg_ctx *ctx, const pbcg_mat *m, const double *x, double *y)
 {
     if (!ctx)

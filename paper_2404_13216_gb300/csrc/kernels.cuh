@@ -1142,6 +1142,27 @@ static __device__ void pipe_y_tail(Ctl *c, const double *dv)
     set_cond(c);
 }
 
+// The bounded barrier wait of the tile loop on a phase that nothing
+// completes (failure-detection check): out[0] = 1 when it gave up, out[1..2]
+// the clock64 cycles it took (low, high words).  One CTA of one warp.
+static __global__ void __launch_bounds__(32) k_check_wait(unsigned probes, unsigned *out)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const long long t0 = clock64();
+    const bool done = mbar_wait_bounded(&bar, 0u, probes);
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) {
+        out[0] = done ? 0u : 1u;
+        out[1] = (unsigned)(unsigned long long)(t1 - t0);
+        out[2] = (unsigned)((unsigned long long)(t1 - t0) >> 32);
+    }
+}
+
 // Row arithmetic of the p-BiCGStab passes (Algorithm 2), shared by the
 // single-system and batched passes so that both round identically.
 // Pass X: p, s, z (bit copies of r, w, t at i = 0; kept as they are right

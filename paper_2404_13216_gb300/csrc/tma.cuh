@@ -24,7 +24,8 @@ constexpr int MCAP = TILE_ROWS * 7;            // staged SELL entries per tile (
 constexpr int SLOFF_STAGE = 16;                // slice offsets copied per tile (needs 9)
 constexpr int GMAX = 6;                        // 256-row blocks of the gathered vector staged per tile
 constexpr int TMETA = 8;                       // ints per tile record: first entry, end entry, GMAX blocks
-constexpr unsigned MBAR_SPIN_LIMIT = 1u << 22;
+constexpr unsigned MBAR_SPIN_LIMIT = 1u << 18;   // about 1 s of probes on GB300 (3.8 us each)
+constexpr unsigned MBAR_CHECK_MAX = 1u << 22;    // largest limit pbcg_check_wait accepts
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -62,9 +63,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // bounded wait: true when the phase completed, false after the spin limit
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned limit = MBAR_SPIN_LIMIT)
 {
-    for (unsigned i = 0; i < MBAR_SPIN_LIMIT; i++)
+    for (unsigned i = 0; i < limit; i++)
         if (mbar_try_wait(bar, parity))
             return true;
     return false;

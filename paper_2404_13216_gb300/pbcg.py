@@ -27,7 +27,7 @@ EXPORTS = ("pbcg_create", "pbcg_destroy", "pbcg_last_error", "pbcg_csr_upload", 
            "pbcg_solve", "pbcg_solve_batched", "pbcg_residual_history", "pbcg_dot", "pbcg_spmv",
            "pbcg_profile_solve", "pbcg_dot_noalloc", "pbcg_set_option", "pbcg_pool_create", "pbcg_pool_destroy",
            "pbcg_pool_admit", "pbcg_pool_step", "pbcg_pool_poll", "pbcg_pool_result", "pbcg_pool_history",
-           "pbcg_pool_room")
+           "pbcg_pool_room", "pbcg_check_wait")
 
 
 class PbcgError(RuntimeError):
@@ -74,6 +74,8 @@ def load_library(path: str = LIB_PATH):
     lib.pbcg_dot.restype = ctypes.c_int
     lib.pbcg_spmv.argtypes = [P, P, P, P]
     lib.pbcg_spmv.restype = ctypes.c_int
+    lib.pbcg_check_wait.argtypes = [P, i32, ctypes.POINTER(i32), ctypes.POINTER(d)]
+    lib.pbcg_check_wait.restype = ctypes.c_int
     lib.pbcg_profile_solve.argtypes = [P, P, P, P, d, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result),
                                        P, P, P, i32, ctypes.POINTER(i32)]
     lib.pbcg_profile_solve.restype = ctypes.c_int
@@ -228,6 +230,12 @@ class Context:
         out = ctypes.c_double(0.0)
         self._check(_lib.pbcg_dot(self.handle, n, _ptr(a), _ptr(b), int(mode), ctypes.byref(out)))
         return out.value
+
+    def check_wait(self, probes: int):
+        """Run the bounded device wait on a phase nothing completes; returns (expired, seconds)."""
+        exp, sec = ctypes.c_int32(0), ctypes.c_double(0.0)
+        self._check(_lib.pbcg_check_wait(self.handle, int(probes), ctypes.byref(exp), ctypes.byref(sec)))
+        return bool(exp.value), sec.value
 
     def spmv(self, mat: Matrix, x, y=None):
         x = _host(x, np.float64)
