@@ -555,6 +555,19 @@ def run_ncu_case(args):
     from paper_2404_13216_gb300 import build, inputs
     build.build_library()
     from paper_2404_13216_gb300 import pbcg
+    if args.ncu_matrix == "batched":
+        # the 512-system batch, one batched solve of --ncu-iters iterations
+        B = inputs.batched_convdiff(nsys=512, seed=4)
+        b = inputs.rhs_ones(B.A)
+        mode = pbcg.EXACT if args.ncu_case == "exact" else pbcg.PLAIN
+        with pbcg.Context(0) as ctx:
+            M = ctx.upload_csr(B.A)
+            x = np.zeros(B.A.n)
+            res = ctx.solve_batched(M, B.sys_row_ptr, b, x, np.full(512, 1e-300), args.ncu_iters,
+                                    args.ncu_alg, mode)
+            print(json.dumps({"case": args.ncu_case, "systems": 512, "n": B.A.n,
+                              "iters_max": max(r.iters for r in res)}))
+        return 0
     if args.ncu_matrix == "powerlaw":
         A = inputs.powerlaw()
     elif args.ncu_matrix == "convdiff2d":
@@ -585,8 +598,9 @@ def main():
     ap.add_argument("--ncu-side", type=int, default=N_SIDE)
     ap.add_argument("--ncu-iters", type=int, default=12)
     ap.add_argument("--ncu-alg", type=int, default=1, help="0 BiCGStab, 1 p-BiCGStab, 2 p-BiCGStabRR")
-    ap.add_argument("--ncu-matrix", choices=["convdiff", "convdiff2d", "powerlaw"], default="convdiff",
-                    help="3D convection-diffusion (side --ncu-side), 2D (Pe 10), or the power-law matrix")
+    ap.add_argument("--ncu-matrix", choices=["convdiff", "convdiff2d", "powerlaw", "batched"], default="convdiff",
+                    help="3D convection-diffusion (side --ncu-side), 2D (Pe 10), the power-law matrix, or the "
+                         "512-system batch (one batched solve)")
     ap.add_argument("--ncu-solve", action="store_true",
                     help="with --ncu-case: run pbcg_solve to tol 1e-8 with maxit --ncu-iters instead of the "
                          "host-driven per-kernel solve")
