@@ -284,9 +284,15 @@ int pbcg_pool_room(const pbcg_pool *pool, int32_t *free_slots, int64_t *free_row
  *     it uses the launch graph of passes whatever the size.  Exact-mode
  *     results are bit-identical either way; plain-mode dots sum their
  *     partials over fewer CTAs.  pbcg_profile_solve always runs the passes.
+ *   PBCG_OPT_BATCH_GRAPH: 1 (default) or 0.  With 0, pbcg_solve_batched
+ *     launches every kernel of its iteration loop from the host and reads
+ *     the control kernel's "any system live" flag after each iteration,
+ *     instead of one CUDA-graph launch with a conditional WHILE node; results
+ *     are identical.  For profilers, which do not profile single kernels of a
+ *     graph with conditional nodes.
  * Returns 0, or INVALID for an unknown option or value.
  */
-enum { PBCG_OPT_RR_PERIOD = 1, PBCG_OPT_PRECOND = 3, PBCG_OPT_SMALL_CLUSTER = 4 };
+enum { PBCG_OPT_RR_PERIOD = 1, PBCG_OPT_PRECOND = 3, PBCG_OPT_SMALL_CLUSTER = 4, PBCG_OPT_BATCH_GRAPH = 5 };
 enum { PBCG_PRECOND_NONE = 0, PBCG_PRECOND_JACOBI = 1 };
 int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value);
 

@@ -112,6 +112,7 @@ struct pbcg_ctx {
     int rr_period = 50;                // residual replacement period of PBCG_ALG_PIPELINED_RR
     int precond = PBCG_PRECOND_NONE;   // preconditioner of pbcg_solve
     int small_cluster = 1;             // Algorithm 2 on small systems as one cluster launch
+    int batch_graph = 1;               // batched solves loop in a CUDA graph (0: host-driven launches)
     std::map<long long, bool> cl_ok;   // cluster shapes (kernel, CTAs, shared memory) that can be resident
     // batched solves
     struct {
@@ -1381,7 +1382,25 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
     }
     // the loop: WHILE(some system running or awaiting its check) { true-res, passes, control }
     std::vector<BKernel> body = mode ? batch_body<1>(alg) : batch_body<0>(alg);
-    if (!(BW.exec && BW.g_layout == (const void *)L && BW.g_alg == alg && BW.g_mode == mode)) {
+    if (!ctx->batch_graph) {
+        // host-driven loop, one kernel launch at a time (for profilers), ending
+        // when the control kernel reports no live system; bounded by maxit + 4
+        // bodies (every system stops at maxit)
+        int any = 1;
+        for (long long it = 0; any && it <= (long long)maxit + 4; it++) {
+            for (auto &bk : body) {
+                void *args[3] = {&A, &V, &B};
+                CK(cudaLaunchKernel(bk.fn, dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem)), dim3(THREADS), args,
+                                    bk.smem, ctx->stream));
+            }
+            unsigned long long hv = 0ull;
+            int zero = 0;
+            void *cargs[3] = {&B, &hv, &zero};
+            CK(cudaLaunchKernel((void *)k_batch_ctl, dim3(1), dim3(1024), cargs, 0, ctx->stream));
+            CK(cudaMemcpyAsync(&any, B.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    } else if (!(BW.exec && BW.g_layout == (const void *)L && BW.g_alg == alg && BW.g_mode == mode)) {
         free_batch_graph(ctx);
         CK(cudaGraphCreate(&BW.graph, 0));
         cudaGraphConditionalHandle h;
@@ -1422,7 +1441,8 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         BW.g_alg = alg;
         BW.g_mode = mode;
     }
-    CK(cudaGraphLaunch(BW.exec, ctx->stream));
+    if (ctx->batch_graph)
+        CK(cudaGraphLaunch(BW.exec, ctx->stream));
     // final true residual of every system, then results
     if ((rc = blaunch(ctx, (void *)k_batched<1, StepTrueRes<true>>, A, V, B)))
         return rc;
@@ -1958,6 +1978,12 @@ int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value)
         if (value < 1 || value > INT32_MAX)
             return fail(ctx, PBCG_ERR_INVALID, "residual replacement period must be >= 1");
         ctx->rr_period = (int)value;
+        return 0;
+    }
+    if (option == PBCG_OPT_BATCH_GRAPH) {
+        if (value != 0 && value != 1)
+            return fail(ctx, PBCG_ERR_INVALID, "PBCG_OPT_BATCH_GRAPH takes 0 or 1");
+        ctx->batch_graph = (int)value;
         return 0;
     }
     if (option == PBCG_OPT_SMALL_CLUSTER) {

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpbcg.so")
 OK, MAXIT, BREAKDOWN, NONFINITE = 0, 1, 2, 3
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = -1, -2, -3, -4
 BICGSTAB, PIPELINED, PIPELINED_RR = 0, 1, 2
-OPT_RR_PERIOD, OPT_PRECOND, OPT_SMALL_CLUSTER = 1, 3, 4
+OPT_RR_PERIOD, OPT_PRECOND, OPT_SMALL_CLUSTER, OPT_BATCH_GRAPH = 1, 3, 4, 5
 PRECOND_NONE, PRECOND_JACOBI = 0, 1
 PLAIN, EXACT = 0, 1
 

@@ -146,3 +146,28 @@ def test_batched_residual_replacement_bitwise(ctx, orc):
         assert same(ctx.history(k), ref.history) and same(x[r0:r1], ref.x), k
     M.free()
     ctx.set_option(pbcg.OPT_RR_PERIOD, 50)
+
+
+@pytest.mark.parametrize("alg", [0, 1, 2], ids=["bicgstab", "pbicgstab", "pbicgstab_rr"])
+def test_batched_host_loop_equals_graph(ctx, alg):
+    """PBCG_OPT_BATCH_GRAPH = 0 (host-driven launches, for profilers) gives the
+    graph loop's results bit for bit, statuses and iteration counts included."""
+    from paper_2404_13216_gb300 import pbcg
+    systems, A, srp, b = small_batch(seed=11, nsys=7)
+    tol = np.full(len(systems), 1e-10)
+    M = ctx.upload_csr(A)
+    out = []
+    for graph in (1, 0):
+        ctx.set_option(pbcg.OPT_BATCH_GRAPH, graph)
+        try:
+            x = np.zeros(A.n)
+            res = ctx.solve_batched(M, srp, b, x, tol, 400, alg, 1)
+            hist = [ctx.history(k) for k in range(len(systems))]
+        finally:
+            ctx.set_option(pbcg.OPT_BATCH_GRAPH, 1)
+        out.append((res, x, hist))
+    (rg, xg, hg), (rh, xh, hh) = out
+    assert [(r.status, r.iters) for r in rg] == [(r.status, r.iters) for r in rh]
+    assert same(xg, xh)
+    assert all(same(a, b_) for a, b_ in zip(hg, hh))
+    M.free()
