@@ -56,6 +56,32 @@ def test_exact_dot_large_random(ctx, orc):
         assert same([ctx.dot(a, b, 1)], [orc.dot_exact(a, b, nthreads=8)]), n
 
 
+def test_exact_dot_random_sweep(ctx, orc):
+    """120 seeded cases: random lengths (ragged against warps and tiles), exponent
+    spans from narrow to the whole double range (subnormals included), signs,
+    exact zeros, and planted cancellation; every result bit-identical."""
+    rng = np.random.default_rng(2024)
+    for case in range(120):
+        n = int(rng.integers(1, 5000))
+        lo = int(rng.integers(-1074, 900))
+        hi = int(min(1000, lo + rng.integers(0, 2000)))
+        ea = rng.integers(lo, hi + 1, n) // 2
+        eb = rng.integers(lo, hi + 1, n) - ea
+        a = np.ldexp(rng.uniform(0.5, 1.0, n), ea) * rng.choice([-1.0, 1.0], n)
+        b = np.ldexp(rng.uniform(0.5, 1.0, n), np.clip(eb, -1074, 1000)) * rng.choice([-1.0, 1.0], n)
+        a[rng.random(n) < 0.05] = 0.0
+        if case % 3 == 0 and n > 1:                  # cancel half of the terms exactly
+            h = n // 2
+            a[h:2 * h] = -a[:h]
+            b[h:2 * h] = b[:h]
+        want = orc.dot_exact(a, b, nthreads=4)
+        got = ctx.dot(a, b, 1)
+        if math.isnan(want):
+            assert math.isnan(got), case
+        else:
+            assert same([got], [want]) or (got == 0.0 and want == 0.0), (case, n, lo, hi, got, want)
+
+
 def test_exact_dot_empty_and_nonfinite(ctx):
     assert ctx.dot(np.zeros(0), np.zeros(0), 1) == 0.0
     a = np.ones(100)
