@@ -299,6 +299,27 @@ def test_full_size_128cubed_first_iterations(ctx, orc):
     assert np.all(rel <= 4 * spread + 1e-13), (rel.max(), spread.max())
 
 
+def test_full_size_128cubed_benchmark_solve(ctx, orc):
+    """The benchmark's whole solve: 128^3, exact p-BiCGStab, tol 1e-10, maxit
+    1000, in the launch graph the benchmark times.  All 1001 residual-history
+    entries, the iteration count, the status, the true residual and x
+    bit-identical to the oracle (about a minute of oracle time on 16 cores)."""
+    import os
+    A = inputs.convdiff3d(128, 50.0)
+    b = inputs.rhs_ones(A)
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=1000, alg=1, mode=1,
+                    nthreads=max(1, min(16, os.cpu_count() or 1)))
+    M = ctx.upload_csr(A)
+    x = np.zeros(A.n)
+    res = ctx.solve(M, b, x, 1e-10, 1000, 1, 1)
+    hist = ctx.history()
+    M.free()
+    assert res.status == ref.status and res.iters == ref.iters, (res, ref.status, ref.iters)
+    assert hist.size == ref.history.size and same(hist, ref.history)
+    assert same(x, ref.x)
+    assert same([res.relres_true], [ref.relres_true])
+
+
 @pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
 def test_powerlaw_exact_bitwise(ctx, orc, alg):
     """Random power-law rows (the rows are sorted by length inside the library
