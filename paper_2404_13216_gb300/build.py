@@ -60,6 +60,9 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
         elif verbose:
             sys.stderr.write(err)
     if errs:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([_nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-ldl"], capture_output=True, text=True)
