@@ -136,3 +136,27 @@ def test_cluster_option_validation(ctx):
         ctx.set_option(pbcg.OPT_SMALL_CLUSTER, 2)
     ctx.set_option(pbcg.OPT_SMALL_CLUSTER, 0)
     ctx.set_option(pbcg.OPT_SMALL_CLUSTER, 1)
+
+
+@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
+def test_cluster_nonzero_x0_and_ragged_sizes(ctx, orc, alg):
+    """A nonzero initial guess, and sizes one row past a CTA's share (4097 rows:
+    2 rows per thread over 9 CTAs) and a prime (3001 rows)."""
+    for n_target, seed in ((4097, 1), (3001, 2)):
+        base = inputs.convdiff2d(int(np.ceil(np.sqrt(n_target))), 25.0)
+        # keep the leading n_target rows and columns (a principal block stays nonsingular: diagonally dominant)
+        m = n_target
+        rp, ci, va = [0], [], []
+        for i in range(m):
+            for k in range(base.row_ptr[i], base.row_ptr[i + 1]):
+                if base.col_idx[k] < m:
+                    ci.append(int(base.col_idx[k]))
+                    va.append(float(base.vals[k]))
+            rp.append(len(ci))
+        A = inputs.CSR(m, np.array(rp, np.int32), np.array(ci, np.int32), np.array(va))
+        b = inputs.rhs_ones(A)
+        x0 = np.random.default_rng(seed).standard_normal(m)
+        ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, x0=x0, tol=1e-10, maxit=800, alg=alg, mode=1, nthreads=8)
+        r, x, h = solve(ctx, A, b, 1e-10, 800, 1, True, x0=x0, alg=alg)
+        assert r.status == ref.status and r.iters == ref.iters, (n_target, r, ref.status, ref.iters)
+        assert same(h, ref.history) and same(x, ref.x), n_target
