@@ -47,6 +47,27 @@ constexpr int WARPS = THREADS / 32;
 constexpr int MAXD = 4;                 // most dots merged in one pass
 constexpr int UNR = PBCG_UNR;
 
+// streamed matrix entries: read once, so they go first when L2 needs room
+// (the gathered vector, reused across rows, stays)
+__device__ __forceinline__ unsigned long long l2_evict_first_policy()
+{
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int ld_stream(const int *a, unsigned long long pol)
+{
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_stream(const double *a, unsigned long long pol)
+{
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
 enum : int { ST_RUNNING = 100, ST_CANDIDATE = 101, ST_SETUP1 = 110, ST_SETUP2 = 111, ST_FREE = 120, ST_INVALID = 130, ST_TIMEOUT = 200 };
 enum : int { PH_SETUP = 0, PH_ITER = 1 };
 enum : int { ALG_BICGSTAB = 0, ALG_PIPELINED = 1 };
@@ -909,14 +930,25 @@ struct TilePipe {
             }
             return acc;
         }
+        const unsigned long long pol = l2_evict_first_policy();
         for (int j0 = 0; j0 < width; j0 += UNR) {
             int c[UNR];
             double v[UNR], xv[UNR];
+            if (st) {                                  // warp-uniform: entries in shared memory
 #pragma unroll
-            for (int j = 0; j < UNR; j++) {
-                if (j0 + j < len) {
-                    c[j] = cp[(j0 + j) * 32];
-                    v[j] = vp[(j0 + j) * 32];
+                for (int j = 0; j < UNR; j++) {
+                    if (j0 + j < len) {
+                        c[j] = cp[(j0 + j) * 32];
+                        v[j] = vp[(j0 + j) * 32];
+                    }
+                }
+            } else {                                   // entries in global memory, streamed
+#pragma unroll
+                for (int j = 0; j < UNR; j++) {
+                    if (j0 + j < len) {
+                        c[j] = ld_stream(cp + (j0 + j) * 32, pol);
+                        v[j] = ld_stream(vp + (j0 + j) * 32, pol);
+                    }
                 }
             }
 #pragma unroll
@@ -944,14 +976,25 @@ struct TilePipe {
         const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
         const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
         double acc = 0.0;
+        const unsigned long long pol = l2_evict_first_policy();
         for (int j0 = 0; j0 < width; j0 += UNR) {
             int c[UNR];
             double v[UNR], xs[UNR], xr[UNR];
+            if (st) {                                  // warp-uniform: entries in shared memory
 #pragma unroll
-            for (int j = 0; j < UNR; j++) {
-                if (j0 + j < len) {
-                    c[j] = cp[(j0 + j) * 32];
-                    v[j] = vp[(j0 + j) * 32];
+                for (int j = 0; j < UNR; j++) {
+                    if (j0 + j < len) {
+                        c[j] = cp[(j0 + j) * 32];
+                        v[j] = vp[(j0 + j) * 32];
+                    }
+                }
+            } else {                                   // entries in global memory, streamed
+#pragma unroll
+                for (int j = 0; j < UNR; j++) {
+                    if (j0 + j < len) {
+                        c[j] = ld_stream(cp + (j0 + j) * 32, pol);
+                        v[j] = ld_stream(vp + (j0 + j) * 32, pol);
+                    }
                 }
             }
 #pragma unroll
