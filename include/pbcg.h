@@ -185,13 +185,17 @@ typedef struct {
     int32_t dot_mode;          /* PBCG_DOT_*, for every system of the pool */
     int64_t max_request_rows;  /* largest n of one request */
     int64_t max_request_nnz;   /* largest nnz of one request (sizes the upload staging) */
+    int32_t precond;           /* PBCG_PRECOND_NONE or PBCG_PRECOND_JACOBI, for every system of the pool */
+    int32_t reserved;          /* 0 */
 } pbcg_pool_config;
 
 /*
  * Create a pool on ctx's device.  Device memory: about 8 * (13 * max_rows +
  * 1.5 * max_entries + max_slots * (maxit + 1)) + 12 * max_request_nnz bytes.
- * Errors: INVALID (NULL, non-positive or too large sizes, unknown alg or
- * dot_mode), OOM, CUDA.  A pool must be destroyed before its context.
+ * Errors: INVALID (NULL, non-positive or too large sizes, unknown alg,
+ * dot_mode or precond, reserved not 0), OOM, CUDA.  A pool must be destroyed
+ * before its context.  With precond = PBCG_PRECOND_JACOBI it holds 8 *
+ * max_rows more bytes (the diagonals).
  */
 int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out);
 
@@ -205,7 +209,12 @@ void pbcg_pool_destroy(pbcg_pool *pool);
  * the following pbcg_pool_step calls.  The caller's arrays are consumed when
  * the call returns.  Host work: O(n) on the row pointers; the column indices
  * are checked on the device, and a request with an index outside [0, n)
- * finishes at once with PBCG_ERR_INVALID as its result.
+ * finishes at once with PBCG_ERR_INVALID as its result.  In a pool created
+ * with precond = PBCG_PRECOND_JACOBI the request runs on A M^-1 y = b, M =
+ * diag(A), with the fixed forms of pbcg_solve (d_i summed in stored order,
+ * entries v / d_col, y0 = x0 * d, x = y / d in pbcg_pool_result); a row
+ * whose diagonal is absent, zero or non-finite also ends it with
+ * PBCG_ERR_INVALID.
  * Returns 0 and the slot in *slot, 1 when the pool has no room for it now
  * (no free slot, tile range or entry range; *slot = -1), or an error
  * (INVALID: NULL pointer, n or nnz beyond the pool's request limits, bad
@@ -275,7 +284,8 @@ int pbcg_pool_room(const pbcg_pool *pool, int32_t *free_slots, int64_t *free_row
  *     non-finite or absent: INVALID); entries v / d_col (one IEEE division);
  *     y0 = x0 * d; x = y / d.  Residual histories and relres_* are those of
  *     the scaled system.  pbcg_solve_batched applies it to every system (a
- *     block-diagonal M); pools do not (their systems run unpreconditioned).
+ *     block-diagonal M); a pool applies it when its pbcg_pool_config asks
+ *     for it (the option does not reach pools).
  *   PBCG_OPT_SMALL_CLUSTER: 1 (default) or 0.  With 1, pbcg_solve runs the
  *     iterations of Algorithm 1 or 2 (not PBCG_ALG_PIPELINED_RR) on a system
  *     of at most 16384 rows whose rows fit in shared memory as one launch

@@ -1579,6 +1579,7 @@ struct pbcg_pool {
     int *st_rp = nullptr, *st_ci = nullptr, *st_meta = nullptr;   // staging of one request
     double *st_va = nullptr;
     double *va = nullptr, *hist = nullptr;
+    double *diag = nullptr;            // Jacobi: d of every resident row (arena order), or NULL
     double *vec[V_COUNT] = {};
     Ctl *ctl = nullptr;
     GAcc *acc = nullptr;
@@ -1604,7 +1605,7 @@ void pool_release(pbcg_pool *P)
         cudaGraphDestroy(P->graph);
     void *ptrs[] = {P->sl_off, P->sl_w, P->rlen,  P->ci,      P->tile_sys, P->t0,   P->t1,   P->left,
                     P->flag,   P->bad,  P->st_rp, P->st_ci,   P->st_meta,  P->st_va, P->va,  P->hist,
-                    P->ctl,    P->acc,  P->part,  P->done,     P->lv_n, P->lv_pre, P->lv_t0};
+                    P->ctl,    P->acc,  P->part,  P->done,     P->lv_n, P->lv_pre, P->lv_t0, P->diag};
     for (void *q : ptrs)
         cudaFree(q);
     for (auto &v : P->vec)
@@ -2148,6 +2149,8 @@ int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out
         return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", c.alg);
     if (c.dot_mode != PBCG_DOT_PLAIN && c.dot_mode != PBCG_DOT_EXACT)
         return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", c.dot_mode);
+    if ((c.precond != PBCG_PRECOND_NONE && c.precond != PBCG_PRECOND_JACOBI) || c.reserved != 0)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown preconditioner %d (or reserved not 0)", c.precond);
     const long long tiles = (c.max_rows + TILE_ROWS - 1) / TILE_ROWS;
     if (tiles * TILE_ROWS > INT32_MAX / 2 || c.max_entries > INT32_MAX || c.max_request_rows > INT32_MAX / 2 ||
         c.max_request_nnz >= (1ll << 31) || c.max_slots > (1 << 20))
@@ -2188,6 +2191,8 @@ int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out
     dev((void **)&P->acc, sizeof(GAcc) * MAXD * ns);
     dev((void **)&P->part, sizeof(double) * MAXD * (size_t)tiles);
     dev((void **)&P->done, sizeof(unsigned) * ns);
+    if (c.precond == PBCG_PRECOND_JACOBI)
+        dev((void **)&P->diag, sizeof(double) * rows);
     for (auto &v : P->vec)
         dev((void **)&v, sizeof(double) * rows);
     for (auto &h : P->snap)
@@ -2355,12 +2360,31 @@ int pbcg_pool_admit(pbcg_pool *P, int32_t n, int64_t nnz, const int32_t *row_ptr
                         &rl, &co, &vo, &bd};
         const int g = std::min((rows + 255) / 256, ctx->num_sms * 8);
         CK(cudaLaunchKernel((void *)k_pool_scatter, dim3(g), dim3(256), args, 0, cs));
+        if (P->diag) {
+            // Jacobi: d from the staged CSR, then the slot's entries become those of A M^-1
+            double *dg = P->diag;
+            void *a1[] = {&nn, &nr, &r0, (void *)&rp_d, (void *)&ci_d, (void *)&va_d, &dg, &bd};
+            CK(cudaLaunchKernel((void *)k_pool_diag, dim3(g), dim3(256), a1, 0, cs));
+            const int *rl_c = rl, *co_c = co;
+            const double *dg_c = dg;
+            void *a2[] = {&nr, &r0, (void *)&so, (void *)&rl_c, (void *)&co_c, &vo, (void *)&dg_c};
+            CK(cudaLaunchKernel((void *)k_pool_jscale, dim3(g), dim3(256), a2, 0, cs));
+        }
     }
     CK(cudaMemsetAsync(P->vec[V_B] + row0, 0, sizeof(double) * rows, cs));
     CK(cudaMemsetAsync(P->vec[V_X] + row0, 0, sizeof(double) * rows, cs));
     CK(cudaMemcpyAsync(P->vec[V_B] + row0, b, sizeof(double) * n, cudaMemcpyDefault, cs));
-    if (x0)
+    if (x0) {
         CK(cudaMemcpyAsync(P->vec[V_X] + row0, x0, sizeof(double) * n, cudaMemcpyDefault, cs));
+        if (P->diag) {                                        // y0 = x0 * d
+            int nn = n;
+            const double *dd = P->diag + row0;
+            double *xx = P->vec[V_X] + row0;
+            void *a3[] = {&nn, (void *)&dd, &xx};
+            CK(cudaLaunchKernel((void *)k_vmul, dim3(std::min((n + 255) / 256, ctx->num_sms * 4)), dim3(256), a3, 0,
+                                cs));
+        }
+    }
     CK(cudaEventRecord(P->up_ev, cs));
     // the slot goes live on the solve stream once its uploads are in
     CK(cudaStreamWaitEvent(ctx->stream, P->up_ev, 0));
@@ -2481,8 +2505,15 @@ int pbcg_pool_result(pbcg_pool *P, int32_t slot, double *x, pbcg_result *out)
     PoolSlot &S = P->slots[slot];
     // a finished slot's rows are no longer written: copy without waiting for running steps
     if (x) {
-        CK(cudaMemcpyAsync(x, P->vec[V_X] + (size_t)S.tile0 * TILE_ROWS, sizeof(double) * (size_t)S.n,
-                           cudaMemcpyDefault, P->cstream));
+        double *xs = P->vec[V_X] + (size_t)S.tile0 * TILE_ROWS;
+        if (P->diag && S.last.status != ST_INVALID) {         // x = y / d (the slot is retiring)
+            int nn = S.n;
+            const double *dd = P->diag + (size_t)S.tile0 * TILE_ROWS;
+            void *a3[] = {&nn, (void *)&dd, &xs};
+            CK(cudaLaunchKernel((void *)k_vdiv, dim3(std::min((S.n + 255) / 256, ctx->num_sms * 4)), dim3(256), a3, 0,
+                                P->cstream));
+        }
+        CK(cudaMemcpyAsync(x, xs, sizeof(double) * (size_t)S.n, cudaMemcpyDefault, P->cstream));
         CK(cudaStreamSynchronize(P->cstream));
     }
     const Ctl &c = S.last;
@@ -2510,7 +2541,8 @@ int pbcg_pool_result(pbcg_pool *P, int32_t slot, double *x, pbcg_result *out)
     if (timeout)
         return fail(ctx, PBCG_ERR_TIMEOUT, "a bounded device wait expired");
     if (invalid)
-        return fail(ctx, PBCG_ERR_INVALID, "request in slot %d has a column index outside [0, n)", slot);
+        return fail(ctx, PBCG_ERR_INVALID,
+                    "request in slot %d has a column index outside [0, n) or, with Jacobi, an unusable diagonal", slot);
     return c.status;
 }
 

@@ -929,6 +929,46 @@ __global__ void k_pool_scatter(int n, int nrows, int row0, const int *__restrict
     }
 }
 
+// Jacobi for a pool request (right preconditioning, M = diag(A)), from the
+// request's staged CSR: d_i = the sum, in stored order, of row i's entries
+// in column i; an absent, zero or non-finite diagonal marks the request bad.
+// Padding rows of the slot get d = 1.
+__global__ void k_pool_diag(int n, int nrows, int row0, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const double *__restrict__ va, double *diag, int *bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
+        double d = 1.0;
+        if (i < n) {
+            bool found = false;
+            double s = 0.0;
+            for (int k = rp[i]; k < rp[i + 1]; k++)
+                if (ci[k] == i) {
+                    s = found ? __dadd_rn(s, va[k]) : va[k];
+                    found = true;
+                }
+            if (!found || s == 0.0 || !isfinite(s))
+                *bad = 1;
+            d = s;
+        }
+        diag[row0 + i] = d;
+    }
+}
+
+// the slot's stored entries become those of A M^-1: v / d_col (one IEEE division)
+__global__ void k_pool_jscale(int nrows, int row0, const int *__restrict__ sl_off, const int *__restrict__ rlen,
+                              const int *__restrict__ ci, double *va, const double *__restrict__ diag)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
+        const int sl = i >> 5;
+        const long long base = (long long)sl_off[sl] + (i & 31);
+        const int len = rlen[row0 + i];
+        for (int j = 0; j < len; j++) {
+            const long long e = base + 32ll * j;
+            va[e] = __ddiv_rn(va[e], diag[ci[e]]);
+        }
+    }
+}
+
 // a slot joins the sweep: its tiles, its tile range and its control block
 __global__ void k_pool_activate(int *tile_sys, int *sys_t0, int *sys_t1, Ctl *ctl, int sid, int t0, int ntl,
                                 Ctl init, const int *bad, unsigned *done, GAcc *acc)

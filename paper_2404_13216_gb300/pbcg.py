@@ -39,7 +39,8 @@ class PbcgError(RuntimeError):
 class _PoolConfig(ctypes.Structure):
     _fields_ = [("max_rows", ctypes.c_int64), ("max_entries", ctypes.c_int64), ("max_slots", ctypes.c_int32),
                 ("maxit", ctypes.c_int32), ("alg", ctypes.c_int32), ("dot_mode", ctypes.c_int32),
-                ("max_request_rows", ctypes.c_int64), ("max_request_nnz", ctypes.c_int64)]
+                ("max_request_rows", ctypes.c_int64), ("max_request_nnz", ctypes.c_int64),
+                ("precond", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _Result(ctypes.Structure):
@@ -280,9 +281,9 @@ class Pool:
 
     def __init__(self, ctx: Context, max_rows: int, max_entries: int, max_slots: int, maxit: int,
                  alg: int = PIPELINED, mode: int = EXACT, max_request_rows: int = None,
-                 max_request_nnz: int = None):
+                 max_request_nnz: int = None, precond: int = 0):
         cfg = _PoolConfig(int(max_rows), int(max_entries), int(max_slots), int(maxit), int(alg), int(mode),
-                          int(max_request_rows or max_rows), int(max_request_nnz or max_entries))
+                          int(max_request_rows or max_rows), int(max_request_nnz or max_entries), int(precond), 0)
         h = ctypes.c_void_p()
         ctx._check(_lib.pbcg_pool_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self.ctx, self.handle, self.max_slots = ctx, h, int(max_slots)

@@ -258,3 +258,52 @@ def test_pool_and_batch_irregular_rows(ctx, orc):
     for k, ref in enumerate(refs):
         assert res[k].status == ref.status and res[k].iters == ref.iters, k
         assert same(x[srp[k]:srp[k + 1]], ref.x), k
+
+
+@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
+def test_pool_jacobi_matches_oracle(ctx, orc, alg):
+    """A pool created with Jacobi preconditioning: every request, with a nonzero
+    x0, equals the oracle's right-Jacobi solve bit for bit; a request whose
+    diagonal has a zero finishes INVALID without touching the others."""
+    from paper_2404_13216_gb300 import pbcg
+    syst = systems(31 + alg, 6)
+    pool = pbcg.Pool(ctx, max_rows=6 * 2048, max_entries=6 * 2048 * 16, max_slots=4, maxit=2000, alg=alg,
+                     mode=pbcg.EXACT, precond=pbcg.PRECOND_JACOBI)
+    rng = np.random.default_rng(3)
+    x0s = [rng.standard_normal(A.n) for A in syst]
+    # a request whose row 3 has no diagonal entry
+    bad = inputs.convdiff2d(12, 4.0)
+    keep = [k for k in range(bad.row_ptr[3], bad.row_ptr[4]) if bad.col_idx[k] != 3]
+    rows = [list(range(bad.row_ptr[i], bad.row_ptr[i + 1])) if i != 3 else keep for i in range(bad.n)]
+    idx = [k for r in rows for k in r]
+    rp = np.zeros(bad.n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    bad = inputs.CSR(bad.n, rp, bad.col_idx[idx].astype(np.int32), bad.vals[idx])
+    live, got, queue = {}, {}, list(range(len(syst))) + ["bad"]
+    it = 0
+    while queue or live:
+        while queue:
+            key = queue[0]
+            A = bad if key == "bad" else syst[key]
+            s = pool.admit(A, inputs.rhs_ones(A), tol=1e-10, maxit=2000, x0=None if key == "bad" else x0s[key])
+            if s is None:
+                break
+            live[s] = queue.pop(0)
+        pool.step(4)
+        it += 1
+        done, _ = pool.poll(wait=True)
+        for s in done:
+            key = live.pop(s)
+            h = pool.history(s)
+            x, r = pool.result(s)
+            got[key] = (x, r, h)
+        assert it < 20000
+    pool.close()
+    assert got["bad"][1].status == -1 and got["bad"][1].iters == 0, got["bad"][1]      # PBCG_ERR_INVALID
+    for k, A in enumerate(syst):
+        ref = orc.solve(A.row_ptr, A.col_idx, A.vals, inputs.rhs_ones(A), x0=x0s[k], tol=1e-10, maxit=2000,
+                        alg=alg, mode=1, jacobi=True)
+        x, r, h = got[k]
+        assert r.status == ref.status and r.iters == ref.iters, (k, r, ref.status, ref.iters)
+        assert same(h, ref.history), k
+        assert same(x, ref.x), k
