@@ -89,3 +89,59 @@ def test_fuzz_spmv_is_row_fma_chain(orc, m):
     got = orc.spmv(rp, ci, va, x)
     want = fma_spmv(rp, ci, va, x)
     assert all(same(g, w) for g, w in zip(got, want))
+
+
+@st.composite
+def tiny_dominant_system(draw):
+    n = draw(st.integers(2, 5))
+    A = np.array([[draw(st.integers(-4, 4)) for _ in range(n)] for _ in range(n)], dtype=np.int64)
+    A += np.diag(np.abs(A).sum(axis=1) + draw(st.integers(1, 5)))
+    b = np.array([draw(st.integers(-6, 6)) for _ in range(n)], dtype=np.int64)
+    b[draw(st.integers(0, n - 1))] = draw(st.integers(1, 9))      # b != 0
+    return A, b
+
+
+@settings(max_examples=40, deadline=None, derandomize=True)
+@given(tiny_dominant_system())
+def test_fuzz_oracle_follows_rational_algorithms(orc, sysb):
+    """Drawn diagonally dominant integer systems: in rational arithmetic
+    Algorithms 1 and 2 give identical iterates and Algorithm 2's invariants
+    hold; the FP64 oracle (both algorithms, exact dots) follows the rational
+    residual norms and alpha, omega over the first two iterations (omega
+    only while the rational q is nonzero: where the exact run reaches the
+    solution, FP64 keeps a rounding-level residual and its own omega)."""
+    from fractions import Fraction
+    from tests import ratref
+    A, b = sysb
+    n = A.shape[0]
+    Af = [[Fraction(int(a)) for a in row] for row in A]
+    bf = [Fraction(int(v)) for v in b]
+    bad = []
+    p = ratref.pbicgstab(Af, bf, [Fraction(0)] * n, 2, check=lambda name, l, r: bad.append(name) if l != r else None)
+    c = ratref.bicgstab(Af, bf, [Fraction(0)] * n, 2)
+    assert not bad, set(bad)
+    assert len(p) == len(c)
+    for rp_, rc_ in zip(p, c):
+        for key in ("x", "r", "alpha", "omega", "beta"):
+            assert rp_[key] == rc_[key], key
+    rp, ci, v = [0], [], []
+    for i in range(n):
+        for j in range(n):
+            if A[i, j] != 0:
+                ci.append(j)
+                v.append(float(A[i, j]))
+        rp.append(len(ci))
+    rp, ci, v = np.array(rp, np.int32), np.array(ci, np.int32), np.array(v)
+    normb = math.sqrt(float(ratref.dot(bf, bf)))
+    for alg in (0, 1):
+        res = orc.solve(rp, ci, v, b.astype(float), tol=1e-300, maxit=2, alg=alg, mode=orc.EXACT, trace=True)
+        for i in range(min(len(c), res.iters)):
+            r = c[i]["r"]
+            want = math.sqrt(float(ratref.dot(r, r))) / normb
+            got = res.history[i + 1]
+            assert abs(got - want) <= 1e-9 * want + 1e-13, (alg, i, got, want)
+            for col, key in ((0, "alpha"), (1, "omega")):
+                if key == "omega" and c[i][key] == 0:
+                    continue     # q = 0: the rational run ends here; FP64 keeps a rounding-level q
+                w = float(c[i][key])
+                assert abs(res.trace[i, col] - w) <= 1e-9 * abs(w) + 1e-300, (alg, i, key)
