@@ -260,13 +260,15 @@ def test_pool_and_batch_irregular_rows(ctx, orc):
         assert same(x[srp[k]:srp[k + 1]], ref.x), k
 
 
-@pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
+@pytest.mark.parametrize("alg", [0, 1, 2], ids=["bicgstab", "pbicgstab", "pbicgstab_rr"])
 def test_pool_jacobi_matches_oracle(ctx, orc, alg):
     """A pool created with Jacobi preconditioning: every request, with a nonzero
     x0, equals the oracle's right-Jacobi solve bit for bit; a request whose
     diagonal has a zero finishes INVALID without touching the others."""
     from paper_2404_13216_gb300 import pbcg
     syst = systems(31 + alg, 6)
+    if alg == 2:
+        ctx.set_option(pbcg.OPT_RR_PERIOD, 7)
     pool = pbcg.Pool(ctx, max_rows=6 * 2048, max_entries=6 * 2048 * 16, max_slots=4, maxit=2000, alg=alg,
                      mode=pbcg.EXACT, precond=pbcg.PRECOND_JACOBI)
     rng = np.random.default_rng(3)
@@ -299,10 +301,12 @@ def test_pool_jacobi_matches_oracle(ctx, orc, alg):
             got[key] = (x, r, h)
         assert it < 20000
     pool.close()
+    if alg == 2:
+        ctx.set_option(pbcg.OPT_RR_PERIOD, 50)
     assert got["bad"][1].status == -1 and got["bad"][1].iters == 0, got["bad"][1]      # PBCG_ERR_INVALID
     for k, A in enumerate(syst):
         ref = orc.solve(A.row_ptr, A.col_idx, A.vals, inputs.rhs_ones(A), x0=x0s[k], tol=1e-10, maxit=2000,
-                        alg=alg, mode=1, jacobi=True)
+                        alg=min(alg, 1), mode=1, jacobi=True, rr_period=7 if alg == 2 else 0)
         x, r, h = got[k]
         assert r.status == ref.status and r.iters == ref.iters, (k, r, ref.status, ref.iters)
         assert same(h, ref.history), k
