@@ -16,7 +16,8 @@ buffers (host<->device copies inside the timed region).  `roofline` gives the
 dominant kernel's achieved HBM bandwidth (algorithmic bytes / CUDA-event time)
 against the measured copy bandwidth.  `cpu_baseline` times the CPU oracle on a
 bounded sample.  `--impl reference` times the CPU oracle alone (the reference
-arm of this comparison).
+arm of this comparison).  `--cpu-table` times the CPU oracle alone on every
+configuration's sample and prints its table (no GPU).
 """
 from __future__ import annotations
 
@@ -118,15 +119,15 @@ def reduce_over_ranks(dist, ms: float, its: int, device):
     return float(t.item()), int(c.item())
 
 
-def oracle_sample(A, b, nthreads: int, mode: int, iters: int):
-    """Time `iters` iterations of the CPU oracle's p-BiCGStab (setup excluded by
-    differencing a 1-iteration run)."""
+def oracle_sample(A, b, nthreads: int, mode: int, iters: int, alg: int = 1):
+    """Time `iters` iterations of the CPU oracle's p-BiCGStab (alg 1) or
+    BiCGStab (alg 0), setup excluded by differencing a 1-iteration run."""
     import oracle
     t0 = time.perf_counter()
-    oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=1, alg=oracle.PIPELINED, mode=mode,
+    oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=1, alg=alg, mode=mode,
                  nthreads=nthreads)
     t1 = time.perf_counter()
-    oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=1 + iters, alg=oracle.PIPELINED, mode=mode,
+    oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=1 + iters, alg=alg, mode=mode,
                  nthreads=nthreads)
     t2 = time.perf_counter()
     dt = (t2 - t1) - (t1 - t0)
@@ -135,6 +136,13 @@ def oracle_sample(A, b, nthreads: int, mode: int, iters: int):
 
 def cpu_model():
     try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu part")):
                 return line.split(":", 1)[1].strip()
@@ -142,6 +150,69 @@ def cpu_model():
         pass
     import platform
     return platform.machine()
+
+
+def run_cpu_table(args):
+    """The CPU oracle's timings on the host cores, no GPU: ms per iteration on
+    the 128^3 system (plain on 1 core for both algorithms; exact on 1 core
+    and on all cores) and on the power-law matrix (plain on 1 core, exact on
+    all cores), each over a fixed iteration count with setup differenced
+    out, and a 16-system subset of the 512-system batch solved exactly to
+    1e-10 on all cores, extrapolated to solves per second.  A reported
+    baseline, not a target; the oracle is run as it stands."""
+    import numpy as np
+    from paper_2404_13216_gb300 import inputs
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    out = {"cpu": cpu_model(), "cores": cores, "unit": "ms/iter"}
+
+    def ms(A, b, nt, mode, its, alg):
+        v, _ = oracle_sample(A, b, nt, mode, its, alg)
+        return round(1e3 / v, 2)
+
+    A = inputs.convdiff3d(N_SIDE, PECLET, WIND)
+    b = inputs.rhs_ones(A)
+    k = args.cpu_iters
+    out["convdiff128"] = {
+        "iters": k,
+        "pbicgstab_plain_1core": ms(A, b, 1, oracle.PLAIN, k, oracle.PIPELINED),
+        "bicgstab_plain_1core": ms(A, b, 1, oracle.PLAIN, k, oracle.BICGSTAB),
+        "pbicgstab_exact_1core": ms(A, b, 1, oracle.EXACT, k, oracle.PIPELINED),
+        "pbicgstab_exact_all_cores": ms(A, b, cores, oracle.EXACT, k, oracle.PIPELINED),
+        "bicgstab_exact_all_cores": ms(A, b, cores, oracle.EXACT, k, oracle.BICGSTAB),
+    }
+    del A, b
+    P = inputs.powerlaw()
+    bp = inputs.rhs_ones(P)
+    kp = args.cpu_powerlaw_iters
+    out["powerlaw"] = {
+        "n": int(P.n), "nnz": int(P.nnz), "iters": kp,
+        "pbicgstab_plain_1core": ms(P, bp, 1, oracle.PLAIN, kp, oracle.PIPELINED),
+        "pbicgstab_exact_all_cores": ms(P, bp, cores, oracle.EXACT, kp, oracle.PIPELINED),
+    }
+    del P, bp
+    B = inputs.batched_convdiff(nsys=512, seed=4)
+    nsub = 16
+    t0 = time.perf_counter()
+    its, conv = [], 0
+    for j in range(nsub):
+        S = inputs.convdiff2d(int(B.sides[j]), float(B.peclet[j]))
+        r = oracle.solve(S.row_ptr, S.col_idx, S.vals, inputs.rhs_ones(S), tol=1e-10, maxit=4000,
+                         alg=oracle.PIPELINED, mode=oracle.EXACT, nthreads=cores)
+        its.append(r.iters)
+        conv += int(r.status == 0)
+    dt = time.perf_counter() - t0
+    rows = int(sum(int(B.sides[j]) ** 2 for j in range(nsub)))
+    out["batched_subset"] = {
+        "systems": nsub, "rows": rows, "rows_all_512": int(B.A.n), "tol": 1e-10, "maxit": 4000,
+        "iters_mean": float(np.mean(its)), "converged": conv, "seconds": round(dt, 2),
+        "solves_per_s": round(nsub / dt, 3),
+        # the subset's rows are fewer than 16/512 of the batch's, so scale by rows too
+        "solves_per_s_rows_scaled": round(nsub / dt * (rows * 512 / nsub) / int(B.A.n), 3),
+    }
+    print(json.dumps({"cpu_table": out}), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -616,7 +687,13 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the other-configuration legs")
     ap.add_argument("--serving-requests", type=int, default=1000)
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the CPU oracle on the host cores (128^3, power-law, a batched subset) and exit")
+    ap.add_argument("--cpu-iters", type=int, default=20)
+    ap.add_argument("--cpu-powerlaw-iters", type=int, default=10)
     args = ap.parse_args()
+    if args.cpu_table:
+        return run_cpu_table(args)
     if args.ncu_case:
         return run_ncu_case(args)
     if args.impl == "reference":
