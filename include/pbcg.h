@@ -96,7 +96,8 @@ int pbcg_mat_free(pbcg_ctx *ctx, pbcg_mat *mat);
  * Solve A x = b from x (in: x_0, out: the last iterate, written for every
  * status).  b and x hold n doubles each.  alg: PBCG_ALG_* (PIPELINED_RR is
  * Algorithm 2 with residual replacement, see pbcg_set_option); dot_mode:
- * PBCG_DOT_*.
+ * PBCG_DOT_*.  tol > 0; 0 <= maxit <= 2^31 - 2 (the history holds maxit + 1
+ * entries); INVALID otherwise.
  *
  * Algorithm 2 (p-BiCGStab), with omega the scalar (q,y)/(y,y) and w the
  * vector A r (the paper uses the letter w for both):
@@ -180,7 +181,7 @@ typedef struct {
     int64_t max_rows;          /* rows of all resident systems together (each rounded up to 256) */
     int64_t max_entries;       /* SELL-32 entries of all resident systems together */
     int32_t max_slots;         /* systems resident at a time */
-    int32_t maxit;             /* largest maxit a request may ask for (history length maxit + 1) */
+    int32_t maxit;             /* largest maxit a request may ask for, 0 .. 2^31 - 2 (history length maxit + 1) */
     int32_t alg;               /* PBCG_ALG_*, for every system of the pool */
     int32_t dot_mode;          /* PBCG_DOT_*, for every system of the pool */
     int64_t max_request_rows;  /* largest n of one request */

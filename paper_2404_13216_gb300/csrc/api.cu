@@ -49,6 +49,7 @@ struct Workspace {
     double *part = nullptr;
     double *hist = nullptr;
     double *dot_out = nullptr;
+    bool base_ready = false;       // ctl, wk, part, dot_out allocated and wk initialised
     LoopGraph loop;
 };
 
@@ -282,11 +283,17 @@ void free_ws(Workspace &ws)
 int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
 {
     Workspace &ws = ctx->ws;
-    if (!ws.ctl) {
-        CK(cudaMalloc(&ws.ctl, sizeof(Ctl)));
-        CK(cudaMalloc(&ws.wk, sizeof(Work)));
-        CK(cudaMalloc(&ws.part, sizeof(double) * MAXD * ctx->maxgrid));
-        CK(cudaMalloc(&ws.dot_out, sizeof(double)));
+    if (!ws.base_ready) {
+        // each buffer is taken only if missing, so a call after an allocation
+        // failure completes the set instead of running with a null one
+        if (!ws.ctl)
+            CK(cudaMalloc(&ws.ctl, sizeof(Ctl)));
+        if (!ws.wk)
+            CK(cudaMalloc(&ws.wk, sizeof(Work)));
+        if (!ws.part)
+            CK(cudaMalloc(&ws.part, sizeof(double) * MAXD * ctx->maxgrid));
+        if (!ws.dot_out)
+            CK(cudaMalloc(&ws.dot_out, sizeof(double)));
         Work h;
         memset(&h, 0, sizeof h);
         for (int d = 0; d < MAXD; d++) {
@@ -297,6 +304,7 @@ int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
         h.maxgrid = ctx->maxgrid;
         h.part = ws.part;
         CK(cudaMemcpy(ws.wk, &h, sizeof h, cudaMemcpyHostToDevice));
+        ws.base_ready = true;
     }
     if (n > ws.n_cap) {
         free_loop(ws.loop);
@@ -698,16 +706,31 @@ int ensure_jacobi(pbcg_ctx *ctx, pbcg_mat *m)
     for (int p = 0; p < n; p++)
         ds[(size_t)p] = d[(size_t)(m->perm ? perm[(size_t)p] : p)];
     const size_t P = (size_t)(m->padded ? m->padded : 1);
-    CK(cudaMalloc(&m->diag, sizeof(double) * (size_t)n));
-    CK(cudaMalloc(&m->va_jac, sizeof(double) * P));
-    CK(cudaMemcpy(m->diag, ds.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
-    long long ne = m->padded;
-    const int *ci = m->ci;
-    const double *va = m->va, *dd = m->diag;
-    double *vs = m->va_jac;
-    void *args[5] = {&ne, (void *)&ci, (void *)&va, (void *)&dd, &vs};
-    CK(cudaLaunchKernel((void *)k_jacobi_scale, dim3(ctx->num_sms * 8), dim3(256), args, 0, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    // built aside and attached only once scaled, so a failed call leaves the
+    // matrix as it was and a later call starts over
+    double *dd = nullptr, *vs = nullptr;
+    cudaError_t e = cudaMalloc(&dd, sizeof(double) * (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&vs, sizeof(double) * P);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dd, ds.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        long long ne = m->padded;
+        const int *ci = m->ci;
+        const double *va = m->va, *ddc = dd;
+        void *args[5] = {&ne, (void *)&ci, (void *)&va, (void *)&ddc, &vs};
+        e = cudaLaunchKernel((void *)k_jacobi_scale, dim3(ctx->num_sms * 8), dim3(256), args, 0, ctx->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(dd);
+        cudaFree(vs);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "Jacobi scaling: %s",
+                    cudaGetErrorString(e));
+    }
+    m->diag = dd;
+    m->va_jac = vs;
     return 0;
 }
 
@@ -864,8 +887,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         return fail(ctx, PBCG_ERR_INVALID, "b and x must not be NULL");
     if (!(tol > 0.0))
         return fail(ctx, PBCG_ERR_INVALID, "tol must be > 0");
-    if (maxit < 0)
-        return fail(ctx, PBCG_ERR_INVALID, "maxit must be >= 0");
+    if (maxit < 0 || maxit == INT32_MAX)      // the history holds maxit + 1 entries
+        return fail(ctx, PBCG_ERR_INVALID, "maxit must be in 0 .. 2^31 - 2");
     if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED && alg != PBCG_ALG_PIPELINED_RR)
         return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", alg);
     if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
@@ -1292,8 +1315,8 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
     if (nsys < 1 || !sys_row_ptr || !b || !x || !tol || !out)
         return fail(ctx, PBCG_ERR_INVALID, "bad batched arguments");
-    if (maxit < 0)
-        return fail(ctx, PBCG_ERR_INVALID, "maxit must be >= 0");
+    if (maxit < 0 || maxit == INT32_MAX)      // the history holds maxit + 1 entries
+        return fail(ctx, PBCG_ERR_INVALID, "maxit must be in 0 .. 2^31 - 2");
     if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED && alg != PBCG_ALG_PIPELINED_RR)
         return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", alg);
     if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
@@ -2040,7 +2063,12 @@ int pbcg_dot(pbcg_ctx *ctx, int64_t n, const double *a, const double *b, int dot
     int rc = ensure_ws(ctx, 0, 0);
     if (rc)
         return rc;
-    double *da = nullptr, *db = nullptr;
+    // host operands are staged in buffers freed on every return
+    struct Staging {
+        double *p = nullptr;
+        ~Staging() { if (p) cudaFree(p); }
+    } sa, sb;
+    double *&da = sa.p, *&db = sb.p;
     cudaPointerAttributes pa, pb;
     bool a_dev = n > 0 && cudaPointerGetAttributes(&pa, a) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
     bool b_dev = n > 0 && cudaPointerGetAttributes(&pb, b) == cudaSuccess && pb.type == cudaMemoryTypeDevice;
@@ -2063,10 +2091,6 @@ int pbcg_dot(pbcg_ctx *ctx, int64_t n, const double *a, const double *b, int dot
                         ctx->stream));
     CK(cudaMemcpyAsync(out, o, sizeof(double), cudaMemcpyDefault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    if (da)
-        cudaFree(da);
-    if (db)
-        cudaFree(db);
     return 0;
 }
 
@@ -2142,9 +2166,10 @@ int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out
         return fail(ctx, PBCG_ERR_INVALID, "NULL argument");
     *out = nullptr;
     const pbcg_pool_config c = *cfg;
-    if (c.max_rows < 1 || c.max_entries < 1 || c.max_slots < 1 || c.maxit < 0 || c.max_request_rows < 1 ||
+    if (c.max_rows < 1 || c.max_entries < 1 || c.max_slots < 1 || c.maxit < 0 || c.maxit == INT32_MAX ||
+        c.max_request_rows < 1 ||
         c.max_request_nnz < 0)
-        return fail(ctx, PBCG_ERR_INVALID, "pool sizes must be positive");
+        return fail(ctx, PBCG_ERR_INVALID, "pool sizes must be positive (maxit 0 .. 2^31 - 2)");
     if (c.alg != PBCG_ALG_BICGSTAB && c.alg != PBCG_ALG_PIPELINED && c.alg != PBCG_ALG_PIPELINED_RR)
         return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", c.alg);
     if (c.dot_mode != PBCG_DOT_PLAIN && c.dot_mode != PBCG_DOT_EXACT)
@@ -2186,7 +2211,7 @@ int pbcg_pool_create(pbcg_ctx *ctx, const pbcg_pool_config *cfg, pbcg_pool **out
     dev((void **)&P->st_meta, sizeof(int) * meta_ints);
     dev((void **)&P->st_ci, sizeof(int) * (size_t)c.max_request_nnz);
     dev((void **)&P->st_va, sizeof(double) * (size_t)c.max_request_nnz);
-    dev((void **)&P->hist, sizeof(double) * ns * (size_t)(c.maxit + 1));
+    dev((void **)&P->hist, sizeof(double) * ns * ((size_t)c.maxit + 1));
     dev((void **)&P->ctl, sizeof(Ctl) * ns);
     dev((void **)&P->acc, sizeof(GAcc) * MAXD * ns);
     dev((void **)&P->part, sizeof(double) * MAXD * (size_t)tiles);

@@ -106,6 +106,9 @@ def test_batched_invalid(ctx):
         ctx.solve_batched(M, np.array([0, 30, A.n], np.int32), b, np.zeros(A.n), np.full(2, 1e-8), 10)
     with pytest.raises(pbcg.PbcgError):
         ctx.solve_batched(M, srp, b, np.zeros(A.n), np.array([1e-8, 0.0]), 10)
+    with pytest.raises(pbcg.PbcgError) as e:
+        ctx.solve_batched(M, srp, b, np.zeros(A.n), np.full(2, 1e-8), 2 ** 31 - 1)
+    assert e.value.code == pbcg.ERR_INVALID
     M.free()
 
 

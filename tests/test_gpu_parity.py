@@ -260,6 +260,9 @@ def test_invalid_inputs(ctx):
         ctx.solve(M, np.ones(A.n), np.zeros(A.n), 1e-8, -1)
     with pytest.raises(pbcg.PbcgError):
         ctx.solve(M, np.ones(A.n), np.zeros(A.n), 1e-8, 10, alg=7)
+    with pytest.raises(pbcg.PbcgError) as e:                     # maxit + 1 history entries must fit int32
+        ctx.solve(M, np.ones(A.n), np.zeros(A.n), 1e-8, 2 ** 31 - 1)
+    assert e.value.code == pbcg.ERR_INVALID
     M.free()
 
 

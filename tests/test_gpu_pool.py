@@ -213,6 +213,9 @@ def test_pool_invalid_arguments(ctx):
         pbcg.Pool(ctx, max_rows=0, max_entries=10, max_slots=1, maxit=10)
     with pytest.raises(pbcg.PbcgError):
         pbcg.Pool(ctx, max_rows=256, max_entries=10, max_slots=1, maxit=10, alg=7)
+    with pytest.raises(pbcg.PbcgError) as e:
+        pbcg.Pool(ctx, max_rows=256, max_entries=10, max_slots=1, maxit=2 ** 31 - 1)
+    assert e.value.code == pbcg.ERR_INVALID
     pool = pbcg.Pool(ctx, max_rows=512, max_entries=4096, max_slots=2, maxit=10, max_request_rows=300,
                      max_request_nnz=2000)
     A = inputs.convdiff2d(18, 5.0)       # 324 rows: beyond max_request_rows
@@ -230,6 +233,29 @@ def test_pool_invalid_arguments(ctx):
     with pytest.raises(pbcg.PbcgError):
         pool.step(0)
     pool.close()
+
+
+def test_pool_out_of_memory_leaves_context_usable(ctx, orc):
+    """A pool whose residual histories cannot be allocated (2^20 slots x
+    (2^30 + 1) iterations, about 9 PB) is refused with OOM; what it had taken
+    is released, and the context still solves exactly, alone and in a pool."""
+    from paper_2404_13216_gb300 import pbcg
+    with pytest.raises(pbcg.PbcgError) as e:
+        pbcg.Pool(ctx, max_rows=256, max_entries=2048, max_slots=1 << 20, maxit=1 << 30)
+    assert e.value.code == pbcg.ERR_OOM
+    A = inputs.convdiff2d(12, 20.0)
+    b = inputs.rhs_ones(A)
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=300, alg=1, mode=1)
+    M = ctx.upload_csr(A)
+    x = np.zeros(A.n)
+    r = ctx.solve(M, b, x, 1e-10, 300, pbcg.PIPELINED, pbcg.EXACT)
+    M.free()
+    assert r.iters == ref.iters and same(x, ref.x)
+    with pbcg.Pool(ctx, max_rows=1024, max_entries=8192, max_slots=2, maxit=300) as pool:
+        s = pool.admit(A, b, tol=1e-10, maxit=300)
+        got = {}
+        drain(pool, {s: 0}, got, 16)
+    assert got[0][1].iters == ref.iters and same(got[0][0], ref.x)
 
 
 def test_pool_and_batch_irregular_rows(ctx, orc):
