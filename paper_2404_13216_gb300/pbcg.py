@@ -116,9 +116,48 @@ def _ptr(a):
 
 
 def _host(a, dtype):
+    """A numpy input converted to a C-contiguous `dtype` array, or a torch
+    tensor (host or device), which must already be contiguous `dtype`."""
     if hasattr(a, "data_ptr"):
+        want = np.dtype(dtype).name
+        if str(a.dtype) != "torch." + want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor, got {a.dtype}"
+                            + ("" if a.is_contiguous() else " (not contiguous)"))
         return a
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _count(a) -> int:
+    return a.numel() if hasattr(a, "numel") else a.size
+
+
+def _vec_in(a, n: int, name: str, dtype=np.float64):
+    """An input vector of exactly n entries."""
+    a = _host(a, dtype)
+    if _count(a) != n:
+        raise ValueError(f"{name} has {_count(a)} entries, expected {n}")
+    return a
+
+
+def _vec_out(a, n: int, name: str):
+    """A float64 vector of n entries that the library writes in place, so it
+    is checked, never converted."""
+    if hasattr(a, "data_ptr"):
+        _host(a, np.float64)
+    elif not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.flags.writeable):
+        raise TypeError(f"{name} must be a writable C-contiguous float64 array or tensor (written in place)")
+    if _count(a) != n:
+        raise ValueError(f"{name} has {_count(a)} entries, expected {n}")
+    return a
+
+
+def _csr(row_ptr, col_idx, vals):
+    rp, ci, va = _host(row_ptr, np.int32), _host(col_idx, np.int32), _host(vals, np.float64)
+    n, nnz = _count(rp) - 1, _count(va)
+    if n < 0 or _count(ci) != nnz:
+        raise ValueError(f"CSR arrays disagree: {_count(rp)} row pointers, {_count(ci)} column indices, "
+                         f"{nnz} values")
+    return rp, ci, va, n, nnz
 
 
 def dot_noalloc(a, b, out, mode: int = EXACT, stream=None) -> int:
@@ -190,9 +229,7 @@ class Context:
         return rc
 
     def upload(self, row_ptr, col_idx, vals) -> Matrix:
-        rp, ci, va = _host(row_ptr, np.int32), _host(col_idx, np.int32), _host(vals, np.float64)
-        n = (rp.numel() if hasattr(rp, "numel") else rp.size) - 1
-        nnz = va.numel() if hasattr(va, "numel") else va.size
+        rp, ci, va, n, nnz = _csr(row_ptr, col_idx, vals)
         m = ctypes.c_void_p()
         dev = int(hasattr(rp, "is_cuda") and rp.is_cuda)
         self._check(_lib.pbcg_csr_upload(self.handle, n, nnz, _ptr(rp), _ptr(ci), _ptr(va), dev, ctypes.byref(m)))
@@ -203,6 +240,7 @@ class Context:
 
     def solve(self, mat: Matrix, b, x, tol: float, maxit: int, alg: int = PIPELINED, mode: int = EXACT) -> Result:
         """Solve in place: x holds x0 on entry and the last iterate on return."""
+        b, x = _vec_in(b, mat.n, "b"), _vec_out(x, mat.n, "x")
         r = _Result()
         self._check(_lib.pbcg_solve(self.handle, mat.handle, _ptr(b), _ptr(x), float(tol), int(maxit), int(alg),
                                     int(mode), ctypes.byref(r)))
@@ -211,8 +249,11 @@ class Context:
     def solve_batched(self, mat: Matrix, sys_row_ptr, b, x, tol, maxit: int, alg: int = PIPELINED,
                       mode: int = EXACT):
         srp = _host(sys_row_ptr, np.int32)
-        nsys = (srp.numel() if hasattr(srp, "numel") else srp.size) - 1
-        tl = _host(tol, np.float64)
+        nsys = _count(srp) - 1
+        if nsys < 1:
+            raise ValueError("sys_row_ptr needs at least two entries")
+        tl = _vec_in(tol, nsys, "tol")
+        b, x = _vec_in(b, mat.n, "b"), _vec_out(x, mat.n, "x")
         res = (_Result * nsys)()
         self._check(_lib.pbcg_solve_batched(self.handle, mat.handle, nsys, _ptr(srp), _ptr(b), _ptr(x), _ptr(tl),
                                             int(maxit), int(alg), int(mode), res))
@@ -226,8 +267,9 @@ class Context:
         return out
 
     def dot(self, a, b, mode: int = EXACT) -> float:
-        a, b = _host(a, np.float64), _host(b, np.float64)
-        n = a.numel() if hasattr(a, "numel") else a.size
+        a = _host(a, np.float64)
+        n = _count(a)
+        b = _vec_in(b, n, "b")
         out = ctypes.c_double(0.0)
         self._check(_lib.pbcg_dot(self.handle, n, _ptr(a), _ptr(b), int(mode), ctypes.byref(out)))
         return out.value
@@ -239,15 +281,15 @@ class Context:
         return bool(exp.value), sec.value
 
     def spmv(self, mat: Matrix, x, y=None):
-        x = _host(x, np.float64)
-        if y is None:
-            y = np.empty(mat.n, dtype=np.float64)
+        x = _vec_in(x, mat.n, "x")
+        y = np.empty(mat.n, dtype=np.float64) if y is None else _vec_out(y, mat.n, "y")
         self._check(_lib.pbcg_spmv(self.handle, mat.handle, _ptr(x), _ptr(y)))
         return y
 
     def profile_solve(self, mat: Matrix, b, x, tol: float, maxit: int, alg: int = PIPELINED, mode: int = EXACT):
         """Solve with a host-driven loop and CUDA events around every kernel.
         Returns (Result, {kernel: (total_ms, launches)})."""
+        b, x = _vec_in(b, mat.n, "b"), _vec_out(x, mat.n, "x")
         cap = 32
         names = (ctypes.c_char * 32 * cap)()
         ms = np.zeros(cap, dtype=np.float64)
@@ -302,11 +344,9 @@ class Pool:
         self.close()
 
     def admit(self, A, b, x0=None, tol: float = 1e-8, maxit: int = 1000):
-        rp, ci, va = _host(A.row_ptr, np.int32), _host(A.col_idx, np.int32), _host(A.vals, np.float64)
-        b = _host(b, np.float64)
-        x0 = None if x0 is None else _host(x0, np.float64)
-        n = (rp.numel() if hasattr(rp, "numel") else rp.size) - 1
-        nnz = va.numel() if hasattr(va, "numel") else va.size
+        rp, ci, va, n, nnz = _csr(A.row_ptr, A.col_idx, A.vals)
+        b = _vec_in(b, n, "b")
+        x0 = None if x0 is None else _vec_in(x0, n, "x0")
         slot = ctypes.c_int32(-1)
         rc = self.ctx._check(_lib.pbcg_pool_admit(self.handle, n, nnz, _ptr(rp), _ptr(ci), _ptr(va), _ptr(b),
                                                   _ptr(x0), float(tol), int(maxit), ctypes.byref(slot)))
@@ -335,8 +375,11 @@ class Pool:
     def result(self, slot: int, x=None):
         """Retire `slot`: (x, Result).  A request that failed (bad column
         index, device wait expired) gives a Result with its negative code."""
+        n = self.sizes.get(slot)
         if x is None:
-            x = np.empty(self.sizes[slot], dtype=np.float64)
+            x = None if n is None else np.empty(n, dtype=np.float64)
+        elif n is not None:
+            x = _vec_out(x, n, "x")
         r = _Result()
         rc = _lib.pbcg_pool_result(self.handle, int(slot), _ptr(x), ctypes.byref(r))
         if rc < 0 and r.status >= 0:
