@@ -81,7 +81,7 @@ const char *pbcg_last_error(pbcg_ctx *ctx);
 /*
  * Copy a CSR matrix to the device.  row_ptr[n+1], col_idx[nnz], vals[nnz];
  * host or device pointers (ptrs_on_device is a hint only, the library checks).
- * Validation (INVALID on failure): n >= 1, nnz >= 0, row_ptr[0] == 0,
+ * Validation (INVALID on failure): 1 <= n <= 2^30 - 1, nnz >= 0, row_ptr[0] == 0,
  * row_ptr non-decreasing, row_ptr[n] == nnz < 2^31, 0 <= col_idx < n.
  * Duplicate columns are allowed and summed in stored order.
  * The matrix belongs to ctx and is freed by pbcg_mat_free or pbcg_destroy.

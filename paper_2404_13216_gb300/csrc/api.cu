@@ -1872,8 +1872,9 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     if (!out || !row_ptr || (nnz > 0 && (!col_idx || !vals)))
         return fail(ctx, PBCG_ERR_INVALID, "NULL argument");
     *out = nullptr;
-    if (n < 1)
-        return fail(ctx, PBCG_ERR_INVALID, "n must be >= 1 (got %d)", n);
+    // rows padded to whole 256-row tiles are indexed in int32 by the kernels
+    if (n < 1 || n > INT32_MAX / 2)
+        return fail(ctx, PBCG_ERR_INVALID, "n must be in 1 .. 2^30 - 1 (got %d)", n);
     if (nnz < 0 || nnz >= (1ll << 31))
         return fail(ctx, PBCG_ERR_INVALID, "nnz out of range (got %lld)", (long long)nnz);
     CK(cudaSetDevice(ctx->device));
