@@ -324,3 +324,62 @@ def test_jacobi_rejects_a_missing_or_zero_diagonal(orc):
     v[A.row_ptr[3]:A.row_ptr[4]][A.col_idx[A.row_ptr[3]:A.row_ptr[4]] == 3] = 0.0
     with pytest.raises(ValueError):
         orc.solve(A.row_ptr, A.col_idx, v, inputs.rhs_ones(A), tol=1e-8, maxit=10, jacobi=True)
+
+
+def _true_relres(A, b, x):
+    """||b - A x|| / ||b|| as the stopping rule defines it: the SpMV row as its
+    fma chain, r_i = b_i - (A x)_i in FP64, both dots correctly rounded, then
+    sqrt((r,r)) / sqrt((b,b)) -- computed here with rationals, not the oracle."""
+    from tests.fracref import exact_dot, fma_spmv, rn
+    r = np.asarray(b) - np.array(fma_spmv(A.row_ptr, A.col_idx, A.vals, x))
+    sb = math.sqrt(rn(exact_dot(b, b)))
+    return math.sqrt(rn(exact_dot(r, r))) / (sb if sb != 0.0 else 1.0)
+
+
+# (side, Peclet, tol, alg, mode, the oracle's status): tolerances at the level
+# of attainable accuracy, where the recursive residual passes the target
+# before the true residual does
+STOP_CASES = [
+    (6, 3.0, 1.35e-15, 0, 0, 0),      # one failed check, then a stop
+    (8, 10.0, 4e-15, 0, 1, 0),
+    (12, 5.0, 4e-15, 0, 1, 0),        # two failed checks
+    (10, 30.0, 3.6e-15, 0, 0, 0),     # three
+    (6, 3.0, 1e-15, 0, 1, 2),         # every check fails until a breakdown
+    (8, 10.0, 3e-15, 1, 1, 1),        # p-BiCGStab: checks fail, the iterate drifts, maxit
+]
+
+
+@pytest.mark.parametrize("case", STOP_CASES, ids=[f"{c[0]}x{c[0]}-tol{c[2]:g}-alg{c[3]}-mode{c[4]}" for c in STOP_CASES])
+def test_stop_rule_true_residual_decides(orc, case):
+    """Reading 6 simulated outside the oracle: from the oracle's residual
+    history and its iterates x_k (a rerun with maxit = k), a check happens at
+    the first k whose recursive residual is <= the target; the true residual
+    (computed above with rationals) ends the solve if it is <= tol, else the
+    target becomes tol*(tol/true) and the loop goes on.  The predicted stop
+    must be the oracle's, and where no check passes the oracle must not
+    report convergence.  (On these systems a target left at tol predicts the
+    same stops: the skipped iterations have true residuals above tol.)"""
+    N, Pe, tol, alg, mode, status = case
+    A = inputs.convdiff2d(N, Pe)
+    b = inputs.rhs_ones(A)
+    maxit = 300
+    full = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=tol, maxit=maxit, alg=alg, mode=mode)
+    assert full.status == status
+    h = full.history
+    target, failed, stop = tol, 0, None
+    for k in range(len(h)):
+        if not h[k] <= target:
+            continue
+        xk = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=tol, maxit=k, alg=alg, mode=mode).x
+        true = _true_relres(A, b, xk)
+        if true <= tol:
+            stop = k
+            break
+        failed += 1
+        target = tol * (tol / true)
+    assert failed >= 1                       # the recursive residual alone would have stopped earlier
+    if status == orc.CONVERGED:
+        assert stop == full.iters
+        assert full.relres_true == _true_relres(A, b, full.x) <= tol
+    else:
+        assert stop is None and full.relres_true > tol
