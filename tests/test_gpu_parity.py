@@ -323,6 +323,34 @@ def test_full_size_128cubed_benchmark_solve(ctx, orc):
     assert same([res.relres_true], [ref.relres_true])
 
 
+def test_full_size_powerlaw_first_iterations(ctx, orc):
+    """The power-law configuration at full size (n = 2^22, about 126 M stored
+    entries, rows sorted by length, tiles claimed dynamically), in the
+    launches the benchmark times (pbcg_solve, tol 1e-300): exact p-BiCGStab
+    over 3 iterations and right-Jacobi exact p-BiCGStab over 2, the residual
+    histories and all 4,194,304 entries of x bit-identical to the oracle."""
+    import os
+    from paper_2404_13216_gb300 import pbcg
+    A = inputs.powerlaw()
+    b = inputs.rhs_ones(A)
+    nt = max(1, min(16, os.cpu_count() or 1))
+    M = ctx.upload_csr(A)
+    try:
+        for jac, its in ((False, 3), (True, 2)):
+            ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=its, alg=1, mode=1, nthreads=nt,
+                            jacobi=jac)
+            ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_JACOBI if jac else pbcg.PRECOND_NONE)
+            x = np.zeros(A.n)
+            res = ctx.solve(M, b, x, 1e-300, its, pbcg.PIPELINED, pbcg.EXACT)
+            hist = ctx.history()
+            assert res.status == ref.status and res.iters == ref.iters == its, (jac, res)
+            assert same(hist, ref.history), jac
+            assert same(x, ref.x), jac
+    finally:
+        ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_NONE)
+        M.free()
+
+
 @pytest.mark.parametrize("alg", [0, 1], ids=["bicgstab", "pbicgstab"])
 def test_powerlaw_exact_bitwise(ctx, orc, alg):
     """Random power-law rows (the rows are sorted by length inside the library
