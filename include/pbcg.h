@@ -239,6 +239,7 @@ int pbcg_pool_step(pbcg_pool *pool, int32_t iters);
  * how many were found (it can exceed cap; the rest are reported by the next
  * call).  wait != 0 first waits for the newest step.  *pending (may be NULL)
  * gets the number of steps not yet complete.
+ * Errors: INVALID (count NULL, cap < 0, or cap > 0 with slots NULL), CUDA.
  */
 int pbcg_pool_poll(pbcg_pool *pool, int wait, int32_t *slots, int32_t cap, int32_t *count, int32_t *pending);
 
@@ -254,13 +255,16 @@ int pbcg_pool_result(pbcg_pool *pool, int32_t slot, double *x, pbcg_result *out)
 
 /*
  * Residual history res_0 .. res_iters of a reported, not yet retired slot,
- * as for pbcg_residual_history.
+ * as for pbcg_residual_history (out host memory; empty for a request that
+ * ended INVALID).  Errors: INVALID (the slot was not reported or is
+ * retired), CUDA.
  */
 int pbcg_pool_history(pbcg_pool *pool, int32_t slot, double *out, int32_t cap, int32_t *len);
 
 /*
  * Free room: free slots, the largest free row range (a multiple of 256) and
- * the largest free entry range.  Any output may be NULL.
+ * the largest free entry range.  Any output may be NULL.  Errors: INVALID
+ * (pool NULL).
  */
 int pbcg_pool_room(const pbcg_pool *pool, int32_t *free_slots, int64_t *free_rows, int64_t *free_entries);
 
@@ -312,6 +316,9 @@ int pbcg_set_option(pbcg_ctx *ctx, int option, int64_t value);
  * pbcg_dot: *out = (a, b) over n entries in dot_mode (exact: correctly
  *   rounded; NaN if an operand is NaN or Inf).  a, b host or device.
  * pbcg_spmv: y = A x with the fixed fma row order.  x, y host or device.
+ * Errors: INVALID (NULL output or operand, n < 0, unknown dot_mode, a
+ * matrix not of this context), OOM (host operands of pbcg_dot are staged in
+ * device buffers freed before it returns), CUDA.  Both wait for the result.
  */
 int pbcg_dot(pbcg_ctx *ctx, int64_t n, const double *a, const double *b, int dot_mode, double *out);
 int pbcg_spmv(pbcg_ctx *ctx, const pbcg_mat *A, const double *x, double *y);
