@@ -2,8 +2,8 @@
 arXiv 2404.13216, Section 2, with plain or exactly rounded dot products.
 
 TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
-``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
-package.  It shares no code with the GPU library and never imports it.
+``cpu_baseline`` / ``--impl reference`` / ``--cpu-table`` CPU-baseline code of
+``bench.py`` may import this package.  It shares no code with the GPU library and never imports it.
 
 The arithmetic lives in ``oracle.c`` (plain C, IEEE binary64, compiled with
 ``-O2 -ffp-contract=off`` so that every fma is explicit).  This module only

@@ -55,6 +55,9 @@
  *       w_i := A r_i, p_i by its recurrence (with the new r_i),
  *       s_i := A p_i, z_i := A s_i, t_i := A w_i; the scalars are kept.  The
  *       paper gives no more detail; k = 0 is plain Algorithm 2.
+ *   R10 Right Jacobi preconditioning (orc_solve_jacobi, M = diag(A)): the
+ *       algorithms run on A M^-1 y = b and x = M^-1 y, with the forms given
+ *       above that function.
  */
 #include <math.h>
 #include <pthread.h>
