@@ -145,3 +145,75 @@ def test_fuzz_oracle_follows_rational_algorithms(orc, sysb):
                     continue     # q = 0: the rational run ends here; FP64 keeps a rounding-level q
                 w = float(c[i][key])
                 assert abs(res.trace[i, col] - w) <= 1e-9 * abs(w) + 1e-300, (alg, i, key)
+
+
+@st.composite
+def small_csr_repeats(draw):
+    """Rows whose columns repeat and come in any order: the stored order is the order of the fma chain."""
+    n = draw(st.integers(1, 10))
+    rows, cols, vals = [0], [], []
+    for _ in range(n):
+        k = draw(st.integers(0, 2 * n))
+        cs = draw(st.lists(st.integers(0, n - 1), min_size=k, max_size=k))      # with repeats, unsorted
+        cols += cs
+        vals += [draw(scaled) for _ in cs]
+        rows.append(len(cols))
+    x = [draw(scaled) for _ in range(n)]
+    return (np.array(rows, np.int32), np.array(cols, np.int32), np.array(vals, np.float64),
+            np.array(x, np.float64))
+
+
+@settings(max_examples=200, deadline=None, derandomize=True)
+@given(small_csr_repeats())
+def test_fuzz_spmv_repeated_unsorted_columns(orc, m):
+    rp, ci, va, x = m
+    got = orc.spmv(rp, ci, va, x)
+    want = fma_spmv(rp, ci, va, x)
+    assert all(same(g, w) for g, w in zip(got, want))
+
+
+@st.composite
+def split_diagonal_system(draw):
+    """A dominant integer system whose diagonal entries are +-2^k, each stored
+    as two parts at two places in its row: 5/8 of it first and 3/8 last.  The
+    parts sum to d exactly, and neither alone is a power of two, so a
+    diagonal taken from one entry cannot hide behind the exact power-of-two
+    scaling invariance of the iteration.  With b and x0."""
+    n = draw(st.integers(2, 6))
+    off = np.array([[draw(st.integers(-3, 3)) if i != j else 0 for j in range(n)] for i in range(n)])
+    k = [draw(st.integers(5, 8)) for _ in range(n)]
+    sgn = [draw(st.sampled_from([-1, 1])) for _ in range(n)]
+    d = np.array([s * 2.0 ** e for s, e in zip(sgn, k)])
+    rp, ci, va = [0], [], []
+    for i in range(n):
+        ci.append(i)
+        va.append(d[i] * 0.625)
+        for j in range(n):
+            if off[i, j] != 0:
+                ci.append(j)
+                va.append(float(off[i, j]))
+        ci.append(i)
+        va.append(d[i] * 0.375)
+        rp.append(len(ci))
+    b = np.array([float(draw(st.integers(-6, 6))) for _ in range(n)])
+    b[0] = 5.0
+    x0 = np.array([float(draw(st.integers(-2, 2))) for _ in range(n)])
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(va), d, b, x0
+
+
+@settings(max_examples=30, deadline=None, derandomize=True)
+@given(split_diagonal_system(), st.sampled_from([0, 1]))
+def test_fuzz_jacobi_sums_a_split_diagonal(orc, sysd, alg):
+    """Right Jacobi takes d_i as the sum of row i's stored diagonal entries.
+    With d_i = +-2^k stored as two parts, every scaled entry v / d_col is
+    exact, so the preconditioned solve must equal, bit for bit, the plain
+    solve of the column-scaled matrix (each stored entry scaled on its own)
+    from y0 = d x0, followed by x = y / d."""
+    rp, ci, va, d, b, x0 = sysd
+    vs = np.array([math.ldexp(abs(v), -int(math.log2(abs(d[c])))) * math.copysign(1.0, v) * math.copysign(1.0, d[c])
+                   for v, c in zip(va, ci)])
+    got = orc.solve(rp, ci, va, b, x0=x0, tol=1e-12, maxit=12, alg=alg, mode=orc.EXACT, jacobi=True)
+    ref = orc.solve(rp, ci, vs, b, x0=x0 * d, tol=1e-12, maxit=12, alg=alg, mode=orc.EXACT)
+    assert got.status == ref.status and got.iters == ref.iters
+    assert np.array_equal(got.history.view(np.int64), ref.history.view(np.int64))
+    assert np.array_equal(got.x.view(np.int64), (ref.x / d).view(np.int64))
