@@ -383,3 +383,30 @@ def test_stop_rule_true_residual_decides(orc, case):
         assert full.relres_true == _true_relres(A, b, full.x) <= tol
     else:
         assert stop is None and full.relres_true > tol
+
+
+# (name, system, tolerance): tolerances at which plain p-BiCGStab stalls on these systems
+TIGHT = [
+    ("2D 96^2, Pe 60", lambda: inputs.convdiff2d(96, 60.0), 1e-10),
+    ("3D 32^3, Pe 50", lambda: inputs.convdiff3d(32, 50.0), 1e-12),
+]
+
+
+@pytest.mark.parametrize("name,make,tol", TIGHT, ids=["2d96", "3d32"])
+def test_exact_dots_let_pipelined_reach_a_tight_tolerance(orc, name, make, tol):
+    """Section 3's observation, on synthetic systems: at a tight tolerance
+    p-BiCGStab with plain FP64 dots loses its true residual (the recursive
+    one falls below tol, the iterate drifts away) while the same iteration
+    with exactly rounded dots converges, and classical BiCGStab converges
+    with either.  A measured, deterministic fact of the oracle; exact mode is
+    bit-identical on the GPU, plain mode here is the sequential dot order."""
+    A = make()
+    b = inputs.rhs_ones(A)
+    kw = dict(tol=tol, maxit=1000, nthreads=4)
+    plain = orc.solve(A.row_ptr, A.col_idx, A.vals, b, alg=1, mode=orc.PLAIN, **kw)
+    exact = orc.solve(A.row_ptr, A.col_idx, A.vals, b, alg=1, mode=orc.EXACT, **kw)
+    assert plain.status == orc.MAXIT and plain.relres_recursive <= tol and plain.relres_true > 1e3 * tol
+    assert exact.status == orc.CONVERGED and exact.relres_true <= tol and exact.iters < 300
+    for mode in (orc.PLAIN, orc.EXACT):
+        classical = orc.solve(A.row_ptr, A.col_idx, A.vals, b, alg=0, mode=mode, **kw)
+        assert classical.status == orc.CONVERGED and classical.relres_true <= tol
