@@ -410,3 +410,23 @@ def test_exact_dots_let_pipelined_reach_a_tight_tolerance(orc, name, make, tol):
     for mode in (orc.PLAIN, orc.EXACT):
         classical = orc.solve(A.row_ptr, A.col_idx, A.vals, b, alg=0, mode=mode, **kw)
         assert classical.status == orc.CONVERGED and classical.relres_true <= tol
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_zero_rhs_uses_the_absolute_residual(orc, alg, mode):
+    """b = 0: sqrt((b,b)) is replaced by 1, so the residual is absolute.
+    x0 = 0 stops at k = 0 with res_0 = 0.  With A = 4I (n = 100) and x0 = 1,
+    r0 = -4 * 1 and res_0 = sqrt(1600) = 40 exactly; then alpha = 1/4, q = 0,
+    omega = 0 (lucky breakdown) and x = 1 + (1/4)(-4) = 0 exactly in one
+    step, with res_1 = 0."""
+    n = 100
+    A = inputs.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.full(n, 4.0))
+    b = np.zeros(n)
+    r = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-12, maxit=10, alg=alg, mode=mode)
+    assert r.status == orc.CONVERGED and r.iters == 0 and list(r.history) == [0.0]
+    assert np.all(r.x == 0.0) and r.relres_true == 0.0
+    r = orc.solve(A.row_ptr, A.col_idx, A.vals, b, x0=np.ones(n), tol=1e-12, maxit=10, alg=alg, mode=mode)
+    assert r.status == orc.CONVERGED and r.iters == 1
+    assert list(r.history) == [40.0, 0.0]
+    assert np.all(r.x == 0.0) and r.relres_true == 0.0
