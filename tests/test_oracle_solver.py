@@ -430,3 +430,37 @@ def test_zero_rhs_uses_the_absolute_residual(orc, alg, mode):
     assert r.status == orc.CONVERGED and r.iters == 1
     assert list(r.history) == [40.0, 0.0]
     assert np.all(r.x == 0.0) and r.relres_true == 0.0
+
+
+def _with_empty_row(A, p):
+    """A with an empty row (and a column nothing references) inserted at index p."""
+    rp, ci, v = [0], [], []
+    for i in range(A.n + 1):
+        if i == p:
+            rp.append(len(ci))
+        if i < A.n:
+            for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                c = int(A.col_idx[k])
+                ci.append(c + 1 if c >= p else c)
+                v.append(float(A.vals[k]))
+            rp.append(len(ci))
+    return inputs.CSR(A.n + 1, np.array(rp, np.int32), np.array(ci, np.int32), np.array(v))
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_empty_row_with_zero_rhs_changes_nothing(orc, alg, mode):
+    """An empty row i (SpMV gives +0 there) with b_i = 0 and x0_i = 0 keeps
+    r_i = 0, so every dot gains only exact zero terms: the residual history is
+    the reduced system's bit for bit, x_i stays 0 and the other entries of x
+    are the reduced solution's, wherever the row is inserted."""
+    A = inputs.convdiff2d(9, 12.0)
+    b = inputs.rhs_ones(A)
+    ref = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-11, maxit=200, alg=alg, mode=mode)
+    for p in (0, A.n // 2, A.n):
+        B = _with_empty_row(A, p)
+        bb = np.insert(b, p, 0.0)
+        got = orc.solve(B.row_ptr, B.col_idx, B.vals, bb, tol=1e-11, maxit=200, alg=alg, mode=mode)
+        assert got.status == ref.status and got.iters == ref.iters, p
+        assert np.array_equal(got.history.view(np.int64), ref.history.view(np.int64)), p
+        assert got.x[p] == 0.0 and np.array_equal(np.delete(got.x, p).view(np.int64), ref.x.view(np.int64)), p
