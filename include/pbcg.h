@@ -342,7 +342,8 @@ int pbcg_check_wait(pbcg_ctx *ctx, int32_t probes, int32_t *expired, double *sec
  * context's stream.  names receives up to cap kernel names (a
  * '\0'-terminated string each, at most 31 characters), ms their total
  * durations, launches their launch counts; *count gets the number of kernels.
- * The solve's results are those of pbcg_solve.
+ * Any of names, ms, launches and count may be NULL (that output is skipped).
+ * The solve's results, return value and errors are those of pbcg_solve.
  */
 int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double *x, double tol,
                        int32_t maxit, int alg, int dot_mode, pbcg_result *out, char (*names)[32],
