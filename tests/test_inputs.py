@@ -60,3 +60,36 @@ def test_serving_stream():
     assert 0.15 < t[-1] < 0.35
     ns = np.array([r.n for r in reqs])
     assert ns.min() >= 2 ** 2 and ns.max() <= 1.2 * (1 << 20)
+
+
+def test_recipe_distributions():
+    """The stated recipes: batched sides log-uniform in [32, 256] with Peclet
+    U(1, 100); power-law off-diagonal magnitudes spread over about eight
+    decades (N(0,1) * 10^U(-4,4)) with diagonal signs +-1 at random; the
+    serving stream half 2D / half 3D, tolerances 1e-8 or 1e-10 and exact or
+    plain dots at about one half each, n log-uniform in [4k, 1M]."""
+    B = inputs.batched_convdiff(nsys=512, seed=4)
+    s = B.sides.astype(float)
+    assert s.min() >= 32 and s.max() <= 256
+    # log-uniform: the median side sits near the geometric mean sqrt(32 * 256) = 90.5
+    assert 75 < np.median(s) < 110
+    assert B.peclet.min() >= 1.0 and B.peclet.max() <= 100.0 and 40 < B.peclet.mean() < 60
+
+    A = inputs.powerlaw(n=20000, mean_len=30, max_len=2000, seed=1)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    off = np.abs(A.vals[A.col_idx != rows])
+    lo, hi = np.percentile(np.log10(off), [5, 95])
+    assert lo < -3 and hi > 3                      # about eight decades
+    diag = A.vals[A.col_idx == rows]
+    assert diag.size == A.n and 0.45 < np.mean(diag < 0) < 0.55
+
+    reqs = inputs.serving_requests(count=2000, rate=2000.0, seed=5)
+    dims = np.array([r.dim for r in reqs])
+    tols = np.array([r.tol for r in reqs])
+    ex = np.array([r.exact for r in reqs])
+    assert set(dims) == {2, 3} and 0.45 < np.mean(dims == 3) < 0.55
+    assert set(tols) == {1e-8, 1e-10} and 0.45 < np.mean(tols == 1e-8) < 0.55
+    assert 0.45 < np.mean(ex) < 0.55
+    ln = np.log(np.array([r.n for r in reqs], dtype=float))
+    # log-uniform over [4096, 2^20] (rounded to whole grid sides): median near sqrt(4096 * 2^20) = 65536
+    assert 40000 < np.exp(np.median(ln)) < 100000
