@@ -464,3 +464,28 @@ def test_empty_row_with_zero_rhs_changes_nothing(orc, alg, mode):
         assert got.status == ref.status and got.iters == ref.iters, p
         assert np.array_equal(got.history.view(np.int64), ref.history.view(np.int64)), p
         assert got.x[p] == 0.0 and np.array_equal(np.delete(got.x, p).view(np.int64), ref.x.view(np.int64)), p
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_first_iteration_copies_keep_the_sign_of_zero(orc, mode):
+    """Reading 4: Algorithm 2 starts from p0 = r0, s0 = w0, z0 = t0 as bit
+    copies.  On an unknown that nothing couples (an empty row and column)
+    with b_p = -0 and x0_p = -0, the IEEE sign rules fix every value by hand:
+    (A v)_p = +0 for any v, so s, z, w, t, v and y stay +0 there, and with
+    alpha, omega > 0 (and beta > 0 wherever the p it forms reaches an x
+    update) the forms q = fma(-a, s, r), r = fma(-w, y, q),
+    p = fma(b, fma(-w, s, p), r) and x = fma(w, q, fma(a, p, x)) keep
+    r_p = q_p = p_p = x_p = -0 after every iteration.  Had p0 been formed as
+    fma(0, ., r0), p0_p would be +0 and x_p would turn +0 at once."""
+    A = inputs.convdiff2d(9, 12.0)
+    b = inputs.rhs_ones(A)
+    p = 5
+    B = _with_empty_row(A, p)
+    bb = np.insert(b, p, -0.0)
+    x0 = np.zeros(B.n)
+    x0[p] = -0.0
+    for its in (1, 2, 6):
+        r = orc.solve(B.row_ptr, B.col_idx, B.vals, bb, x0=x0, tol=1e-300, maxit=its, alg=1, mode=mode, trace=True)
+        # alpha, omega > 0 in every iteration run; beta > 0 where it forms a p that an x update uses
+        assert r.iters == its and np.all(r.trace[:, :2] > 0) and np.all(r.trace[:-1, 2] > 0)
+        assert r.x[p] == 0.0 and math.copysign(1.0, r.x[p]) == -1.0, its
