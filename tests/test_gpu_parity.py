@@ -511,3 +511,83 @@ def test_jacobi_batched_bitwise(ctx, orc):
             assert res[k].status == ref.status and res[k].iters == ref.iters, (jac, k)
             assert same(x[r0:r1], ref.x), (jac, k)
     M.free()
+
+
+# --------------------------------------------------------------------------- degenerate inputs
+# Written against the oracle pins of the same cases; kept skipped until they
+# have run on a GPU once.
+NOT_YET_RUN = pytest.mark.skip(reason="not yet run on a GPU")
+
+
+def _duplicated(A, rng):
+    """A with about half its rows holding one entry as two stored copies,
+    0.625 v at the row's start and 0.375 v at its end (both exact), so the
+    row's fma chain and a Jacobi diagonal meet the same column twice."""
+    rp, ci, va = [0], [], []
+    for i in range(A.n):
+        cols = list(A.col_idx[A.row_ptr[i]:A.row_ptr[i + 1]])
+        vals = list(A.vals[A.row_ptr[i]:A.row_ptr[i + 1]])
+        if rng.random() < 0.5 and cols:
+            k = int(rng.integers(len(cols)))
+            c, v = cols.pop(k), vals.pop(k)
+            cols = [c] + cols + [c]
+            vals = [v * 0.625] + vals + [v * 0.375]
+        ci += [int(c) for c in cols]
+        va += [float(v) for v in vals]
+        rp.append(len(ci))
+    return inputs.CSR(A.n, np.array(rp, np.int32), np.array(ci, np.int32), np.array(va))
+
+
+@NOT_YET_RUN
+@pytest.mark.parametrize("alg", [0, 1])
+def test_duplicate_columns_exact_bitwise(ctx, orc, alg, small_path):
+    from paper_2404_13216_gb300 import pbcg
+    A = _duplicated(inputs.convdiff2d(30, 25.0), np.random.default_rng(3))
+    b = inputs.rhs_ones(A)
+    ref, res, x, hist = run_both(ctx, orc, A, b, 1e-10, 600, alg, 1)
+    assert res.status == ref.status and res.iters == ref.iters
+    assert same(hist, ref.history) and same(x, ref.x)
+    ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_JACOBI)         # the diagonal sums its copies
+    try:
+        refj = orc.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-10, maxit=600, alg=alg, mode=1, nthreads=8,
+                         jacobi=True)
+        M = ctx.upload_csr(A)
+        xj = np.zeros(A.n)
+        rj = ctx.solve(M, b, xj, 1e-10, 600, alg, 1)
+        hj = ctx.history()
+        M.free()
+    finally:
+        ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_NONE)
+    assert rj.iters == refj.iters and same(hj, refj.history) and same(xj, refj.x)
+
+
+@NOT_YET_RUN
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_zero_rhs_and_empty_row(ctx, orc, alg, mode, small_path):
+    n = 100
+    A = inputs.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.full(n, 4.0))
+    ref, res, x, hist = run_both(ctx, orc, A, np.zeros(n), 1e-12, 10, alg, mode)
+    assert res.status == 0 and res.iters == 0 and list(hist) == [0.0] and np.all(x == 0.0)
+    ref, res, x, hist = run_both(ctx, orc, A, np.zeros(n), 1e-12, 10, alg, mode, x0=np.ones(n))
+    assert res.status == 0 and res.iters == 1 and list(hist) == [40.0, 0.0] and np.all(x == 0.0)
+    B = inputs.convdiff2d(9, 12.0)
+    b = inputs.rhs_ones(B)
+    rp, ci, va = [0], [], []
+    p = B.n // 2
+    for i in range(B.n + 1):                # an empty row and an unreferenced column at index p
+        if i == p:
+            rp.append(len(ci))
+        if i < B.n:
+            for k in range(B.row_ptr[i], B.row_ptr[i + 1]):
+                c = int(B.col_idx[k])
+                ci.append(c + 1 if c >= p else c)
+                va.append(float(B.vals[k]))
+            rp.append(len(ci))
+    E = inputs.CSR(B.n + 1, np.array(rp, np.int32), np.array(ci, np.int32), np.array(va))
+    ref, res, x, hist = run_both(ctx, orc, E, np.insert(b, p, 0.0), 1e-11, 200, alg, mode)
+    assert res.status == ref.status and res.iters == ref.iters
+    if mode == 1:
+        assert same(hist, ref.history) and same(x, ref.x)
+    else:
+        assert res.status == 0 and res.relres_true <= 1e-11
