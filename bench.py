@@ -434,6 +434,7 @@ def run_ours(args):
         "configs": configs,
         "gpu_launches": launches_e,
     }
+    line["summary"] = summary_block(line)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -441,8 +442,58 @@ def run_ours(args):
     return 0
 
 
+def summary_block(line):
+    """The headline figures again, compact, as the line's last key (a reader
+    that keeps only the end of the output still sees them)."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+    ir = line["iteration_roofline"]
+    out = {"exact_us_per_iter": g(line, "exact", "us_per_iter"), "plain_us_per_iter": g(line, "plain", "us_per_iter"),
+           "exact_over_plain": g(line, "exact_over_plain_time_per_iter"),
+           "frac_exact": g(ir, "frac_exact"), "frac_plain": g(ir, "frac_plain"), "peak_gbs": g(ir, "peak_gbs"),
+           "dominant_kernel": g(line, "roofline", "kernel"), "dominant_frac": g(line, "roofline", "frac"),
+           "e2e_iter_per_s": g(line, "e2e", "value")}
+    bt = line.get("batched")
+    if bt:
+        out["batched"] = {"solves_per_s": g(bt, "solves_per_s"), "converged": g(bt, "converged"),
+                          "converged_solves_per_s": g(bt, "converged_solves_per_s"),
+                          "one_at_a_time_solves_per_s": g(bt, "one_at_a_time_solves_per_s"),
+                          "one_at_a_time_converged_solves_per_s": g(bt, "one_at_a_time_converged_solves_per_s")}
+        rr = bt.get("residual_replacement")
+        if rr:
+            out["batched_rr50"] = {"converged": g(rr, "converged"),
+                                   "converged_solves_per_s": g(rr, "converged_solves_per_s"),
+                                   "one_at_a_time_converged": g(rr, "one_at_a_time_converged"),
+                                   "one_at_a_time_converged_solves_per_s":
+                                       g(rr, "one_at_a_time_converged_solves_per_s"),
+                                   "speedup": g(rr, "speedup")}
+    sv = line.get("serving")
+    if sv:
+        out["serving"] = {k: g(sv, k) for k in ("rate_per_s", "solves_per_s", "p50_ms", "p99_ms", "finished",
+                                                "converged", "maxit")
+                          if g(sv, k) is not None}
+        for sub in ("sub_capacity", "residual_replacement"):
+            if isinstance(sv.get(sub), dict):
+                out["serving"][sub] = {k: g(sv[sub], k) for k in ("rate_per_s", "solves_per_s", "p50_ms", "p99_ms",
+                                                                  "converged")
+                                       if g(sv[sub], k) is not None}
+    cf = line.get("configs") or {}
+    for k in ("powerlaw_pbicgstab_exact", "powerlaw_pbicgstab_plain", "convdiff64_pbicgstab_exact",
+              "convdiff64_pbicgstab_plain", "convdiff128_pbicgstab_rr50_exact"):
+        if k in cf:
+            out[k] = {"us_per_iter": g(cf, k, "us_per_iter"), "frac": g(cf, k, "frac_of_measured_hbm"),
+                      "iters": g(cf, k, "iters"), "status": g(cf, k, "status")}
+    return out
+
+
 def run_batched_rr(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, period=50):
-    """The config-4 batch solved with residual replacement every `period` iterations."""
+    """The config-4 batch solved with residual replacement every `period`
+    iterations, as one batched call and as nsys single solves (same algorithm,
+    tolerance and period), so that both arms reach the same true residual."""
     import numpy as np
     from paper_2404_13216_gb300 import inputs
     B = inputs.batched_convdiff(nsys=nsys, seed=4)
@@ -463,11 +514,38 @@ def run_batched_rr(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, perio
     torch.cuda.synchronize(dev)
     t = e0.elapsed_time(e1) * 1e-3
     M.free()
+    # one at a time: each block uploaded beforehand, then nsys solves back to back
+    singles = []
+    for k in range(nsys):
+        S = inputs.convdiff2d(int(B.sides[k]), float(B.peclet[k]))
+        r0, r1 = int(B.sys_row_ptr[k]), int(B.sys_row_ptr[k + 1])
+        singles.append((ctx.upload_csr(S), b_d[r0:r1], torch.zeros(r1 - r0, dtype=torch.float64, device=dev)))
+    for Ms, bs, xs in singles[:4]:
+        ctx.solve(Ms, bs, xs, tol, maxit, pbcg.PIPELINED_RR, 1)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    single_res = []
+    for Ms, bs, xs in singles:
+        xs.zero_()
+        single_res.append(ctx.solve(Ms, bs, xs, tol, maxit, pbcg.PIPELINED_RR, 1))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_s = e0.elapsed_time(e1) * 1e-3
+    for Ms, _, _ in singles:
+        Ms.free()
     its = np.array([r.iters for r in res])
-    return {"period": period, "solves_per_s": nsys / t, "seconds": t,
-            "converged": int(sum(r.status == 0 for r in res)),
+    conv = int(sum(r.status == 0 for r in res))
+    conv_s = int(sum(r.status == 0 for r in single_res))
+    return {"period": period, "solves_per_s": nsys / t, "seconds": t, "converged": conv,
+            "converged_solves_per_s": conv / t,
             "max_true_relres": float(max(r.relres_true for r in res)),
-            "iters_mean": float(its.mean()), "iters_max": int(its.max())}
+            "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+            "one_at_a_time_solves_per_s": nsys / t_s, "one_at_a_time_seconds": t_s,
+            "one_at_a_time_converged": conv_s, "one_at_a_time_converged_solves_per_s": conv_s / t_s,
+            "one_at_a_time_max_true_relres": float(max(r.relres_true for r in single_res)),
+            "speedup": t_s / t,
+            "identical_iterations_to_single_solves": bool(all(r.iters == q.iters
+                                                              for r, q in zip(res, single_res)))}
 
 
 def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, mode=1):
@@ -519,7 +597,9 @@ def run_batched_leg(ctx, pbcg, torch, dev, nsys=512, tol=1e-10, maxit=4000, mode
             "tol": tol, "solves_per_s": nsys / t_b, "seconds": t_b,
             "one_at_a_time_solves_per_s": nsys / t_s, "one_at_a_time_seconds": t_s,
             "speedup": t_s / t_b, "converged": int(sum(r.status == 0 for r in res)),
+            "converged_solves_per_s": int(sum(r.status == 0 for r in res)) / t_b,
             "one_at_a_time_converged": int(sum(r.status == 0 for r in single_res)),
+            "one_at_a_time_converged_solves_per_s": int(sum(r.status == 0 for r in single_res)) / t_s,
             "max_true_relres": float(max(r.relres_true for r in res)),
             "iters_mean": float(its.mean()), "iters_max": int(its.max()), "maxit": maxit,
             "status_counts": {str(k): int(sum(r.status == k for r in res)) for k in range(4)},

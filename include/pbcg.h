@@ -367,13 +367,15 @@ int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double
  * 70,144 bytes that every GPU loading this library holds until the process
  * exits.  Every call on a device shares it and clears it first; calls that
  * overlap on the GPU (other streams, other host threads) race on it and give
- * wrong results, so serialise them.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and the occupancy of its
- * kernels, with that device current; make that first call before any stream
- * capture.
+ * wrong results, so serialise them.  Every call looks up the array's device
+ * address (cudaGetSymbolAddress, which allocates nothing) with the current
+ * device; the first call on a device also reads the occupancy of its
+ * kernels.  Make that first call before any stream capture.
  *
  * Limits: 0 <= n <= 2^31 - 1 (INVALID beyond); at most 2048 CTAs per call.
- * Errors: INVALID (bad size, NULL pointer, unknown dot_mode), CUDA.
+ * Errors: INVALID (bad size, NULL pointer, unknown dot_mode, or a, b or out
+ * not device memory of the current device, as cudaPointerGetAttributes
+ * reports it; nothing is launched then), CUDA.
  */
 int pbcg_dot_noalloc(int64_t n, const double *a, const double *b, int dot_mode, double *out, void *cuda_stream);
 

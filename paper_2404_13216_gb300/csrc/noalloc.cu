@@ -35,7 +35,6 @@ namespace {
 constexpr int MAXDEV = 64;
 std::mutex g_mu;
 bool g_ready[MAXDEV];
-unsigned char *g_ptr[MAXDEV];
 int g_sms[MAXDEV];
 int g_occ[MAXDEV][2];
 
@@ -87,15 +86,13 @@ __global__ void __launch_bounds__(THREADS) k_noalloc_dot(long long n, const doub
         *out = sh.dv[0];
 }
 
-// once per device, with that device current: the device address of the scratch array
+// once per device, with that device current: the SM count and the occupancy
+// of the two dot kernels (neither changes while the process runs)
 int noalloc_setup(int dev)
 {
     std::lock_guard<std::mutex> lock(g_mu);
     if (g_ready[dev])
         return 0;
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
-        return PBCG_ERR_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         return PBCG_ERR_CUDA;
@@ -107,10 +104,21 @@ int noalloc_setup(int dev)
             return PBCG_ERR_CUDA;
         g_occ[dev][m] = o;
     }
-    g_ptr[dev] = static_cast<unsigned char *>(p);
     g_sms[dev] = sms;
     g_ready[dev] = true;
     return 0;
+}
+
+// true when p is device (or managed) memory that device `dev` owns; the
+// query allocates nothing
+bool on_device(const void *p, int dev)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -127,9 +135,18 @@ extern "C" int pbcg_dot_noalloc(int64_t n, const double *a, const double *b, int
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV)
         return PBCG_ERR_CUDA;
+    if ((n > 0 && (!on_device(a, dev) || !on_device(b, dev))) || !on_device(out, dev))
+        return PBCG_ERR_INVALID;
     int rc = noalloc_setup(dev);
     if (rc)
         return rc;
+    // the array's device address, looked up on every call (it allocates
+    // nothing), so that a module reloaded after a device reset is followed
+    void *sym = nullptr;
+    if (cudaGetSymbolAddress(&sym, g_noalloc_scratch) != cudaSuccess || !sym) {
+        cudaGetLastError();
+        return PBCG_ERR_CUDA;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     long long tiles = (n + 31) / 32;
     long long need = (tiles + WARPS - 1) / WARPS;
@@ -140,7 +157,7 @@ extern "C" int pbcg_dot_noalloc(int64_t n, const double *a, const double *b, int
         grid = NOALLOC_MAXGRID;
     if (grid < 1)
         grid = 1;
-    unsigned char *base = g_ptr[dev];
+    unsigned char *base = static_cast<unsigned char *>(sym);
     k_noalloc_init<<<1, THREADS, 0, st>>>(base);
     Work *wk = reinterpret_cast<Work *>(base);
     long long nn = n;

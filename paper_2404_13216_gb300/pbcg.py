@@ -160,11 +160,31 @@ def _csr(row_ptr, col_idx, vals):
     return rp, ci, va, n, nnz
 
 
+def _cuda_f64(t, name: str):
+    """A contiguous float64 CUDA tensor on the current device (pbcg_dot_noalloc
+    takes device memory only and reads or writes it without a copy)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (device memory)")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 tensor, got {t.dtype}"
+                        + ("" if t.is_contiguous() else " (not contiguous)"))
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, the current device is cuda:{torch.cuda.current_device()}")
+    return t
+
+
 def dot_noalloc(a, b, out, mode: int = EXACT, stream=None) -> int:
-    """pbcg_dot_noalloc: (a, b) into out[0]; a, b, out are CUDA tensors on the
-    current device.  Asynchronous on `stream` (a raw cudaStream_t or None).
-    Returns the library's status code (0 or negative)."""
+    """pbcg_dot_noalloc: (a, b) into out[0]; a, b, out are contiguous float64
+    CUDA tensors on the current device, b as long as a.  Asynchronous on
+    `stream` (a raw cudaStream_t or None).  Returns the library's status code
+    (0 or negative)."""
+    a, b, out = _cuda_f64(a, "a"), _cuda_f64(b, "b"), _cuda_f64(out, "out")
     n = a.numel()
+    if b.numel() != n:
+        raise ValueError(f"b has {b.numel()} entries, expected {n}")
+    if out.numel() < 1:
+        raise ValueError("out needs at least one entry")
     s = ctypes.c_void_p(stream) if stream else None
     return _lib.pbcg_dot_noalloc(n, _ptr(a), _ptr(b), int(mode), _ptr(out), s)
 

@@ -82,3 +82,15 @@ def test_pool_admit_and_result_lengths(pbcg):
         pool.admit(bad, np.ones(25))
     with pytest.raises(ValueError):
         pool.result(0, np.zeros(24))
+
+
+def test_dot_noalloc_takes_device_tensors_only(pbcg):
+    """pbcg_dot_noalloc reads and writes device memory in place: host arrays
+    and host tensors are refused before the library is called."""
+    torch = pytest.importorskip("torch")
+    a = np.ones(8)
+    with pytest.raises(TypeError):
+        pbcg.dot_noalloc(a, a, np.zeros(1))
+    t = torch.ones(8, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        pbcg.dot_noalloc(t, t, torch.zeros(1, dtype=torch.float64))

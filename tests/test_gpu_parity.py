@@ -514,9 +514,7 @@ def test_jacobi_batched_bitwise(ctx, orc):
 
 
 # --------------------------------------------------------------------------- degenerate inputs
-# Written against the oracle pins of the same cases; kept skipped until they
-# have run on a GPU once.
-NOT_YET_RUN = pytest.mark.skip(reason="not yet run on a GPU")
+# Written against the oracle pins of the same cases.
 
 
 def _duplicated(A, rng):
@@ -538,7 +536,6 @@ def _duplicated(A, rng):
     return inputs.CSR(A.n, np.array(rp, np.int32), np.array(ci, np.int32), np.array(va))
 
 
-@NOT_YET_RUN
 @pytest.mark.parametrize("alg", [0, 1])
 def test_duplicate_columns_exact_bitwise(ctx, orc, alg, small_path):
     from paper_2404_13216_gb300 import pbcg
@@ -561,7 +558,6 @@ def test_duplicate_columns_exact_bitwise(ctx, orc, alg, small_path):
     assert rj.iters == refj.iters and same(hj, refj.history) and same(xj, refj.x)
 
 
-@NOT_YET_RUN
 @pytest.mark.parametrize("alg", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_zero_rhs_and_empty_row(ctx, orc, alg, mode, small_path):

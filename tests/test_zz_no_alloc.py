@@ -4,6 +4,8 @@ a loop that must not enter the allocator).  It takes device inputs and a
 device output, keeps its merge state in a fixed static device array, and must
 agree with the context-based pbcg_dot: bit for bit in exact mode, within the
 plain-dot tolerance of the other tests in plain mode, on two calls in a row.
+In exact mode it is also held to the CPU oracle's correctly rounded dot on
+the adversarial cases and the random exponent sweep of the parity tests.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test; it also passes on its own in a fresh process.
@@ -53,6 +55,55 @@ def test_noalloc_matches_context_dot_twice(env, n):
         assert abs(got_plain - want_plain) <= 1e-12 * float(np.abs(a * b).sum()) + 0.0
 
 
+def _exact_noalloc(torch, pbcg, a, b):
+    da = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    db = torch.from_numpy(np.ascontiguousarray(b, dtype=np.float64)).cuda()
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    assert pbcg.dot_noalloc(da, db, out, pbcg.EXACT) == 0
+    torch.cuda.synchronize()
+    return float(out.item())
+
+
+def _same(got, want):
+    if math.isnan(want):
+        return math.isnan(got)
+    return np.array_equal(np.array([got]).view(np.int64), np.array([want]).view(np.int64))
+
+
+def test_noalloc_exact_matches_oracle_adversarial(env, orc):
+    """Cancellation, ties, subnormal results, products whose FMA error term
+    underflows, overflow: every case correctly rounded, as the oracle's
+    big-integer sum gives it."""
+    from tests import dotcases
+    torch, pbcg, ctx = env
+    for name, a, b in dotcases.cases(0):
+        got = _exact_noalloc(torch, pbcg, a, b)
+        assert _same(got, orc.dot_exact(a, b)), name
+
+
+def test_noalloc_exact_matches_oracle_sweep(env, orc):
+    """60 seeded cases: ragged lengths, exponent spans from narrow to the
+    whole double range, exact zeros and planted cancellation."""
+    torch, pbcg, ctx = env
+    rng = np.random.default_rng(77)
+    for case in range(60):
+        n = int(rng.integers(1, 5000))
+        lo = int(rng.integers(-1074, 900))
+        hi = int(min(1000, lo + rng.integers(0, 2000)))
+        ea = rng.integers(lo, hi + 1, n) // 2
+        eb = rng.integers(lo, hi + 1, n) - ea
+        a = np.ldexp(rng.uniform(0.5, 1.0, n), ea) * rng.choice([-1.0, 1.0], n)
+        b = np.ldexp(rng.uniform(0.5, 1.0, n), np.clip(eb, -1074, 1000)) * rng.choice([-1.0, 1.0], n)
+        a[rng.random(n) < 0.05] = 0.0
+        if case % 3 == 0 and n > 1:
+            h = n // 2
+            a[h:2 * h] = -a[:h]
+            b[h:2 * h] = b[:h]
+        got = _exact_noalloc(torch, pbcg, a, b)
+        want = orc.dot_exact(a, b, nthreads=4)
+        assert _same(got, want) or (got == 0.0 and want == 0.0), (case, n, got, want)
+
+
 def test_noalloc_nonfinite_then_clean(env):
     torch, pbcg, ctx = env
     a = torch.ones(100, dtype=torch.float64, device="cuda")
@@ -79,4 +130,25 @@ def test_noalloc_rejects_bad_arguments(env):
     assert lib.pbcg_dot_noalloc(4, None, pbcg._ptr(a), 1, pbcg._ptr(out), None) == pbcg.ERR_INVALID
     assert lib.pbcg_dot_noalloc(4, pbcg._ptr(a), pbcg._ptr(a), 1, None, None) == pbcg.ERR_INVALID
     assert lib.pbcg_dot_noalloc(4, pbcg._ptr(a), pbcg._ptr(a), 5, pbcg._ptr(out), None) == pbcg.ERR_INVALID
-    del ctypes
+    # host memory is refused by the library itself (checked before any launch)
+    h = np.ones(4)
+    hp = h.ctypes.data_as(ctypes.c_void_p)
+    assert lib.pbcg_dot_noalloc(4, hp, pbcg._ptr(a), 1, pbcg._ptr(out), None) == pbcg.ERR_INVALID
+    assert lib.pbcg_dot_noalloc(4, pbcg._ptr(a), hp, 1, pbcg._ptr(out), None) == pbcg.ERR_INVALID
+    ho = np.zeros(1)
+    assert lib.pbcg_dot_noalloc(4, pbcg._ptr(a), pbcg._ptr(a), 1, ho.ctypes.data_as(ctypes.c_void_p),
+                                None) == pbcg.ERR_INVALID
+    assert ho[0] == 0.0
+    # the binding refuses what the library would misread
+    with pytest.raises(TypeError):
+        pbcg.dot_noalloc(a.float(), a.float(), out)
+    with pytest.raises(TypeError):
+        pbcg.dot_noalloc(torch.ones(8, dtype=torch.float64, device="cuda")[::2], a, out)
+    with pytest.raises(ValueError):
+        pbcg.dot_noalloc(a, a[:3], out)
+    with pytest.raises(ValueError):
+        pbcg.dot_noalloc(a, a, out[:0])
+    # and the entry point still works after the refusals
+    assert pbcg.dot_noalloc(a, a, out, pbcg.EXACT) == 0
+    torch.cuda.synchronize()
+    assert out.item() == 4.0
