@@ -49,7 +49,8 @@ enum {
     PBCG_ERR_INVALID = -1,  /* bad argument; nothing was launched */
     PBCG_ERR_OOM = -2,      /* device allocation failed */
     PBCG_ERR_CUDA = -3,     /* a CUDA call failed */
-    PBCG_ERR_TIMEOUT = -4   /* a bounded device wait expired */
+    PBCG_ERR_TIMEOUT = -4,  /* a bounded device wait expired */
+    PBCG_ERR_COMM = -5      /* a communicator callback of a partitioned solve failed */
 };
 
 enum { PBCG_ALG_BICGSTAB = 0, PBCG_ALG_PIPELINED = 1, PBCG_ALG_PIPELINED_RR = 2 };
@@ -378,6 +379,95 @@ int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double
  * reports it; nothing is launched then), CUDA.
  */
 int pbcg_dot_noalloc(int64_t n, const double *a, const double *b, int dot_mode, double *out, void *cuda_stream);
+
+/*
+ * Row-partitioned solves (Section 2: the method runs on distributed memory,
+ * each process owning a block of rows, with the dot products as global
+ * reductions; Tables 2 and 3: with ExBLAS dots the iteration counts do not
+ * change with the number of processes).
+ *
+ * Each of nranks ranks (one GPU, or one context, each) owns the contiguous
+ * global rows [row_starts[rank], row_starts[rank+1]) of A, b and x.  Before a
+ * pass whose SpMV gathers a vector, the entries of it that the rank's columns
+ * need from other ranks (the halo) are exchanged; at every reduction point
+ * each rank forms its share of the dots (exact mode: the integer digits of
+ * its long accumulator; plain mode: its partial sums), the shares are added
+ * over the ranks by one collective, and every rank rounds the same total
+ * once.  Exact-mode results -- residual history, iteration count, status and
+ * every rank's block of x -- are therefore bit-identical to pbcg_solve of the
+ * whole system whatever nranks and row_starts are.  Plain mode adds the
+ * ranks' partial sums in rank order: deterministic for a given partition,
+ * not across partitions.
+ *
+ * The library does not talk to other ranks itself: the caller supplies the
+ * two collectives, on host memory, over any transport (MPI, NCCL, gloo, ...).
+ * Every rank must make the same sequence of calls; each callback returns 0,
+ * or nonzero to fail the calling entry point with PBCG_ERR_COMM.
+ *   allreduce_sum_i64: buf[0 .. count-1] := the sum over all ranks of every
+ *     rank's buf (two's complement int64 addition, in place);
+ *   alltoallv: rank r sends the send_bytes[k] bytes at send + send_displs[k]
+ *     to rank k and receives recv_bytes[k] bytes from rank k at
+ *     recv + recv_displs[k] (byte counts and offsets; zero counts allowed).
+ * A rank that fails leaves the others waiting in their next collective until
+ * the transport's own timeout ends it; arguments are checked on every rank
+ * and agreed with one allreduce before any other exchange, so bad arguments
+ * fail on all ranks together.
+ */
+typedef struct {
+    void *user;
+    int (*allreduce_sum_i64)(void *user, int64_t *buf, int64_t count);
+    int (*alltoallv)(void *user, const void *send, const int64_t *send_bytes, const int64_t *send_displs,
+                     void *recv, const int64_t *recv_bytes, const int64_t *recv_displs);
+} pbcg_comm;
+
+typedef struct pbcg_part pbcg_part;   /* opaque, library-owned: one rank's block */
+
+/*
+ * The halo of one rank's row block, on the host only (no CUDA call): the
+ * global columns outside [row_starts[rank], row_starts[rank+1]) that the
+ * block's rows reference, sorted ascending (so grouped by owning rank), and
+ * for every rank k the number of them that rank k owns.  row_ptr[nloc+1],
+ * col_idx[nnz] hold the block in CSR with global column indices.
+ * halo_cols (capacity cap, may be NULL), recv_counts[nranks] (may be NULL)
+ * and local_col[nnz] (may be NULL) receive the halo, the counts and each
+ * entry's column in the rank's local numbering (own columns c - row0, halo
+ * column h at nloc + h); *nhalo gets the halo's length (which may exceed cap).
+ * Validation (INVALID): 1 <= nranks, 0 <= rank < nranks, row_starts[0] == 0,
+ * row_starts non-decreasing, the rank's block non-empty, row_ptr[0] == 0,
+ * non-decreasing, row_ptr[nloc] == nnz, 0 <= col_idx < row_starts[nranks].
+ */
+int pbcg_part_plan(int32_t nranks, int32_t rank, const int32_t *row_starts, int64_t nnz, const int32_t *row_ptr,
+                   const int32_t *col_idx, int32_t *nhalo, int32_t *halo_cols, int32_t cap, int32_t *recv_counts,
+                   int32_t *local_col);
+
+/*
+ * Create this rank's block on ctx's device (collective: every rank calls it
+ * with the same nranks and row_starts).  row_ptr, col_idx (global column
+ * indices) and vals describe the block's rows as for pbcg_part_plan; host or
+ * device pointers; the library copies them.  One alltoallv tells every rank
+ * which of its entries the others gather.  The block must be destroyed before
+ * ctx.  Errors: INVALID (validation as for pbcg_part_plan, on any rank, or a
+ * halo request outside the receiving rank's rows), OOM, CUDA, COMM.
+ */
+int pbcg_part_create(pbcg_ctx *ctx, const pbcg_comm *comm, int32_t nranks, int32_t rank, const int32_t *row_starts,
+                     int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx, const double *vals,
+                     pbcg_part **out);
+
+/*
+ * Solve A x = b over all ranks (collective).  b and x hold this rank's block
+ * (row_starts[rank+1] - row_starts[rank] doubles, host or device; x: x_0 in,
+ * the block of the last iterate out).  tol, maxit, dot_mode and the stopping
+ * rule as for pbcg_solve; alg: PBCG_ALG_BICGSTAB or PBCG_ALG_PIPELINED (no
+ * residual replacement or preconditioner).  Launches are driven from the
+ * host, one pass at a time.  The residual history goes to the block's
+ * context (pbcg_residual_history with sys = 0).  Returns the status (the
+ * same on every rank) or an error.
+ */
+int pbcg_part_solve(pbcg_part *part, const double *b, double *x, double tol, int32_t maxit, int alg, int dot_mode,
+                    pbcg_result *out);
+
+/* Free a block (not collective).  destroy(NULL) is a no-op. */
+void pbcg_part_destroy(pbcg_part *part);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpbcg.so")
 SOURCES = ["api.cu", "noalloc.cu"]
-HEADERS = ["exdot.cuh", "kernels.cuh", "tma.cuh", "batched.cuh", "cluster.cuh"]
+HEADERS = ["exdot.cuh", "kernels.cuh", "tma.cuh", "batched.cuh", "cluster.cuh", "dist.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

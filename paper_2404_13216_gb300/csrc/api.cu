@@ -24,6 +24,7 @@
 #include "../../include/pbcg.h"
 #include "batched.cuh"
 #include "cluster.cuh"
+#include "dist.cuh"
 
 using namespace pbcg;
 
@@ -279,10 +280,9 @@ void free_ws(Workspace &ws)
     ws = Workspace();
 }
 
-// make sure the workspace holds n-vectors and a history of hist_cap entries
-int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
+// make sure workspace ws holds n-vectors and a history of hist_cap entries
+int ensure_ws_in(pbcg_ctx *ctx, Workspace &ws, long long n, int hist_cap)
 {
-    Workspace &ws = ctx->ws;
     if (!ws.base_ready) {
         // each buffer is taken only if missing, so a call after an allocation
         // failure completes the set instead of running with a null one
@@ -332,6 +332,11 @@ int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
     return 0;
 }
 
+int ensure_ws(pbcg_ctx *ctx, long long n, int hist_cap)
+{
+    return ensure_ws_in(ctx, ctx->ws, n, hist_cap);
+}
+
 // SELL-32 layout of a CSR matrix (host side), with an optional row order
 // sorted by length when that saves padding.  Up to SELL_GLOBAL rows (their
 // gathered vectors fit easily in L2) the sort is global, so the longest rows
@@ -351,7 +356,10 @@ struct Sell {
     std::vector<double> va;
 };
 
-bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val, Sell &S)
+// ncols > n: a rectangular matrix whose columns n .. ncols - 1 keep their
+// index (the halo of a row-partitioned solve); rows and the first n columns
+// share the solver order
+bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val, Sell &S, int ncols = 0)
 {
     int ns = (n + 31) / 32;
     S.nslices = ns;
@@ -385,9 +393,11 @@ bool build_sell(int n, const int32_t *rp, const int32_t *col, const double *val,
         }
         S.permuted = true;
     }
-    std::vector<int> inv(n);
+    std::vector<int> inv((size_t)std::max(n, ncols));
     for (int p = 0; p < n; p++)
         inv[S.perm[p]] = p;
+    for (int c = n; c < ncols; c++)
+        inv[(size_t)c] = c;
     S.sl_off.assign(ns + 1, 0);
     long long off = 0;
     for (int s = 0; s < ns; s++) {
@@ -597,9 +607,9 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, Loop
     return 0;
 }
 
-int read_ctl(pbcg_ctx *ctx)
+int read_ctl(pbcg_ctx *ctx, const Ctl *dev_ctl = nullptr)
 {
-    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_ctl, dev_ctl ? dev_ctl : ctx->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return 0;
 }
@@ -745,14 +755,15 @@ int jacobi_vec(pbcg_ctx *ctx, const pbcg_mat *m, double *x, bool to_scaled)
     return 0;
 }
 
-int vec_in(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst)
+int vec_in(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst, double *tmp = nullptr)
 {
     size_t bytes = sizeof(double) * (size_t)m->n;
     if (!m->perm) {
         CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
         return 0;
     }
-    double *tmp = ctx->ws.vec[V_TMP];
+    if (!tmp)
+        tmp = ctx->ws.vec[V_TMP];
     CK(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyDefault, ctx->stream));
     int n = m->n;
     const int *pm = m->perm;
@@ -762,14 +773,15 @@ int vec_in(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst)
 }
 
 // solver-order device vector -> caller-order vector (host or device)
-int vec_out(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst)
+int vec_out(pbcg_ctx *ctx, const pbcg_mat *m, const double *src, double *dst, double *tmp = nullptr)
 {
     size_t bytes = sizeof(double) * (size_t)m->n;
     if (!m->perm) {
         CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
         return 0;
     }
-    double *tmp = ctx->ws.vec[V_TMP];
+    if (!tmp)
+        tmp = ctx->ws.vec[V_TMP];
     int n = m->n;
     const int *pm = m->perm;
     void *args[4] = {&n, &pm, &src, &tmp};
@@ -1785,6 +1797,414 @@ int pool_build_graph(pbcg_ctx *ctx, pbcg_pool *P)
     return 0;
 }
 
+// SELL-32 device copy of a validated host CSR matrix with n rows (ncols > n:
+// the columns n .. ncols - 1 are a halo, see build_sell); not registered in
+// ctx->mats
+int make_mat(pbcg_ctx *ctx, int n, int ncols, std::vector<int32_t> &&hrp, std::vector<int32_t> &&hci,
+             std::vector<double> &&hva, pbcg_mat **out)
+{
+    const long long nnz = (long long)hci.size();
+    Sell S;
+    if (!build_sell(n, hrp.data(), hci.data(), hva.data(), S, ncols))
+        return fail(ctx, PBCG_ERR_INVALID, "padded matrix exceeds 2^31 entries");
+    pbcg_mat *m = new pbcg_mat();
+    m->n = n;
+    m->nnz = nnz;
+    m->nslices = S.nslices;
+    m->padded = S.padded;
+    m->sl_off = m->rlen = m->ci = m->perm = m->tmeta = nullptr;
+    m->lci = nullptr;
+    m->va = nullptr;
+    m->narrow = S.narrow;
+    m->bl = nullptr;
+    m->h_sloff.assign(S.sl_off.begin(), S.sl_off.begin() + (S.nslices + 1));
+    m->h_rp = std::move(hrp);
+    m->h_ci = std::move(hci);
+    m->h_va = std::move(hva);
+    size_t P = (size_t)(S.padded ? S.padded : 1);
+    cudaError_t e = cudaMalloc(&m->sl_off, sizeof(int) * S.sl_off.size());
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->rlen, sizeof(int) * S.rlen.size());
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->ci, sizeof(int) * P);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->va, sizeof(double) * P);
+    if (e == cudaSuccess && S.permuted)
+        e = cudaMalloc(&m->perm, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->lci, sizeof(uint16_t) * P);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&m->tmeta, sizeof(int) * S.tmeta.size());
+    if (e == cudaSuccess && S.padded)
+        e = cudaMemcpy(m->lci, S.lci.data(), sizeof(uint16_t) * (size_t)S.padded, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->tmeta, S.tmeta.data(), sizeof(int) * S.tmeta.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->sl_off, S.sl_off.data(), sizeof(int) * S.sl_off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(m->rlen, S.rlen.data(), sizeof(int) * S.rlen.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && S.padded)
+        e = cudaMemcpy(m->ci, S.ci.data(), sizeof(int) * (size_t)S.padded, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && S.padded)
+        e = cudaMemcpy(m->va, S.va.data(), sizeof(double) * (size_t)S.padded, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && S.permuted)
+        e = cudaMemcpy(m->perm, S.perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        mat_release(m);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "matrix upload: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = m;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// row-partitioned solves (one rank's block; see pbcg_part_* in pbcg.h)
+// ---------------------------------------------------------------------------
+// Host plan of one block: its halo (external columns, ascending, hence grouped
+// by owner), how many of them each rank owns, and every entry's local column.
+int part_plan_host(int nranks, int rank, const int32_t *rs, long long nnz, const int32_t *rp, const int32_t *ci,
+                   std::vector<int32_t> &halo, std::vector<int32_t> &recv_counts, std::vector<int32_t> *local,
+                   std::string &why)
+{
+    char buf[200];
+    if (nranks < 1 || rank < 0 || rank >= nranks) {
+        why = "need 1 <= nranks and 0 <= rank < nranks";
+        return PBCG_ERR_INVALID;
+    }
+    if (rs[0] != 0) {
+        why = "row_starts[0] must be 0";
+        return PBCG_ERR_INVALID;
+    }
+    for (int k = 0; k < nranks; k++)
+        if (rs[k + 1] < rs[k]) {
+            snprintf(buf, sizeof buf, "row_starts decreases at rank %d", k);
+            why = buf;
+            return PBCG_ERR_INVALID;
+        }
+    const int row0 = rs[rank], nloc = rs[rank + 1] - rs[rank], nglob = rs[nranks];
+    if (nloc < 1 || nloc > INT32_MAX / 2) {
+        why = "the rank's block must hold 1 .. 2^30 - 1 rows";
+        return PBCG_ERR_INVALID;
+    }
+    if (nnz < 0 || nnz >= (1ll << 31) || rp[0] != 0 || (long long)rp[nloc] != nnz) {
+        why = "row_ptr must start at 0 and end at nnz < 2^31";
+        return PBCG_ERR_INVALID;
+    }
+    for (int i = 0; i < nloc; i++)
+        if (rp[i + 1] < rp[i]) {
+            snprintf(buf, sizeof buf, "row_ptr decreases at local row %d", i);
+            why = buf;
+            return PBCG_ERR_INVALID;
+        }
+    for (long long k = 0; k < nnz; k++)
+        if (ci[k] < 0 || ci[k] >= nglob) {
+            snprintf(buf, sizeof buf, "col_idx[%lld] = %d outside [0, %d)", k, ci[k], nglob);
+            why = buf;
+            return PBCG_ERR_INVALID;
+        }
+    halo.clear();
+    for (long long k = 0; k < nnz; k++)
+        if (ci[k] < row0 || ci[k] >= row0 + nloc)
+            halo.push_back(ci[k]);
+    std::sort(halo.begin(), halo.end());
+    halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+    if ((long long)nloc + (long long)halo.size() > INT32_MAX / 2) {
+        why = "rows plus halo exceed 2^30 - 1";
+        return PBCG_ERR_INVALID;
+    }
+    recv_counts.assign((size_t)nranks, 0);
+    int owner = 0;
+    for (int32_t c : halo) {
+        while (c >= rs[owner + 1])
+            owner++;
+        recv_counts[(size_t)owner]++;
+    }
+    if (local) {
+        local->resize((size_t)nnz);
+        for (long long k = 0; k < nnz; k++) {
+            const int32_t c = ci[k];
+            (*local)[(size_t)k] = (c >= row0 && c < row0 + nloc)
+                                      ? c - row0
+                                      : nloc + (int32_t)(std::lower_bound(halo.begin(), halo.end(), c) - halo.begin());
+        }
+    }
+    return 0;
+}
+
+}  // namespace
+
+struct pbcg_part {
+    pbcg_ctx *ctx = nullptr;
+    pbcg_comm comm{};
+    int nranks = 1, rank = 0, row0 = 0, nloc = 0, nhalo = 0, nsend = 0;
+    pbcg_mat *m = nullptr;                       // rows nloc, columns nloc + nhalo (local numbering)
+    Workspace ws;                                // vectors hold the halo after the block's rows
+    std::vector<int64_t> sb, sd, rb, rd;         // alltoallv byte counts and offsets of a halo exchange
+    int *d_send_idx = nullptr;                   // [nsend] solver-order rows the other ranks gather
+    double *d_send = nullptr;                    // [nsend]
+    double *h_send = nullptr, *h_recv = nullptr; // pinned
+    long long *h_red = nullptr, *d_red = nullptr;
+    GAcc *h_g = nullptr;                         // pinned copy of the block's global accumulators
+    double *h_loc = nullptr;
+    int *h_err = nullptr;
+    int red_cap = 0;
+};
+
+namespace {
+
+void part_release(pbcg_part *P)
+{
+    if (!P)
+        return;
+    if (P->m)
+        mat_release(P->m);
+    free_ws(P->ws);
+    cudaFree(P->d_send_idx);
+    cudaFree(P->d_send);
+    cudaFree(P->d_red);
+    cudaFreeHost(P->h_send);
+    cudaFreeHost(P->h_recv);
+    cudaFreeHost(P->h_red);
+    cudaFreeHost(P->h_g);
+    cudaFreeHost(P->h_loc);
+    cudaFreeHost(P->h_err);
+    delete P;
+}
+
+// every rank's flag summed: nonzero when any rank reported a problem
+int comm_any(pbcg_ctx *ctx, const pbcg_comm &cm, long long flag, long long *sum)
+{
+    int64_t v = flag;
+    if (cm.allreduce_sum_i64(cm.user, &v, 1) != 0)
+        return fail(ctx, PBCG_ERR_COMM, "allreduce callback failed");
+    *sum = v;
+    return 0;
+}
+
+// copy the entries of solver vector v that other ranks need to them, and
+// theirs into v's halo (after the block's rows)
+int part_halo(pbcg_part *P, double *v)
+{
+    pbcg_ctx *ctx = P->ctx;
+    if (P->nranks == 1)
+        return 0;
+    if (P->nsend > 0) {
+        int m = P->nsend;
+        const int *idx = P->d_send_idx;
+        double *out = P->d_send;
+        void *args[4] = {&m, (void *)&idx, &v, &out};
+        CK(cudaLaunchKernel((void *)k_halo_pack, dim3(std::min(ctx->num_sms * 4, (m + 255) / 256)), dim3(256), args,
+                            0, ctx->stream));
+        CK(cudaMemcpyAsync(P->h_send, P->d_send, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (P->comm.alltoallv(P->comm.user, P->h_send, P->sb.data(), P->sd.data(), P->h_recv, P->rb.data(),
+                          P->rd.data()) != 0)
+        return fail(ctx, PBCG_ERR_COMM, "alltoallv callback failed (halo exchange)");
+    if (P->nhalo > 0)
+        CK(cudaMemcpyAsync(v + P->nloc, P->h_recv, sizeof(double) * (size_t)P->nhalo, cudaMemcpyHostToDevice,
+                           ctx->stream));
+    return 0;
+}
+
+// the reduction point after a pass with nd dots: add the ranks' shares and
+// run k_dist_finish (rounding and the scalar step `which`)
+int part_reduce(pbcg_part *P, int nd, int mode, int which)
+{
+    pbcg_ctx *ctx = P->ctx;
+    Work *wk = P->ws.wk;
+    if (mode)
+        CK(cudaMemcpyAsync(P->h_g, wk->g, sizeof(GAcc) * (size_t)nd, cudaMemcpyDeviceToHost, ctx->stream));
+    else
+        CK(cudaMemcpyAsync(P->h_loc, wk->loc, sizeof(double) * (size_t)nd, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(P->h_err, &P->ws.ctl->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int words = mode ? 1 + nd * RED_EXACT_STRIDE : 1 + P->nranks * nd;
+    long long *r = P->h_red;
+    memset(r, 0, sizeof(long long) * (size_t)words);
+    r[0] = *P->h_err ? 1 : 0;
+    if (mode) {
+        for (int d = 0; d < nd; d++) {
+            const GAcc &g = P->h_g[d];
+            for (int k = 0; k < NDIG; k++)
+                r[1 + d * RED_EXACT_STRIDE + k] = (k >= g.kmin && k <= g.kmax) ? (long long)g.dig[k] : 0ll;
+            r[1 + d * RED_EXACT_STRIDE + NDIG] = g.nf ? 1 : 0;
+        }
+    } else {
+        for (int d = 0; d < nd; d++) {
+            long long bits;
+            memcpy(&bits, &P->h_loc[d], sizeof bits);
+            r[1 + P->rank * nd + d] = bits;
+        }
+    }
+    if (P->nranks > 1 && P->comm.allreduce_sum_i64(P->comm.user, reinterpret_cast<int64_t *>(r), words) != 0)
+        return fail(ctx, PBCG_ERR_COMM, "allreduce callback failed (dot products)");
+    CK(cudaMemcpyAsync(P->d_red, r, sizeof(long long) * (size_t)words, cudaMemcpyHostToDevice, ctx->stream));
+    Ctl *c = P->ws.ctl;
+    const long long *red = P->d_red;
+    int nranks = P->nranks;
+    void *args[6] = {&c, &wk, (void *)&red, &nd, &nranks, &which};
+    CK(cudaLaunchKernel(mode ? (void *)k_dist_finish<1> : (void *)k_dist_finish<0>, dim3(1), dim3(THREADS), args, 0,
+                        ctx->stream));
+    return 0;
+}
+
+int part_solve_impl(pbcg_part *P, const double *b, double *x, double tol, int32_t maxit, int alg, int mode,
+                    pbcg_result *out)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    pbcg_ctx *ctx = P->ctx;
+    // arguments checked here and agreed over the ranks before any exchange
+    long long bad = 0;
+    if (!b || !x)
+        fail(ctx, PBCG_ERR_INVALID, "b and x must not be NULL"), bad = 1;
+    else if (!(tol > 0.0))
+        fail(ctx, PBCG_ERR_INVALID, "tol must be > 0"), bad = 1;
+    else if (maxit < 0 || maxit == INT32_MAX)
+        fail(ctx, PBCG_ERR_INVALID, "maxit must be in 0 .. 2^31 - 2"), bad = 1;
+    else if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED)
+        fail(ctx, PBCG_ERR_INVALID, "a partitioned solve runs PBCG_ALG_BICGSTAB or PBCG_ALG_PIPELINED"), bad = 1;
+    else if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
+        fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", mode), bad = 1;
+    int rc = 0;
+    if (!bad && cudaSetDevice(ctx->device) != cudaSuccess)
+        fail(ctx, PBCG_ERR_CUDA, "cudaSetDevice failed"), bad = 1;
+    if (!bad && (rc = ensure_ws_in(ctx, P->ws, std::max<long long>(P->nloc, (long long)P->nloc + P->nhalo),
+                                   maxit + 1)))
+        bad = 1;
+    if (!bad) {
+        // this workspace's merges belong to a partitioned solve
+        int one = 1;
+        if (cudaMemcpy(&P->ws.wk->dist, &one, sizeof one, cudaMemcpyHostToDevice) != cudaSuccess)
+            fail(ctx, PBCG_ERR_CUDA, "workspace setup failed"), bad = 1;
+    }
+    long long anybad = 0;
+    if (P->nranks > 1) {
+        if ((rc = comm_any(ctx, P->comm, bad, &anybad)))
+            return rc;
+    } else {
+        anybad = bad;
+    }
+    if (anybad) {
+        if (bad)
+            return rc ? rc : PBCG_ERR_INVALID;
+        return fail(ctx, PBCG_ERR_INVALID, "another rank refused the solve's arguments");
+    }
+    Workspace &ws = P->ws;
+    const pbcg_mat *m = P->m;
+    double *tmp = ws.vec[V_TMP];
+    if ((rc = vec_in(ctx, m, b, ws.vec[V_B], tmp)) || (rc = vec_in(ctx, m, x, ws.vec[V_X], tmp)))
+        return rc;
+    Ctl h;
+    memset(&h, 0, sizeof h);
+    h.maxit = maxit;
+    h.status = ST_RUNNING;
+    h.tol = tol;
+    h.target = tol;
+    h.alg = (alg == PBCG_ALG_BICGSTAB) ? ALG_BICGSTAB : ALG_PIPELINED;
+    h.hist = ws.hist;
+    h.hist_cap = maxit + 1;
+    h.trueres = __builtin_nan("");
+    *ctx->h_ctl = h;
+    CK(cudaMemcpyAsync(ws.ctl, ctx->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    Mat A = mat_of(m);
+    Vecs V = vecs_of(ws);
+    Ctl *c = ws.ctl;
+    Work *wk = ws.wk;
+    Launcher L{ctx, nullptr, 0, {}};
+    auto status = [&](int *st) -> int {
+        int r = read_ctl(ctx, c);
+        *st = ctx->h_ctl->status;
+        return r;
+    };
+    const bool pipe = alg == PBCG_ALG_PIPELINED;
+    // setup: r0 = b - A x0 (and w0 = A r0, t0 = A w0)
+    if ((rc = part_halo(P, V.x)) || (rc = L.go("setup1", mode ? Kern<1>::setup1() : Kern<0>::setup1(), A, V, c, wk, 1)) ||
+        (rc = part_reduce(P, 2, mode, pipe ? FIN_SETUP1_P : FIN_SETUP1_B)))
+        return rc;
+    if (pipe) {
+        int st = 0;
+        if ((rc = part_halo(P, V.r0)) ||
+            (rc = L.go("setup2", mode ? Kern<1>::setup2() : Kern<0>::setup2(), A, V, c, wk, 1)) ||
+            (rc = part_reduce(P, 1, mode, FIN_SETUP2)) || (rc = status(&st)))
+            return rc;
+        if (st == ST_RUNNING || st == ST_CANDIDATE)
+            if ((rc = part_halo(P, V.w)) || (rc = L.go("setup3", (void *)k_setup3, A, V, c, wk, 0)))
+                return rc;
+    }
+    auto body = body_kernels(alg, mode, m->narrow);
+    bool true_done = false;
+    for (;;) {
+        int st = 0;
+        if ((rc = status(&st)))
+            return rc;
+        if (st == ST_CANDIDATE) {
+            if ((rc = part_halo(P, V.x)) || (rc = L.go("true_res", (void *)k_true_res, A, V, c, wk, 1)) ||
+                (rc = part_reduce(P, 2, 1, FIN_TRUE)))
+                return rc;
+            true_done = true;
+            continue;
+        }
+        if (st != ST_RUNNING)
+            break;
+        true_done = false;
+        if (pipe) {
+            const BodyKernel &bx = body[0], &by = body[1];
+            if ((rc = part_halo(P, V.w)) || (rc = L.go(bx.name, bx.fn, A, V, c, wk, 1, bx.smem)) ||
+                (rc = part_reduce(P, 4, mode, FIN_X)) || (rc = status(&st)))
+                return rc;
+            if (st != ST_RUNNING)
+                continue;
+            if ((rc = part_halo(P, V.z)) || (rc = L.go(by.name, by.fn, A, V, c, wk, 1, by.smem)) ||
+                (rc = part_reduce(P, 3, mode, FIN_Y)))
+                return rc;
+        } else {
+            const BodyKernel &kp = body[0], &ka = body[1], &kb = body[2], &kc = body[3];
+            if ((rc = L.go(kp.name, kp.fn, A, V, c, wk, 1, kp.smem)) || (rc = part_halo(P, V.p)) ||
+                (rc = L.go(ka.name, ka.fn, A, V, c, wk, 1, ka.smem)) || (rc = part_reduce(P, 1, mode, FIN_BA)) ||
+                (rc = status(&st)))
+                return rc;
+            if (st != ST_RUNNING)
+                continue;
+            if ((rc = part_halo(P, V.s)) || (rc = part_halo(P, V.r)) ||
+                (rc = L.go(kb.name, kb.fn, A, V, c, wk, 1, kb.smem)) || (rc = part_reduce(P, 2, mode, FIN_BB)) ||
+                (rc = status(&st)))
+                return rc;
+            if (st != ST_RUNNING)
+                continue;
+            if ((rc = L.go(kc.name, kc.fn, A, V, c, wk, 1, kc.smem)) || (rc = part_reduce(P, 2, mode, FIN_BC)))
+                return rc;
+        }
+    }
+    if (!true_done) {
+        if ((rc = part_halo(P, V.x)) || (rc = L.go("true_res", (void *)k_true_res, A, V, c, wk, 1)) ||
+            (rc = part_reduce(P, 2, 1, FIN_TRUE)) || (rc = read_ctl(ctx, c)))
+            return rc;
+    }
+    Ctl fin_ctl = *ctx->h_ctl;
+    if (fin_ctl.err || fin_ctl.status == ST_TIMEOUT)
+        return fail(ctx, PBCG_ERR_TIMEOUT, "a bounded device wait expired on some rank");
+    if ((rc = vec_out(ctx, m, ws.vec[V_X], x, tmp)))
+        return rc;
+    int hl = std::min(fin_ctl.it + 1, maxit + 1);
+    ctx->hist.assign((size_t)hl, 0.0);
+    CK(cudaMemcpyAsync(ctx->hist.data(), ws.hist, sizeof(double) * (size_t)hl, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->have_hist = true;
+    ctx->last_batched = false;
+    if (out) {
+        out->iters = fin_ctl.it;
+        out->status = fin_ctl.status;
+        out->relres_recursive = fin_ctl.res;
+        out->relres_true = fin_ctl.trueres;
+        out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        out->launches = (int32_t)L.launches;
+        out->reserved = 0;
+    }
+    return fin_ctl.status;
+}
+
 bool final_status(const Ctl &c)
 {
     return (c.status >= 0 && c.status <= 3) || c.status == ST_INVALID || c.status == ST_TIMEOUT || c.err;
@@ -1889,56 +2309,9 @@ int pbcg_csr_upload(pbcg_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_pt
     int rc = validate_csr_host(ctx, n, nnz, hrp.data(), hci.data());
     if (rc)
         return rc;
-    Sell S;
-    if (!build_sell(n, hrp.data(), hci.data(), hva.data(), S))
-        return fail(ctx, PBCG_ERR_INVALID, "padded matrix exceeds 2^31 entries");
-    pbcg_mat *m = new pbcg_mat();
-    m->n = n;
-    m->nnz = nnz;
-    m->nslices = S.nslices;
-    m->padded = S.padded;
-    m->sl_off = m->rlen = m->ci = m->perm = m->tmeta = nullptr;
-    m->lci = nullptr;
-    m->va = nullptr;
-    m->narrow = S.narrow;
-    m->bl = nullptr;
-    m->h_sloff.assign(S.sl_off.begin(), S.sl_off.begin() + (S.nslices + 1));
-    m->h_rp = std::move(hrp);
-    m->h_ci = std::move(hci);
-    m->h_va = std::move(hva);
-    size_t P = (size_t)(S.padded ? S.padded : 1);
-    cudaError_t e = cudaMalloc(&m->sl_off, sizeof(int) * S.sl_off.size());
-    if (e == cudaSuccess)
-        e = cudaMalloc(&m->rlen, sizeof(int) * S.rlen.size());
-    if (e == cudaSuccess)
-        e = cudaMalloc(&m->ci, sizeof(int) * P);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&m->va, sizeof(double) * P);
-    if (e == cudaSuccess && S.permuted)
-        e = cudaMalloc(&m->perm, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&m->lci, sizeof(uint16_t) * P);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&m->tmeta, sizeof(int) * S.tmeta.size());
-    if (e == cudaSuccess && S.padded)
-        e = cudaMemcpy(m->lci, S.lci.data(), sizeof(uint16_t) * (size_t)S.padded, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(m->tmeta, S.tmeta.data(), sizeof(int) * S.tmeta.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(m->sl_off, S.sl_off.data(), sizeof(int) * S.sl_off.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(m->rlen, S.rlen.data(), sizeof(int) * S.rlen.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && S.padded)
-        e = cudaMemcpy(m->ci, S.ci.data(), sizeof(int) * (size_t)S.padded, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && S.padded)
-        e = cudaMemcpy(m->va, S.va.data(), sizeof(double) * (size_t)S.padded, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && S.permuted)
-        e = cudaMemcpy(m->perm, S.perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        mat_release(m);
-        return fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "matrix upload: %s",
-                    cudaGetErrorString(e));
-    }
+    pbcg_mat *m = nullptr;
+    if ((rc = make_mat(ctx, n, 0, std::move(hrp), std::move(hci), std::move(hva), &m)))
+        return rc;
     ctx->mats.insert(m);
     *out = m;
     return 0;
@@ -2606,6 +2979,216 @@ int pbcg_pool_room(const pbcg_pool *P, int32_t *free_slots, int64_t *free_rows, 
     if (free_entries)
         *free_entries = P->entries.largest();
     return 0;
+}
+
+int pbcg_part_plan(int32_t nranks, int32_t rank, const int32_t *row_starts, int64_t nnz, const int32_t *row_ptr,
+                   const int32_t *col_idx, int32_t *nhalo, int32_t *halo_cols, int32_t cap, int32_t *recv_counts,
+                   int32_t *local_col)
+{
+    if (!row_starts || !row_ptr || (nnz > 0 && !col_idx) || !nhalo || cap < 0 || (cap > 0 && !halo_cols) ||
+        nranks < 1 || rank < 0 || rank >= nranks)
+        return PBCG_ERR_INVALID;
+    std::vector<int32_t> halo, rc, loc;
+    std::string why;
+    int r = part_plan_host(nranks, rank, row_starts, nnz, row_ptr, col_idx, halo, rc, local_col ? &loc : nullptr,
+                           why);
+    if (r)
+        return r;
+    *nhalo = (int32_t)halo.size();
+    for (int32_t i = 0; i < cap && i < (int32_t)halo.size(); i++)
+        halo_cols[i] = halo[(size_t)i];
+    if (recv_counts)
+        for (int k = 0; k < nranks; k++)
+            recv_counts[k] = rc[(size_t)k];
+    if (local_col)
+        std::copy(loc.begin(), loc.end(), local_col);
+    return 0;
+}
+
+int pbcg_part_create(pbcg_ctx *ctx, const pbcg_comm *comm, int32_t nranks, int32_t rank, const int32_t *row_starts,
+                     int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx, const double *vals,
+                     pbcg_part **out)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!out || !comm || !comm->allreduce_sum_i64 || !comm->alltoallv || !row_starts || nranks < 1 || rank < 0 ||
+        rank >= nranks)
+        return fail(ctx, PBCG_ERR_INVALID, "NULL argument, communicator callback or bad rank");
+    *out = nullptr;
+    NvtxRange trace("pbcg_part_create");
+    // local checks first, then one allreduce so that every rank fails together
+    long long bad = 0;
+    std::vector<int32_t> rs((size_t)nranks + 1), hrp, hci, halo, rcount, local;
+    std::vector<double> hva;
+    int rc = 0;
+    memcpy(rs.data(), row_starts, sizeof(int32_t) * ((size_t)nranks + 1));
+    const int nloc = rs[(size_t)rank + 1] - rs[(size_t)rank];
+    if (cudaSetDevice(ctx->device) != cudaSuccess)
+        rc = fail(ctx, PBCG_ERR_CUDA, "cudaSetDevice failed");
+    else if (!row_ptr || (nnz > 0 && (!col_idx || !vals)) || nnz < 0 || nnz >= (1ll << 31) || nloc < 1 ||
+             nloc > INT32_MAX / 2)
+        rc = fail(ctx, PBCG_ERR_INVALID, "bad block: NULL CSR array, nnz out of range or rows outside 1 .. 2^30 - 1");
+    if (!rc) {
+        hrp.resize((size_t)nloc + 1);
+        hci.resize((size_t)nnz);
+        hva.resize((size_t)nnz);
+        cudaError_t e = cudaMemcpy(hrp.data(), row_ptr, sizeof(int32_t) * hrp.size(), cudaMemcpyDefault);
+        if (e == cudaSuccess && nnz)
+            e = cudaMemcpy(hci.data(), col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDefault);
+        if (e == cudaSuccess && nnz)
+            e = cudaMemcpy(hva.data(), vals, sizeof(double) * (size_t)nnz, cudaMemcpyDefault);
+        if (e != cudaSuccess)
+            rc = fail(ctx, PBCG_ERR_CUDA, "copying the block: %s", cudaGetErrorString(e));
+    }
+    if (!rc) {
+        std::string why;
+        if ((rc = part_plan_host(nranks, rank, rs.data(), nnz, hrp.data(), hci.data(), halo, rcount, &local, why)))
+            fail(ctx, rc, "%s", why.c_str());
+    }
+    bad = rc ? 1 : 0;
+    long long anybad = bad;
+    if (nranks > 1) {
+        int r2 = comm_any(ctx, *comm, bad, &anybad);
+        if (r2)
+            return r2;
+    }
+    if (anybad)
+        return rc ? rc : fail(ctx, PBCG_ERR_INVALID, "another rank refused its block");
+    pbcg_part *P = new pbcg_part();
+    P->ctx = ctx;
+    P->comm = *comm;
+    P->nranks = nranks;
+    P->rank = rank;
+    P->row0 = rs[(size_t)rank];
+    P->nloc = nloc;
+    P->nhalo = (int)halo.size();
+    // which of my rows each rank gathers: counts, then the global indices
+    std::vector<int64_t> cnt_send((size_t)nranks), cnt_recv((size_t)nranks), b8((size_t)nranks, 8), d8((size_t)nranks);
+    for (int k = 0; k < nranks; k++) {
+        cnt_send[(size_t)k] = rcount[(size_t)k];
+        d8[(size_t)k] = 8ll * k;
+    }
+    if (nranks > 1 && comm->alltoallv(comm->user, cnt_send.data(), b8.data(), d8.data(), cnt_recv.data(), b8.data(),
+                                      d8.data()) != 0) {
+        part_release(P);
+        return fail(ctx, PBCG_ERR_COMM, "alltoallv callback failed (halo counts)");
+    }
+    if (nranks == 1)
+        cnt_recv = cnt_send;
+    std::vector<int64_t> qb((size_t)nranks), qd((size_t)nranks), ab((size_t)nranks), ad((size_t)nranks);
+    long long qoff = 0, aoff = 0;
+    for (int k = 0; k < nranks; k++) {
+        qb[(size_t)k] = 4ll * cnt_send[(size_t)k];     // my halo columns owned by k (requests to k)
+        qd[(size_t)k] = qoff;
+        qoff += qb[(size_t)k];
+        ab[(size_t)k] = 4ll * cnt_recv[(size_t)k];     // rows of mine that k requests
+        ad[(size_t)k] = aoff;
+        aoff += ab[(size_t)k];
+    }
+    std::vector<int32_t> wanted((size_t)(aoff / 4) + 1);
+    if (nranks > 1 && comm->alltoallv(comm->user, halo.data(), qb.data(), qd.data(), wanted.data(), ab.data(),
+                                      ad.data()) != 0) {
+        part_release(P);
+        return fail(ctx, PBCG_ERR_COMM, "alltoallv callback failed (halo indices)");
+    }
+    P->nsend = (int)(aoff / 4);
+    bad = 0;
+    for (int j = 0; j < P->nsend; j++)
+        if (wanted[(size_t)j] < P->row0 || wanted[(size_t)j] >= P->row0 + nloc)
+            bad = 1;
+    if (bad)
+        fail(ctx, PBCG_ERR_INVALID, "a rank asked for rows outside this block (row_starts differ between ranks?)");
+    // the block's matrix with local columns, and the buffers of the exchanges
+    if (!bad) {
+        rc = make_mat(ctx, nloc, nloc + P->nhalo, std::move(hrp), std::move(local), std::move(hva), &P->m);
+        if (rc)
+            bad = 1;
+    }
+    if (!bad) {
+        std::vector<int> perm;
+        if (P->m->perm) {
+            perm.resize((size_t)nloc);
+            if (cudaMemcpy(perm.data(), P->m->perm, sizeof(int) * (size_t)nloc, cudaMemcpyDeviceToHost) != cudaSuccess)
+                bad = 1;
+        }
+        std::vector<int> inv((size_t)nloc);
+        for (int p = 0; p < nloc; p++)
+            inv[(size_t)(perm.empty() ? p : perm[(size_t)p])] = p;
+        std::vector<int> sidx((size_t)P->nsend + 1);
+        for (int j = 0; j < P->nsend; j++)
+            sidx[(size_t)j] = inv[(size_t)(wanted[(size_t)j] - P->row0)];
+        P->red_cap = 1 + std::max(MAXD * RED_EXACT_STRIDE, nranks * MAXD);
+        cudaError_t e = bad ? cudaErrorUnknown : cudaSuccess;
+        if (e == cudaSuccess)
+            e = cudaMalloc(&P->d_send_idx, sizeof(int) * sidx.size());
+        if (e == cudaSuccess)
+            e = cudaMalloc(&P->d_send, sizeof(double) * sidx.size());
+        if (e == cudaSuccess)
+            e = cudaMalloc(&P->d_red, sizeof(long long) * (size_t)P->red_cap);
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&P->h_send, sizeof(double) * sidx.size());
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&P->h_recv, sizeof(double) * ((size_t)P->nhalo + 1));
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&P->h_red, sizeof(long long) * (size_t)P->red_cap);
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&P->h_g, sizeof(GAcc) * MAXD);
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&P->h_loc, sizeof(double) * MAXD);
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&P->h_err, sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_send_idx, sidx.data(), sizeof(int) * sidx.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            rc = fail(ctx, e == cudaErrorMemoryAllocation ? PBCG_ERR_OOM : PBCG_ERR_CUDA, "block buffers: %s",
+                      cudaGetErrorString(e));
+            bad = 1;
+        }
+    }
+    if (!bad) {
+        P->sb.resize((size_t)nranks);
+        P->sd.resize((size_t)nranks);
+        P->rb.resize((size_t)nranks);
+        P->rd.resize((size_t)nranks);
+        for (int k = 0; k < nranks; k++) {
+            P->sb[(size_t)k] = 2 * ab[(size_t)k];       // doubles where the requests were int32
+            P->sd[(size_t)k] = 2 * ad[(size_t)k];
+            P->rb[(size_t)k] = 2 * qb[(size_t)k];
+            P->rd[(size_t)k] = 2 * qd[(size_t)k];
+        }
+    }
+    anybad = bad;
+    if (nranks > 1) {
+        int r2 = comm_any(ctx, *comm, bad, &anybad);
+        if (r2) {
+            part_release(P);
+            return r2;
+        }
+    }
+    if (anybad) {
+        part_release(P);
+        return bad ? (rc ? rc : PBCG_ERR_INVALID) : fail(ctx, PBCG_ERR_INVALID, "another rank failed to set up");
+    }
+    *out = P;
+    return 0;
+}
+
+int pbcg_part_solve(pbcg_part *part, const double *b, double *x, double tol, int32_t maxit, int alg, int dot_mode,
+                    pbcg_result *out)
+{
+    if (!part)
+        return PBCG_ERR_INVALID;
+    NvtxRange trace("pbcg_part_solve");
+    return part_solve_impl(part, b, x, tol, maxit, alg, dot_mode, out);
+}
+
+void pbcg_part_destroy(pbcg_part *part)
+{
+    if (!part)
+        return;
+    cudaSetDevice(part->ctx->device);
+    cudaStreamSynchronize(part->ctx->stream);
+    part_release(part);
 }
 
 }  // extern "C"

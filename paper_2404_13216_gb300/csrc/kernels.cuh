@@ -93,7 +93,9 @@ struct Work {
     unsigned int ticket;
     unsigned int tile_next;              // next tile to claim in a pass that schedules tiles dynamically
     int maxgrid;
+    int dist;                            // 1: this grid is one rank of a row-partitioned solve
     double *part;                        // plain partials [MAXD][maxgrid]
+    double loc[MAXD];                    // dist, plain: this rank's dots, its CTAs' partials summed in CTA order
 };
 
 // SELL-32 matrix in the solver's (possibly permuted) row order
@@ -433,6 +435,23 @@ __device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
     __syncthreads();
     if (!sh.last)
         return false;
+    if (wk->dist) {
+        // one rank of a row-partitioned solve: the exact digits stay in wk->g
+        // and the plain partials are summed into wk->loc; the host adds them
+        // over the ranks and k_dist_finish rounds and takes the scalar step
+        if (MODE == 0) {
+            merge_finish<ND, MODE>(sh, wk);
+            __syncthreads();
+            if (threadIdx.x < ND)
+                wk->loc[threadIdx.x] = sh.dv[threadIdx.x];
+        }
+        if (threadIdx.x == 0) {
+            wk->ticket = 0u;
+            wk->tile_next = 0u;
+        }
+        __syncthreads();
+        return false;
+    }
     merge_finish<ND, MODE>(sh, wk);
     if (threadIdx.x == 0) {
         wk->ticket = 0u;
@@ -629,6 +648,26 @@ static __global__ void __launch_bounds__(THREADS) k_setup3(Mat A, Vecs V, const 
 // ---------------------------------------------------------------------------
 // true residual ||b - A x|| / ||b|| with exact dots; resolves a candidate stop
 // ---------------------------------------------------------------------------
+// the scalar step after the dots (r,r) and (b,b) of the true residual (one thread)
+static __device__ void true_res_tail(Ctl *c, const double *dv)
+{
+    double nb = __dsqrt_rn(dv[1]);
+    if (nb == 0.0)
+        nb = 1.0;
+    double tr = __ddiv_rn(__dsqrt_rn(dv[0]), nb);
+    c->trueres = tr;
+    c->bbx = dv[1];
+    if (c->status == ST_CANDIDATE) {
+        if (tr <= c->tol) {
+            c->status = 0;
+        } else {
+            c->target = __dmul_rn(c->tol, __ddiv_rn(c->tol, tr));
+            c->status = ST_RUNNING;
+            post_stop(c);
+        }
+    }
+}
+
 static __global__ void __launch_bounds__(THREADS) k_true_res(Mat A, Vecs V, Ctl *c, Work *wk)
 {
     __shared__ Shm<2> sh;
@@ -652,23 +691,8 @@ static __global__ void __launch_bounds__(THREADS) k_true_res(Mat A, Vecs V, Ctl 
     }
     if (!finalize<2, 1>(D, sh, wk))
         return;
-    if (threadIdx.x == 0) {
-        double nb = __dsqrt_rn(sh.dv[1]);
-        if (nb == 0.0)
-            nb = 1.0;
-        double tr = __ddiv_rn(__dsqrt_rn(sh.dv[0]), nb);
-        c->trueres = tr;
-        c->bbx = sh.dv[1];
-        if (c->status == ST_CANDIDATE) {
-            if (tr <= c->tol) {
-                c->status = 0;
-            } else {
-                c->target = __dmul_rn(c->tol, __ddiv_rn(c->tol, tr));
-                c->status = ST_RUNNING;
-                post_stop(c);
-            }
-        }
-    }
+    if (threadIdx.x == 0)
+        true_res_tail(c, sh.dv);
 }
 
 // ---------------------------------------------------------------------------

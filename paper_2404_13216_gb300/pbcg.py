@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpbcg.so")
 
 OK, MAXIT, BREAKDOWN, NONFINITE = 0, 1, 2, 3
-ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT = -1, -2, -3, -4
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_COMM = -1, -2, -3, -4, -5
 BICGSTAB, PIPELINED, PIPELINED_RR = 0, 1, 2
 OPT_RR_PERIOD, OPT_PRECOND, OPT_SMALL_CLUSTER, OPT_BATCH_GRAPH = 1, 3, 4, 5
 PRECOND_NONE, PRECOND_JACOBI = 0, 1
@@ -27,7 +27,8 @@ EXPORTS = ("pbcg_create", "pbcg_destroy", "pbcg_last_error", "pbcg_csr_upload", 
            "pbcg_solve", "pbcg_solve_batched", "pbcg_residual_history", "pbcg_dot", "pbcg_spmv",
            "pbcg_profile_solve", "pbcg_dot_noalloc", "pbcg_set_option", "pbcg_pool_create", "pbcg_pool_destroy",
            "pbcg_pool_admit", "pbcg_pool_step", "pbcg_pool_poll", "pbcg_pool_result", "pbcg_pool_history",
-           "pbcg_pool_room", "pbcg_check_wait")
+           "pbcg_pool_room", "pbcg_check_wait", "pbcg_part_plan", "pbcg_part_create", "pbcg_part_solve",
+           "pbcg_part_destroy")
 
 
 class PbcgError(RuntimeError):
@@ -47,6 +48,16 @@ class _Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres_recursive", ctypes.c_double),
                 ("relres_true", ctypes.c_double), ("seconds", ctypes.c_double), ("launches", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+_ALLREDUCE = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64)
+_ALLTOALLV = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int64))
+
+
+class _Comm(ctypes.Structure):
+    _fields_ = [("user", ctypes.c_void_p), ("allreduce_sum_i64", _ALLREDUCE), ("alltoallv", _ALLTOALLV)]
 
 
 def load_library(path: str = LIB_PATH):
@@ -100,6 +111,14 @@ def load_library(path: str = LIB_PATH):
     lib.pbcg_pool_history.restype = ctypes.c_int
     lib.pbcg_pool_room.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.pbcg_pool_room.restype = ctypes.c_int
+    lib.pbcg_part_plan.argtypes = [i32, i32, P, i64, P, P, ctypes.POINTER(i32), P, i32, P, P]
+    lib.pbcg_part_plan.restype = ctypes.c_int
+    lib.pbcg_part_create.argtypes = [P, ctypes.POINTER(_Comm), i32, i32, P, i64, P, P, P, ctypes.POINTER(P)]
+    lib.pbcg_part_create.restype = ctypes.c_int
+    lib.pbcg_part_solve.argtypes = [P, P, P, d, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result)]
+    lib.pbcg_part_solve.restype = ctypes.c_int
+    lib.pbcg_part_destroy.argtypes = [P]
+    lib.pbcg_part_destroy.restype = None
     return lib
 
 
@@ -412,3 +431,102 @@ class Pool:
         fs, fr, fe = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0)
         self.ctx._check(_lib.pbcg_pool_room(self.handle, ctypes.byref(fs), ctypes.byref(fr), ctypes.byref(fe)))
         return fs.value, fr.value, fe.value
+
+
+def part_plan(nranks: int, rank: int, row_starts, row_ptr, col_idx):
+    """pbcg_part_plan (host only): (halo columns, per-rank counts, local column
+    of every entry) of rank `rank`'s block with global column indices."""
+    rs = np.ascontiguousarray(row_starts, dtype=np.int32)
+    if rs.size != nranks + 1:
+        raise ValueError(f"row_starts has {rs.size} entries, expected {nranks + 1}")
+    rp, ci = np.ascontiguousarray(row_ptr, dtype=np.int32), np.ascontiguousarray(col_idx, dtype=np.int32)
+    nh = ctypes.c_int32(0)
+    cnt = np.zeros(max(nranks, 1), dtype=np.int32)
+    loc = np.zeros(ci.size, dtype=np.int32)
+    rc = _lib.pbcg_part_plan(nranks, rank, _ptr(rs), ci.size, _ptr(rp), _ptr(ci), ctypes.byref(nh), None, 0,
+                             _ptr(cnt), _ptr(loc))
+    if rc != 0:
+        raise PbcgError(rc, "pbcg_part_plan refused the block")
+    halo = np.zeros(max(nh.value, 1), dtype=np.int32)
+    rc = _lib.pbcg_part_plan(nranks, rank, _ptr(rs), ci.size, _ptr(rp), _ptr(ci), ctypes.byref(nh), _ptr(halo),
+                             nh.value, None, None)
+    if rc != 0:
+        raise PbcgError(rc, "pbcg_part_plan refused the block")
+    return halo[:nh.value], cnt[:nranks], loc
+
+
+def _c_comm(comm):
+    """C callbacks calling comm.allreduce_sum_i64(int64 array) and
+    comm.alltoallv(send, send_bytes, send_displs, recv, recv_bytes,
+    recv_displs) on numpy views of the library's host buffers; an exception
+    becomes a nonzero return (PBCG_ERR_COMM)."""
+    size = int(comm.size)
+
+    def _view(addr, nbytes):
+        if nbytes <= 0 or not addr:
+            return np.zeros(0, np.uint8)
+        return np.ctypeslib.as_array((ctypes.c_uint8 * nbytes).from_address(addr))
+
+    def allreduce(user, buf, count):
+        try:
+            if count > 0:
+                comm.allreduce_sum_i64(np.ctypeslib.as_array(buf, shape=(count,)))
+            return 0
+        except Exception:
+            return 1
+
+    def alltoallv(user, send, sb, sd, recv, rb, rd):
+        try:
+            sbn, sdn = np.ctypeslib.as_array(sb, shape=(size,)), np.ctypeslib.as_array(sd, shape=(size,))
+            rbn, rdn = np.ctypeslib.as_array(rb, shape=(size,)), np.ctypeslib.as_array(rd, shape=(size,))
+            comm.alltoallv(_view(send, int((sbn + sdn).max(initial=0))), sbn, sdn,
+                           _view(recv, int((rbn + rdn).max(initial=0))), rbn, rdn)
+            return 0
+        except Exception:
+            return 1
+
+    f1, f2 = _ALLREDUCE(allreduce), _ALLTOALLV(alltoallv)
+    return _Comm(None, f1, f2), (f1, f2)
+
+
+class Partition:
+    """pbcg_part_*: this rank's block of a row-partitioned system.
+
+    comm has .size and the two collectives (paper_2404_13216_gb300.comm);
+    row_ptr, col_idx (global columns) and vals hold the block's rows
+    row_starts[rank] .. row_starts[rank+1] - 1.  Creation and solve are
+    collective: every rank calls them in the same order."""
+
+    def __init__(self, ctx: "Context", comm, row_starts, row_ptr, col_idx, vals):
+        rs = np.ascontiguousarray(row_starts, dtype=np.int32)
+        nranks, rank = int(comm.size), int(comm.rank)
+        if rs.size != nranks + 1:
+            raise ValueError(f"row_starts has {rs.size} entries, expected {nranks + 1}")
+        rp, ci, va, n, nnz = _csr(row_ptr, col_idx, vals)
+        if n != int(rs[rank + 1] - rs[rank]):
+            raise ValueError(f"the block has {n} rows, row_starts gives {int(rs[rank + 1] - rs[rank])}")
+        self._ccomm, self._keep = _c_comm(comm)
+        h = ctypes.c_void_p()
+        ctx._check(_lib.pbcg_part_create(ctx.handle, ctypes.byref(self._ccomm), nranks, rank, _ptr(rs), nnz,
+                                         _ptr(rp), _ptr(ci), _ptr(va), ctypes.byref(h)))
+        self.ctx, self.handle, self.n, self.rank, self.nranks = ctx, h, n, rank, nranks
+
+    def solve(self, b, x, tol: float, maxit: int, alg: int = PIPELINED, mode: int = EXACT) -> Result:
+        """Solve in place over all ranks: x holds this rank's block of x0 on entry
+        and of the last iterate on return."""
+        b, x = _vec_in(b, self.n, "b"), _vec_out(x, self.n, "x")
+        r = _Result()
+        self.ctx._check(_lib.pbcg_part_solve(self.handle, _ptr(b), _ptr(x), float(tol), int(maxit), int(alg),
+                                             int(mode), ctypes.byref(r)))
+        return Result(r.status, r.iters, r.relres_recursive, r.relres_true, r.seconds, r.launches)
+
+    def close(self):
+        if self.handle:
+            _lib.pbcg_part_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
