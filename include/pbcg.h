@@ -351,6 +351,68 @@ int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double
                        double *ms, int32_t *launches, int32_t cap, int32_t *count);
 
 /*
+ * Launch variants and the autotuner.
+ *
+ * How the passes are launched changes neither the paper's arithmetic nor,
+ * in exact mode, a single bit of the results: every SpMV row keeps its fma
+ * chain in stored order (a row is never split across lanes) and every exact
+ * dot is rounded once from the same integer sum.  What may change is speed,
+ * and in plain mode the order in which the partial sums are added.  The
+ * choices:
+ *   staged       1: tiles whose SELL entries fit the shared-memory stage are
+ *                copied there by bulk copies (default); 0: entries stream
+ *                from global memory;
+ *   order        tile order of a pass: 0 default (round-robin when staged,
+ *                claimed otherwise), 1 round-robin, 2 claimed from a
+ *                grid-wide counter in index order;
+ *   ctas_per_sm  resident CTAs per SM of the passes of pbcg_solve (0: as
+ *                many as fit; else at most that many);
+ *   batched_ctas_per_sm  the same for pbcg_solve_batched's passes (fewer
+ *                CTAs: longer chunks of the tile list per CTA).
+ * A variant belongs to a matrix and is used by every later solve of it
+ * (pbcg_solve, pbcg_profile_solve, pbcg_solve_batched); pools and
+ * partitioned solves keep the default.
+ */
+typedef struct {
+    int32_t staged;
+    int32_t order;
+    int32_t ctas_per_sm;
+    int32_t batched_ctas_per_sm;
+    double us_per_iter;          /* pbcg_tune: measured time per iteration; ignored by pbcg_set_variant */
+} pbcg_variant;
+
+/* Set (v != NULL) or reset to the default (v == NULL) A's launch variant.
+ * Errors: INVALID (unknown matrix, a field out of range). */
+int pbcg_set_variant(pbcg_ctx *ctx, pbcg_mat *A, const pbcg_variant *v);
+
+/* A's current launch variant (us_per_iter: the last tuned figure, or 0). */
+int pbcg_get_variant(pbcg_ctx *ctx, const pbcg_mat *A, pbcg_variant *out);
+
+/*
+ * Autotune A's launch variant for algorithm alg and dot_mode: every
+ * candidate variant runs a trial solve of `iters` iterations (b = A * ones,
+ * x0 = 0, no stop) and the fastest per iteration (CUDA events on the
+ * context's stream, after one untimed trial) becomes A's variant; the
+ * default is always a candidate, so the choice is never slower than it as
+ * measured.  nsys = 0 tunes pbcg_solve's passes; nsys >= 1 with
+ * sys_row_ptr[nsys+1] tunes pbcg_solve_batched's passes for that block
+ * structure.  A system small enough for the one-cluster loop keeps the
+ * default (its launch is fixed).
+ * cache_path (may be NULL): a file of JSON lines, one per tuned key
+ * {"key": "...", "staged": s, "order": o, "ctas_per_sm": c,
+ *  "batched_ctas_per_sm": b, "us_per_iter": t}; the key is made of n, nnz,
+ * a hash of the row-length histogram (and of sys_row_ptr), alg, dot_mode and
+ * the SM count.  A key found there is applied without timing; a new one is
+ * appended.  chosen (may be NULL) receives the variant applied; tried (cap
+ * entries, may be NULL) the candidates with their times, *ntried (may be
+ * NULL) how many ran (0 when the cache answered).
+ * Errors: INVALID (bad arguments, iters < 1), OOM, CUDA, or a trial's error.
+ */
+int pbcg_tune(pbcg_ctx *ctx, pbcg_mat *A, int alg, int dot_mode, int32_t nsys, const int32_t *sys_row_ptr,
+              int32_t iters, const char *cache_path, pbcg_variant *chosen, pbcg_variant *tried, int32_t cap,
+              int32_t *ntried);
+
+/*
  * pbcg_dot_noalloc: the dot product of pbcg_dot for callers that cannot
  * allocate device memory (code inside another allocator's arena, a fixed or
  * capped memory budget, or a loop that must not enter the allocator, since

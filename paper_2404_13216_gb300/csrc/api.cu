@@ -39,6 +39,7 @@ struct LoopGraph {
     int alg = -1, mode = -1, n = -1;
     bool jac = false;                  // built on the Jacobi-scaled entries
     const void *mat = nullptr;
+    int var = -1;                      // launch variant it was built for (staged, order, CTAs per SM)
 };
 
 struct Workspace {
@@ -84,6 +85,12 @@ struct pbcg_mat {
     std::vector<int> h_sloff;          // [nslices + 1] host copy of sl_off
     std::vector<double> h_va;
     struct BatchLayout *bl;            // tile-aligned layout of the last batched solve, or NULL
+    // launch variant of pbcg_solve's passes (pbcg_set_variant / pbcg_tune); none changes exact results
+    int v_staged = 1;                  // stage tiles in shared memory when they fit (narrow matrices)
+    int v_order = 0;                   // tile order: 0 default, 1 round-robin, 2 claimed
+    int v_ctas = 0;                    // resident CTAs per SM of the passes (0: as many as fit)
+    int b_ctas = 0;                    // same, batched passes
+    double v_us = 0.0;                 // time per iteration pbcg_tune measured for it
 };
 
 // a block-diagonal matrix laid out with every system padded to whole 256-row tiles
@@ -133,7 +140,7 @@ struct pbcg_ctx {
         cudaGraphExec_t exec = nullptr;
         cudaGraph_t graph = nullptr;
         const void *g_layout = nullptr;
-        int g_alg = -1, g_mode = -1;
+        int g_alg = -1, g_mode = -1, g_ctas = 0;
         std::vector<Ctl> last;         // per-system control blocks of the last batched solve
         int hist_stride = 0;
     } b;
@@ -225,7 +232,7 @@ Vecs vecs_of(Workspace &ws)
 }
 
 // persistent grid: every CTA resident (occupancy of this kernel x SMs), at least one slice per warp
-int grid_for(pbcg_ctx *ctx, const void *fn, long long nslices, size_t smem = 0)
+int grid_for(pbcg_ctx *ctx, const void *fn, long long nslices, size_t smem = 0, int cap = 0)
 {
     int per_sm = 0;
     auto it = ctx->occ.find(fn);
@@ -239,6 +246,8 @@ int grid_for(pbcg_ctx *ctx, const void *fn, long long nslices, size_t smem = 0)
         cudaGetLastError();
         ctx->occ[fn] = per_sm;
     }
+    if (cap > 0 && cap < per_sm)
+        per_sm = cap;
     long long g = (long long)per_sm * ctx->num_sms;
     long long need = (nslices + WARPS - 1) / WARPS;
     if (g > need)
@@ -518,6 +527,8 @@ struct BodyKernel {
     size_t smem;     // dynamic shared memory
 };
 
+// narrow: the passes stage tiles in shared memory (the matrix's tiles fit and
+// the launch variant stages)
 std::vector<BodyKernel> body_kernels(int alg, int mode, bool narrow)
 {
     std::vector<BodyKernel> k;
@@ -548,11 +559,11 @@ std::vector<BodyKernel> body_kernels(int alg, int mode, bool narrow)
     return k;
 }
 
-int launch_kernel(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work, size_t smem)
+int launch_kernel(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work, size_t smem, int cap = 0)
 {
     void *args4[4] = {&A, &V, &c, &wk};
     void *args3[3] = {&A, &V, &c};
-    int grid = grid_for(ctx, fn, A.nslices, smem);
+    int grid = grid_for(ctx, fn, A.nslices, smem, cap);
     CK(cudaLaunchKernel(fn, dim3(grid), dim3(THREADS), has_work ? args4 : args3, smem, ctx->stream));
     return 0;
 }
@@ -561,7 +572,8 @@ int launch_kernel(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, in
 int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, LoopGraph **out)
 {
     LoopGraph &L = ctx->ws.loop;
-    if (L.exec && L.mat == m && L.alg == alg && L.mode == mode && L.n == m->n && L.jac == jac) {
+    const int var = m->v_staged | (m->v_order << 1) | (m->v_ctas << 4);
+    if (L.exec && L.mat == m && L.alg == alg && L.mode == mode && L.n == m->n && L.jac == jac && L.var == var) {
         *out = &L;
         return 0;
     }
@@ -584,12 +596,12 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, Loop
     Ctl *c = ctx->ws.ctl;
     Work *wk = ctx->ws.wk;
     cudaGraphNode_t prev = nullptr;
-    for (auto &bk : body_kernels(alg, mode, m->narrow)) {
+    for (auto &bk : body_kernels(alg, mode, m->narrow && m->v_staged)) {
         void *args4[4] = {&A, &V, &c, &wk};
         void *args3[3] = {&A, &V, &c};
         cudaKernelNodeParams kp{};
         kp.func = bk.fn;
-        kp.gridDim = dim3(grid_for(ctx, bk.fn, A.nslices, bk.smem));
+        kp.gridDim = dim3(grid_for(ctx, bk.fn, A.nslices, bk.smem, bk.has_work ? m->v_ctas : 0));
         kp.blockDim = dim3(THREADS);
         kp.sharedMemBytes = (unsigned)bk.smem;
         kp.kernelParams = bk.has_work ? args4 : args3;
@@ -601,6 +613,7 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, Loop
     L.alg = alg;
     L.mode = mode;
     L.jac = jac;
+    L.var = var;
     L.mat = m;
     L.n = m->n;
     *out = &L;
@@ -642,7 +655,7 @@ struct Launcher {
     long long launches = 0;
     std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
 
-    int go(const char *name, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work, size_t smem = 0)
+    int go(const char *name, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, int has_work, size_t smem = 0, int cap = 0)
     {
         NvtxRange trace(name);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -651,7 +664,7 @@ struct Launcher {
             CK(cudaEventCreate(&e1));
             CK(cudaEventRecord(e0, ctx->stream));
         }
-        int rc = launch_kernel(ctx, fn, A, V, c, wk, has_work, smem);
+        int rc = launch_kernel(ctx, fn, A, V, c, wk, has_work, smem, cap);
         if (rc)
             return rc;
         launches++;
@@ -928,6 +941,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
     h.alg = (alg == PBCG_ALG_BICGSTAB) ? ALG_BICGSTAB : ALG_PIPELINED;
     h.rr_period = (alg == PBCG_ALG_PIPELINED_RR) ? ctx->rr_period : 0;
     h.use_cond = 0;
+    h.order = m->v_order;
     h.hist = ws.hist;
     h.hist_cap = maxit + 1;
     h.trueres = __builtin_nan("");
@@ -952,7 +966,7 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         return rc;
     bool cond_on = false;
     bool true_done = false;
-    auto body = body_kernels(alg, mode, m->narrow);
+    auto body = body_kernels(alg, mode, m->narrow && m->v_staged);
     bool fresh = false;      // h_ctl already mirrors the device after a graph launch
     for (;;) {
         if (prof && (rc = L.flush()))
@@ -975,7 +989,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
         if (prof) {
             // host-driven iteration, one kernel at a time
             for (auto &bk : body)
-                if ((rc = L.go(bk.name, bk.fn, A, V, ws.ctl, ws.wk, bk.has_work, bk.smem)))
+                if ((rc = L.go(bk.name, bk.fn, A, V, ws.ctl, ws.wk, bk.has_work, bk.smem,
+                               bk.has_work ? m->v_ctas : 0)))
                     return rc;
         } else if (alg != PBCG_ALG_PIPELINED_RR && ctx->small_cluster && cluster_shape(ctx, m, alg, mode, &cs)) {
             // small system: every iteration up to the next stop in one cluster launch
@@ -1304,9 +1319,9 @@ std::vector<BKernel> batch_body(int alg)
     return k;
 }
 
-int bgrid(pbcg_ctx *ctx, const void *fn, int ntiles, size_t smem = 0)
+int bgrid(pbcg_ctx *ctx, const void *fn, int ntiles, size_t smem = 0, int cap = 0)
 {
-    return grid_for(ctx, fn, (long long)ntiles * TILE_SLICES, smem);
+    return grid_for(ctx, fn, (long long)ntiles * TILE_SLICES, smem, cap);
 }
 
 int blaunch(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Batch &B)
@@ -1425,8 +1440,8 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         for (long long it = 0; any && it <= (long long)maxit + 4; it++) {
             for (auto &bk : body) {
                 void *args[3] = {&A, &V, &B};
-                CK(cudaLaunchKernel(bk.fn, dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem)), dim3(THREADS), args,
-                                    bk.smem, ctx->stream));
+                CK(cudaLaunchKernel(bk.fn, dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem, m->b_ctas)), dim3(THREADS),
+                                    args, bk.smem, ctx->stream));
             }
             unsigned long long hv = 0ull;
             int zero = 0;
@@ -1435,7 +1450,8 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
             CK(cudaMemcpyAsync(&any, B.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
         }
-    } else if (!(BW.exec && BW.g_layout == (const void *)L && BW.g_alg == alg && BW.g_mode == mode)) {
+    } else if (!(BW.exec && BW.g_layout == (const void *)L && BW.g_alg == alg && BW.g_mode == mode &&
+                 BW.g_ctas == m->b_ctas)) {
         free_batch_graph(ctx);
         CK(cudaGraphCreate(&BW.graph, 0));
         cudaGraphConditionalHandle h;
@@ -1453,7 +1469,7 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
             void *args[3] = {&A, &V, &B};
             cudaKernelNodeParams kp{};
             kp.func = bk.fn;
-            kp.gridDim = dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem));
+            kp.gridDim = dim3(bgrid(ctx, bk.fn, B.ntiles, bk.smem, m->b_ctas));
             kp.blockDim = dim3(THREADS);
             kp.sharedMemBytes = (unsigned)bk.smem;
             kp.kernelParams = args;
@@ -1475,6 +1491,7 @@ int solve_batched_impl(pbcg_ctx *ctx, const pbcg_mat *Ac, int32_t nsys, const in
         BW.g_layout = L;
         BW.g_alg = alg;
         BW.g_mode = mode;
+        BW.g_ctas = m->b_ctas;
     }
     if (ctx->batch_graph)
         CK(cudaGraphLaunch(BW.exec, ctx->stream));
@@ -1855,6 +1872,248 @@ int make_mat(pbcg_ctx *ctx, int n, int ncols, std::vector<int32_t> &&hrp, std::v
                     cudaGetErrorString(e));
     }
     *out = m;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// launch variants and the autotuner (pbcg_tune)
+// ---------------------------------------------------------------------------
+pbcg_variant variant_of(const pbcg_mat *m)
+{
+    pbcg_variant v;
+    v.staged = m->v_staged;
+    v.order = m->v_order;
+    v.ctas_per_sm = m->v_ctas;
+    v.batched_ctas_per_sm = m->b_ctas;
+    v.us_per_iter = m->v_us;
+    return v;
+}
+
+bool variant_ok(const pbcg_variant &v)
+{
+    return (v.staged == 0 || v.staged == 1) && v.order >= 0 && v.order <= 2 && v.ctas_per_sm >= 0 &&
+           v.ctas_per_sm <= 32 && v.batched_ctas_per_sm >= 0 && v.batched_ctas_per_sm <= 32;
+}
+
+void apply_variant(pbcg_mat *m, const pbcg_variant &v)
+{
+    m->v_staged = v.staged;
+    m->v_order = v.order;
+    m->v_ctas = v.ctas_per_sm;
+    m->b_ctas = v.batched_ctas_per_sm;
+    m->v_us = v.us_per_iter;
+}
+
+// FNV-1a over 64-bit words
+struct Fnv {
+    unsigned long long h = 1469598103934665603ull;
+    void add(unsigned long long v)
+    {
+        for (int k = 0; k < 8; k++) {
+            h ^= (v >> (8 * k)) & 0xffull;
+            h *= 1099511628211ull;
+        }
+    }
+};
+
+std::string tune_key(const pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, int nsys, const int32_t *srp)
+{
+    // row-length histogram: how many rows have each length (sparse, by length)
+    std::map<int, long long> hist;
+    for (int i = 0; i < m->n; i++)
+        hist[m->h_rp[(size_t)i + 1] - m->h_rp[(size_t)i]]++;
+    Fnv f;
+    for (auto &e : hist) {
+        f.add((unsigned long long)e.first);
+        f.add((unsigned long long)e.second);
+    }
+    Fnv g;
+    for (int k = 0; nsys > 0 && k <= nsys; k++)
+        g.add((unsigned long long)(unsigned)srp[k]);
+    char buf[256];
+    snprintf(buf, sizeof buf, "n=%d;nnz=%lld;rows=%016llx;nsys=%d;sys=%016llx;alg=%d;mode=%d;sms=%d", m->n, m->nnz, f.h,
+             nsys, nsys > 0 ? g.h : 0ull, alg, mode, ctx->num_sms);
+    return buf;
+}
+
+// the variant recorded for `key` in a JSON-lines cache file, if any
+bool cache_find(const char *path, const std::string &key, pbcg_variant *v)
+{
+    FILE *f = path ? fopen(path, "r") : nullptr;
+    if (!f)
+        return false;
+    char line[1024];
+    bool found = false;
+    const std::string want = "\"key\": \"" + key + "\"";
+    while (fgets(line, sizeof line, f)) {
+        if (!strstr(line, want.c_str()))
+            continue;
+        pbcg_variant t{};
+        const char *p;
+        if ((p = strstr(line, "\"staged\": ")) && sscanf(p + 10, "%d", &t.staged) == 1 &&
+            (p = strstr(line, "\"order\": ")) && sscanf(p + 9, "%d", &t.order) == 1 &&
+            (p = strstr(line, "\"ctas_per_sm\": ")) && sscanf(p + 15, "%d", &t.ctas_per_sm) == 1 &&
+            (p = strstr(line, "\"batched_ctas_per_sm\": ")) && sscanf(p + 23, "%d", &t.batched_ctas_per_sm) == 1 &&
+            (p = strstr(line, "\"us_per_iter\": ")) && sscanf(p + 15, "%lf", &t.us_per_iter) == 1 && variant_ok(t)) {
+            *v = t;                  // the last record of a key wins
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_add(const char *path, const std::string &key, const pbcg_variant &v)
+{
+    FILE *f = path ? fopen(path, "a") : nullptr;
+    if (!f)
+        return;
+    fprintf(f,
+            "{\"key\": \"%s\", \"staged\": %d, \"order\": %d, \"ctas_per_sm\": %d, \"batched_ctas_per_sm\": %d, "
+            "\"us_per_iter\": %.4f}\n",
+            key.c_str(), v.staged, v.order, v.ctas_per_sm, v.batched_ctas_per_sm, v.us_per_iter);
+    fclose(f);
+}
+
+int tune_impl(pbcg_ctx *ctx, pbcg_mat *m, int alg, int mode, int32_t nsys, const int32_t *srp, int32_t iters,
+              const char *cache_path, pbcg_variant *chosen, pbcg_variant *tried, int32_t cap, int32_t *ntried)
+{
+    if (!m || !ctx->mats.count(m))
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
+    if (alg != PBCG_ALG_BICGSTAB && alg != PBCG_ALG_PIPELINED && alg != PBCG_ALG_PIPELINED_RR)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", alg);
+    if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", mode);
+    if (iters < 1 || iters > 100000 || nsys < 0 || (nsys > 0 && !srp) || cap < 0 || (cap > 0 && !tried))
+        return fail(ctx, PBCG_ERR_INVALID, "bad tuning arguments");
+    if (nsys > 0) {
+        if (srp[0] != 0 || srp[nsys] != m->n)
+            return fail(ctx, PBCG_ERR_INVALID, "sys_row_ptr must run from 0 to n");
+        for (int k = 0; k < nsys; k++)
+            if (srp[k + 1] <= srp[k])
+                return fail(ctx, PBCG_ERR_INVALID, "sys_row_ptr must increase strictly");
+    }
+    if (ntried)
+        *ntried = 0;
+    CK(cudaSetDevice(ctx->device));
+    const std::string key = tune_key(ctx, m, alg, mode, nsys, srp);
+    pbcg_variant base = variant_of(m);
+    pbcg_variant got;
+    if (cache_find(cache_path, key, &got)) {
+        // the part of the variant this key tunes; the rest stays
+        if (nsys > 0) {
+            base.batched_ctas_per_sm = got.batched_ctas_per_sm;
+        } else {
+            base.staged = got.staged;
+            base.order = got.order;
+            base.ctas_per_sm = got.ctas_per_sm;
+        }
+        base.us_per_iter = got.us_per_iter;
+        got = base;
+        apply_variant(m, got);
+        if (chosen)
+            *chosen = got;
+        return 0;
+    }
+    // candidates, the default first
+    std::vector<pbcg_variant> cand;
+    pbcg_variant d = base;
+    if (nsys > 0) {
+        for (int c : {0, 1}) {
+            d.batched_ctas_per_sm = c;
+            cand.push_back(d);
+        }
+    } else {
+        ClusterShape cs;
+        const bool cluster = alg != PBCG_ALG_PIPELINED_RR && ctx->small_cluster && cluster_shape(ctx, m, alg, mode, &cs);
+        for (int st : {1, 0}) {
+            if (st == 0 && (!m->narrow || cluster))
+                continue;           // nothing to stage either way
+            for (int alt : {0, 1}) {
+                if (alt && cluster)
+                    continue;
+                for (int c : {0, 1}) {
+                    if (c && cluster)
+                        continue;
+                    d.staged = st;
+                    // the order other than this staging's default
+                    d.order = alt ? ((m->narrow && st) ? 2 : 1) : 0;
+                    d.ctas_per_sm = c;
+                    cand.push_back(d);
+                }
+            }
+        }
+    }
+    // trial system: b = A * ones, x0 = 0, no stop (tol far below any residual)
+    struct Buf {
+        double *p = nullptr;
+        ~Buf() { if (p) cudaFree(p); }
+    } one, bb, xx;
+    const size_t n = (size_t)m->n;
+    CK(cudaMalloc(&one.p, sizeof(double) * n));
+    CK(cudaMalloc(&bb.p, sizeof(double) * n));
+    CK(cudaMalloc(&xx.p, sizeof(double) * n));
+    {
+        std::vector<double> h(n, 1.0);
+        CK(cudaMemcpy(one.p, h.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    }
+    int rc;
+    if ((rc = pbcg_spmv(ctx, m, one.p, bb.p)))
+        return rc;
+    std::vector<double> tols((size_t)std::max(nsys, 1), 1e-300);
+    std::vector<pbcg_result> res((size_t)std::max(nsys, 1));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } ev{e0, e1};
+    auto trial = [&](bool timed, double *us) -> int {
+        CK(cudaMemsetAsync(xx.p, 0, sizeof(double) * n, ctx->stream));
+        if (timed)
+            CK(cudaEventRecord(e0, ctx->stream));
+        int r = nsys > 0 ? solve_batched_impl(ctx, m, nsys, srp, bb.p, xx.p, tols.data(), iters, alg, mode, res.data())
+                         : solve_impl(ctx, m, bb.p, xx.p, 1e-300, iters, alg, mode, res.data(), nullptr);
+        if (r < 0)
+            return r;
+        if (timed) {
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            int its = 0;
+            for (auto &q : res)
+                its = std::max(its, q.iters);
+            *us = 1e3 * ms / std::max(its, 1);
+        }
+        return 0;
+    };
+    pbcg_variant best = base;
+    double best_us = 1e300;
+    int k = 0;
+    for (auto &c : cand) {
+        apply_variant(m, c);
+        double us = 0.0;
+        if ((rc = trial(false, &us)) || (rc = trial(true, &us))) {
+            apply_variant(m, base);
+            return rc;
+        }
+        c.us_per_iter = us;
+        if (tried && k < cap)
+            tried[k] = c;
+        k++;
+        if (us < best_us) {
+            best_us = us;
+            best = c;
+        }
+    }
+    if (ntried)
+        *ntried = k;
+    apply_variant(m, best);
+    cache_add(cache_path, key, best);
+    if (chosen)
+        *chosen = best;
     return 0;
 }
 
@@ -3189,6 +3448,41 @@ void pbcg_part_destroy(pbcg_part *part)
     cudaSetDevice(part->ctx->device);
     cudaStreamSynchronize(part->ctx->stream);
     part_release(part);
+}
+
+int pbcg_set_variant(pbcg_ctx *ctx, pbcg_mat *m, const pbcg_variant *v)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!m || !ctx->mats.count(m))
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle");
+    pbcg_variant d{1, 0, 0, 0, 0.0};
+    if (v && !variant_ok(*v))
+        return fail(ctx, PBCG_ERR_INVALID, "variant field out of range");
+    apply_variant(m, v ? *v : d);
+    if (v)
+        m->v_us = 0.0;
+    return 0;
+}
+
+int pbcg_get_variant(pbcg_ctx *ctx, const pbcg_mat *m, pbcg_variant *out)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!m || !out || !ctx->mats.count(const_cast<pbcg_mat *>(m)))
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle or NULL output");
+    *out = variant_of(m);
+    return 0;
+}
+
+int pbcg_tune(pbcg_ctx *ctx, pbcg_mat *A, int alg, int dot_mode, int32_t nsys, const int32_t *sys_row_ptr,
+              int32_t iters, const char *cache_path, pbcg_variant *chosen, pbcg_variant *tried, int32_t cap,
+              int32_t *ntried)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    NvtxRange trace("pbcg_tune");
+    return tune_impl(ctx, A, alg, dot_mode, nsys, sys_row_ptr, iters, cache_path, chosen, tried, cap, ntried);
 }
 
 }  // extern "C"

@@ -84,7 +84,8 @@ struct Ctl {
     unsigned long long cond;            // cudaGraphConditionalHandle of the loop
     double *hist;
     int hist_cap, need_t;               // need_t: t0 = A w0 still to be formed (pool slots)
-    int gen, pad_i;                     // gen: admission number of a pool slot's occupant
+    int gen;                            // admission number of a pool slot's occupant
+    int order;                          // tile order of the staged passes: 0 default, 1 round-robin, 2 claimed
 };
 
 // grid-wide merge workspace
@@ -115,6 +116,16 @@ struct Mat {
 struct Vecs {
     double *x, *b, *r0, *r, *w, *t, *p, *s, *z, *v, *y, *q;
 };
+
+// Whether a staged pass hands its tiles out from a grid-wide counter (claimed
+// in index order) rather than round-robin: by default only when its tiles are
+// not staged (wide rows); Ctl::order overrides (a tuned launch variant).
+// Either order gives bit-identical exact dots.
+template <bool MATS>
+__device__ __forceinline__ bool claimed_tiles(const Ctl *c)
+{
+    return c->order == 2 || (c->order == 0 && !MATS);
+}
 
 // residual replacement at the start of iteration it (every rr_period iterations, never at 0)
 __device__ __forceinline__ bool rr_now(const Ctl *c)
@@ -1334,7 +1345,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         D.template add2<true>(sh, 1, y, y, dy, dy, act);
         D.template add2<false>(sh, 2, r0i, si, dr, ds, act);
         D.template add2<false>(sh, 3, r0i, zi, dr, dz, act);
-    }, MATS ? nullptr : &wk->tile_next);
+    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr);
     if (!finalize<4, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1379,7 +1390,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
         D.template add_row<3, false, false, true>(sh, act, r0i, rn, dr0, dr, r0i, wn, dr0, dw, rn, rn, &dr, &dr);
-    }, MATS ? nullptr : &wk->tile_next);
+    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr);
     if (!finalize<3, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1483,7 +1494,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dr = decode(r0i), ds = decode(si);
         D.template add2<false>(sh, 0, r0i, si, dr, ds, act);
-    }, MATS ? nullptr : &wk->tile_next);
+    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr);
     if (!finalize<1, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1519,7 +1530,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dq = decode(qi), dy = decode(yi);
         D.template add_row<2, false, true>(sh, act, qi, yi, dq, dy, yi, yi, dy, dy);
-    }, MATS ? nullptr : &wk->tile_next);
+    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr);
     if (!finalize<2, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)

@@ -28,7 +28,7 @@ EXPORTS = ("pbcg_create", "pbcg_destroy", "pbcg_last_error", "pbcg_csr_upload", 
            "pbcg_profile_solve", "pbcg_dot_noalloc", "pbcg_set_option", "pbcg_pool_create", "pbcg_pool_destroy",
            "pbcg_pool_admit", "pbcg_pool_step", "pbcg_pool_poll", "pbcg_pool_result", "pbcg_pool_history",
            "pbcg_pool_room", "pbcg_check_wait", "pbcg_part_plan", "pbcg_part_create", "pbcg_part_solve",
-           "pbcg_part_destroy")
+           "pbcg_part_destroy", "pbcg_set_variant", "pbcg_get_variant", "pbcg_tune")
 
 
 class PbcgError(RuntimeError):
@@ -54,6 +54,11 @@ _ALLREDUCE = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctyp
 _ALLTOALLV = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                               ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                               ctypes.POINTER(ctypes.c_int64))
+
+
+class _Variant(ctypes.Structure):
+    _fields_ = [("staged", ctypes.c_int32), ("order", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("batched_ctas_per_sm", ctypes.c_int32), ("us_per_iter", ctypes.c_double)]
 
 
 class _Comm(ctypes.Structure):
@@ -119,6 +124,13 @@ def load_library(path: str = LIB_PATH):
     lib.pbcg_part_solve.restype = ctypes.c_int
     lib.pbcg_part_destroy.argtypes = [P]
     lib.pbcg_part_destroy.restype = None
+    lib.pbcg_set_variant.argtypes = [P, P, ctypes.POINTER(_Variant)]
+    lib.pbcg_set_variant.restype = ctypes.c_int
+    lib.pbcg_get_variant.argtypes = [P, P, ctypes.POINTER(_Variant)]
+    lib.pbcg_get_variant.restype = ctypes.c_int
+    lib.pbcg_tune.argtypes = [P, P, ctypes.c_int, ctypes.c_int, i32, P, i32, ctypes.c_char_p,
+                              ctypes.POINTER(_Variant), P, i32, ctypes.POINTER(i32)]
+    lib.pbcg_tune.restype = ctypes.c_int
     return lib
 
 
@@ -206,6 +218,24 @@ def dot_noalloc(a, b, out, mode: int = EXACT, stream=None) -> int:
         raise ValueError("out needs at least one entry")
     s = ctypes.c_void_p(stream) if stream else None
     return _lib.pbcg_dot_noalloc(n, _ptr(a), _ptr(b), int(mode), _ptr(out), s)
+
+
+@dataclass
+class Variant:
+    """A launch variant of the passes (pbcg_variant): none changes exact results."""
+    staged: int = 1
+    order: int = 0
+    ctas_per_sm: int = 0
+    batched_ctas_per_sm: int = 0
+    us_per_iter: float = 0.0
+
+    def _c(self):
+        return _Variant(int(self.staged), int(self.order), int(self.ctas_per_sm), int(self.batched_ctas_per_sm),
+                        float(self.us_per_iter))
+
+    @staticmethod
+    def _of(v):
+        return Variant(v.staged, v.order, v.ctas_per_sm, v.batched_ctas_per_sm, v.us_per_iter)
 
 
 @dataclass
@@ -312,6 +342,30 @@ class Context:
         out = ctypes.c_double(0.0)
         self._check(_lib.pbcg_dot(self.handle, n, _ptr(a), _ptr(b), int(mode), ctypes.byref(out)))
         return out.value
+
+    def set_variant(self, mat: Matrix, v: "Variant" = None):
+        """Set mat's launch variant (None: the default)."""
+        c = v._c() if v is not None else None
+        self._check(_lib.pbcg_set_variant(self.handle, mat.handle, ctypes.byref(c) if c is not None else None))
+
+    def get_variant(self, mat: Matrix) -> "Variant":
+        v = _Variant()
+        self._check(_lib.pbcg_get_variant(self.handle, mat.handle, ctypes.byref(v)))
+        return Variant._of(v)
+
+    def tune(self, mat: Matrix, alg: int = PIPELINED, mode: int = EXACT, iters: int = 30, sys_row_ptr=None,
+             cache_path: str = None):
+        """pbcg_tune: time the launch variants on a trial solve and keep the
+        fastest for mat.  Returns (chosen Variant, [tried Variants])."""
+        srp = None if sys_row_ptr is None else _host(sys_row_ptr, np.int32)
+        nsys = 0 if srp is None else _count(srp) - 1
+        cap = 16
+        tried = (_Variant * cap)()
+        ch, nt = _Variant(), ctypes.c_int32(0)
+        self._check(_lib.pbcg_tune(self.handle, mat.handle, int(alg), int(mode), nsys, _ptr(srp), int(iters),
+                                   cache_path.encode() if cache_path else None, ctypes.byref(ch),
+                                   ctypes.cast(tried, ctypes.c_void_p), cap, ctypes.byref(nt)))
+        return Variant._of(ch), [Variant._of(tried[i]) for i in range(min(nt.value, cap))]
 
     def check_wait(self, probes: int):
         """Run the bounded device wait on a phase nothing completes; returns (expired, seconds)."""
