@@ -413,6 +413,36 @@ int pbcg_tune(pbcg_ctx *ctx, pbcg_mat *A, int alg, int dot_mode, int32_t nsys, c
               int32_t *ntried);
 
 /*
+ * Memory-safety checks (compute-sanitizer is not available on the target
+ * machines, so the library checks itself).
+ *
+ * pbcg_mat_check (every build): validate A's device layout with a read-only
+ * kernel -- slice offsets non-decreasing in whole 32-entry columns, every row
+ * no longer than its slice, every stored column inside the gathered vector,
+ * every tile record matching the slice offsets with its gather blocks inside
+ * the vector, every staged local index naming its entry's column.  *word
+ * receives 0, or the first failure as kind << 56 | position (kinds: 1
+ * column, 2 local index, 3 row length, 4 slice offsets, 5 gather block, 6
+ * tile record).
+ *
+ * The checked build (libpbcg_checked.so, compiled with PBCG_CHECKS=1) also
+ * checks, inside every kernel, each index it takes from the layout, a tile
+ * record or a tile list before using it (a column, a staged local index, a
+ * row length, a slice's span in its stage, a gather block, a tile, a tile's
+ * system, a cluster CTA's entry count); a failure is recorded in a device
+ * word and the access skipped, never trapped.  pbcg_check_word reads that
+ * word (*enabled = 1 in the checked build, 0 otherwise, when *word is always
+ * 0; same kinds as above, plus 7 system and 8 cluster) and clears it when
+ * reset != 0.  pbcg_debug_set_col (checked build only; INVALID otherwise)
+ * overwrites stored column `entry` of A's device layout, so that a test can
+ * see the checks fire.
+ * Errors: INVALID (unknown matrix, NULL output), CUDA.
+ */
+int pbcg_mat_check(pbcg_ctx *ctx, const pbcg_mat *A, uint64_t *word);
+int pbcg_check_word(pbcg_ctx *ctx, int reset, int32_t *enabled, uint64_t *word);
+int pbcg_debug_set_col(pbcg_ctx *ctx, pbcg_mat *A, int64_t entry, int32_t col);
+
+/*
  * pbcg_dot_noalloc: the dot product of pbcg_dot for callers that cannot
  * allocate device memory (code inside another allocator's arena, a fixed or
  * capped memory budget, or a loop that must not enter the allocator, since

@@ -68,6 +68,7 @@ struct NvtxRange {
 
 struct pbcg_mat {
     int n;
+    int ncols;             // columns: n, or n plus the halo of a partition block
     long long nnz;
     int nslices;
     long long padded;      // stored SELL-32 entries (nnz plus padding)
@@ -173,6 +174,7 @@ Mat mat_of(const pbcg_mat *m)
 {
     Mat A;
     A.n = m->n;
+    A.ncols = m->ncols;
     A.nslices = m->nslices;
     A.sl_off = m->sl_off;
     A.rlen = m->rlen;
@@ -1242,6 +1244,7 @@ Mat layout_mat(const BatchLayout *L)
 {
     Mat A;
     A.n = L->n_int;
+    A.ncols = L->n_int;
     A.nslices = L->nslices;
     A.sl_off = L->sl_off;
     A.rlen = L->rlen;
@@ -1679,6 +1682,7 @@ Mat pool_mat(const pbcg_pool *P)
 {
     Mat A;
     A.n = P->max_tiles * TILE_ROWS;
+    A.ncols = A.n;
     A.nslices = P->max_tiles * TILE_SLICES;
     A.sl_off = P->sl_off;
     A.sl_w = P->sl_w;
@@ -1826,6 +1830,7 @@ int make_mat(pbcg_ctx *ctx, int n, int ncols, std::vector<int32_t> &&hrp, std::v
         return fail(ctx, PBCG_ERR_INVALID, "padded matrix exceeds 2^31 entries");
     pbcg_mat *m = new pbcg_mat();
     m->n = n;
+    m->ncols = ncols > n ? ncols : n;
     m->nnz = nnz;
     m->nslices = S.nslices;
     m->padded = S.padded;
@@ -3483,6 +3488,78 @@ int pbcg_tune(pbcg_ctx *ctx, pbcg_mat *A, int alg, int dot_mode, int32_t nsys, c
         return PBCG_ERR_INVALID;
     NvtxRange trace("pbcg_tune");
     return tune_impl(ctx, A, alg, dot_mode, nsys, sys_row_ptr, iters, cache_path, chosen, tried, cap, ntried);
+}
+
+int pbcg_check_word(pbcg_ctx *ctx, int reset, int32_t *enabled, uint64_t *word)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!enabled || !word)
+        return fail(ctx, PBCG_ERR_INVALID, "NULL output");
+    *enabled = PBCG_CHECKS;
+    *word = 0;
+#if PBCG_CHECKS
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned long long w = 0;
+    CK(cudaMemcpyFromSymbol(&w, g_check_word, sizeof w));
+    *word = (uint64_t)w;
+    if (reset) {
+        const unsigned long long z = 0;
+        CK(cudaMemcpyToSymbol(g_check_word, &z, sizeof z));
+    }
+#else
+    (void)reset;
+#endif
+    return 0;
+}
+
+int pbcg_mat_check(pbcg_ctx *ctx, const pbcg_mat *m, uint64_t *word)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+    if (!m || !word || !ctx->mats.count(const_cast<pbcg_mat *>(m)))
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle or NULL output");
+    CK(cudaSetDevice(ctx->device));
+    unsigned long long *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(unsigned long long)));
+    Mat A = mat_of(m);
+    long long padded = m->padded;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) {
+        void *args[3] = {&A, &padded, &d};
+        e = cudaLaunchKernel((void *)k_mat_check, dim3(ctx->num_sms * 4), dim3(256), args, 0, ctx->stream);
+    }
+    unsigned long long h = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return fail(ctx, PBCG_ERR_CUDA, "pbcg_mat_check: %s", cudaGetErrorString(e));
+    *word = (uint64_t)h;
+    return 0;
+}
+
+int pbcg_debug_set_col(pbcg_ctx *ctx, pbcg_mat *m, int64_t entry, int32_t col)
+{
+    if (!ctx)
+        return PBCG_ERR_INVALID;
+#if PBCG_CHECKS
+    if (!m || !ctx->mats.count(m) || entry < 0 || entry >= m->padded)
+        return fail(ctx, PBCG_ERR_INVALID, "unknown matrix handle or entry outside the layout");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(m->ci + entry, &col, sizeof col, cudaMemcpyHostToDevice));
+    free_loop(ctx->ws.loop);
+    return 0;
+#else
+    (void)m;
+    (void)entry;
+    (void)col;
+    return fail(ctx, PBCG_ERR_INVALID, "pbcg_debug_set_col needs the checked build");
+#endif
 }
 
 }  // extern "C"

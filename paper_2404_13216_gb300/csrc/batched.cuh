@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(THREADS) k_batched(Mat A, Vecs V, Batch B)
                 j++;
             t = B.lv_t0[j] + (q - B.lv_pre[j]);
         }
-        const int sys = B.tile_sys[t];
-        if (sys < 0) {
+        const int sys = PBCG_IN(t, B.ntiles, CHK_TILE) ? B.tile_sys[t] : -1;
+        if (sys < 0 || !PBCG_IN(sys, B.nsys, CHK_SYS)) {
             q++;
             continue;                    // unallocated tile of a pool
         }
@@ -496,8 +496,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_bstaged(Mat A, Vecs V, Batch B)
                 }
                 t = B.lv_t0[lo] + (q - B.lv_pre[lo]);
             }
-            const int sys = B.tile_sys[t];
-            if (sys < 0 || !Step::wants(B.ctl + sys))
+            const int sys = PBCG_IN(t, B.ntiles, CHK_TILE) ? B.tile_sys[t] : -1;
+            if (sys < 0 || !PBCG_IN(sys, B.nsys, CHK_SYS) || !Step::wants(B.ctl + sys))
                 continue;
             BEntry &e = mine[nm++];
             e.tile = t;

@@ -149,11 +149,14 @@ __device__ __forceinline__ ClusterRows cluster_load(const Mat &A, const Vecs &V,
     R.mlen = reinterpret_cast<int *>(R.mcode + emax);
     R.msoff = R.mlen + R.rows;
     const int gs0 = min((int)blockIdx.x * R.nsl, A.nslices), gs1 = min(gs0 + R.nsl, A.nslices);
-    const int e0 = A.sl_off[gs0], ne = A.sl_off[gs1] - e0;
+    const int e0 = A.sl_off[gs0];
+    const int ne = PBCG_IN(A.sl_off[gs1] - e0, emax + 1, CHK_CLUSTER) ? A.sl_off[gs1] - e0 : 0;
     for (int t = threadIdx.x; t <= R.nsl; t += THREADS)
         R.msoff[t] = A.sl_off[min(gs0 + t, gs1)] - e0;
     for (int e = threadIdx.x; e < ne; e += THREADS) {
-        const int col = A.ci[e0 + e];
+        int col = A.ci[e0 + e];
+        if (!PBCG_IN(col, A.n, CHK_COL))
+            col = 0;
         R.mva[e] = A.va[e0 + e];
         R.mcode[e] = ((uint32_t)(col >> lg) << 16) | (uint32_t)(col & (R.rows - 1));
     }

@@ -42,6 +42,47 @@ namespace pbcg {
 #define PBCG_INTERLEAVE 1               // 1: warp w takes slices w, w + W, ...; 0: one contiguous run per warp
 #endif
 
+// ---------------------------------------------------------------------------
+// device-side bounds checks (a build with PBCG_CHECKS=1 only)
+//
+// Every index a kernel takes from the matrix layout, a tile record or a tile
+// list is checked before it is used; a failed check records what failed
+// (the first failure: kind << 56 | the offending value) in g_check_word,
+// which the host reads with pbcg_check_word, and the access is skipped (a
+// clamped index stands in).  No trap, no assert: the context stays usable.
+// In the ordinary build the checks compile to nothing.
+// ---------------------------------------------------------------------------
+#ifndef PBCG_CHECKS
+#define PBCG_CHECKS 0
+#endif
+enum : int {
+    CHK_COL = 1,        // a column index outside the gathered vector
+    CHK_LOCAL = 2,      // a staged local column outside the tile's staged blocks
+    CHK_RLEN = 3,       // a row longer than its slice
+    CHK_SPAN = 4,       // a slice's entries outside its tile's staged span
+    CHK_BLOCK = 5,      // a gather block outside the vector
+    CHK_TILE = 6,       // a tile index outside the matrix
+    CHK_SYS = 7,        // a tile's system outside the batch
+    CHK_CLUSTER = 8     // a cluster row's entries or owner outside the cluster
+};
+#if PBCG_CHECKS
+static __device__ unsigned long long g_check_word;
+static __device__ __noinline__ void check_fail(int kind, long long v)
+{
+    atomicCAS(&g_check_word, 0ull, ((unsigned long long)kind << 56) | ((unsigned long long)v & ((1ull << 56) - 1)));
+}
+__device__ __forceinline__ bool check_in(long long v, long long hi, int kind)
+{
+    const bool ok = v >= 0 && v < hi;
+    if (!ok)
+        check_fail(kind, v);
+    return ok;
+}
+#define PBCG_IN(v, hi, kind) check_in((long long)(v), (long long)(hi), (kind))
+#else
+#define PBCG_IN(v, hi, kind) true
+#endif
+
 constexpr int THREADS = 256;
 constexpr int WARPS = THREADS / 32;
 constexpr int MAXD = 4;                 // most dots merged in one pass
@@ -102,6 +143,7 @@ struct Work {
 // SELL-32 matrix in the solver's (possibly permuted) row order
 struct Mat {
     int n;                               // rows
+    int ncols;                           // entries of the gathered vector (n, or n plus a partition's halo)
     int nslices;                         // ceil(n / 32)
     const int *__restrict__ sl_off;      // [nslices + 1] first entry of each slice; width = diff / 32
     const int *__restrict__ rlen;        // [nslices * 32] row lengths (0 past n)
@@ -180,23 +222,26 @@ __device__ __forceinline__ RowRef row_ref(const Mat &A, int s, int lane)
 __device__ __forceinline__ double spmv_row(const Mat &A, const RowRef &R, const double *__restrict__ x)
 {
     double acc = 0.0;
+    const int len = PBCG_IN(R.len, R.width + 1, CHK_RLEN) ? R.len : R.width;
     for (int j0 = 0; j0 < R.width; j0 += UNR) {      // warp-uniform bound
         int c[UNR];
         double v[UNR], xv[UNR];
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
-            if (j0 + j < R.len) {
+            if (j0 + j < len) {
                 c[j] = __ldg(A.ci + R.base + (j0 + j) * 32);
                 v[j] = __ldg(A.va + R.base + (j0 + j) * 32);
+                if (!PBCG_IN(c[j], A.ncols, CHK_COL))
+                    c[j] = 0;
             }
         }
 #pragma unroll
         for (int j = 0; j < UNR; j++)
-            if (j0 + j < R.len)
+            if (j0 + j < len)
                 xv[j] = __ldg(x + c[j]);
 #pragma unroll
         for (int j = 0; j < UNR; j++)
-            if (j0 + j < R.len)
+            if (j0 + j < len)
                 acc = __fma_rn(v[j], xv[j], acc);
     }
     return acc;
@@ -207,26 +252,29 @@ __device__ __forceinline__ double spmv_row_axpy(const Mat &A, const RowRef &R, d
                                                 const double *__restrict__ s, const double *__restrict__ r)
 {
     double acc = 0.0;
+    const int len = PBCG_IN(R.len, R.width + 1, CHK_RLEN) ? R.len : R.width;
     for (int j0 = 0; j0 < R.width; j0 += UNR) {
         int c[UNR];
         double v[UNR], xs[UNR], xr[UNR];
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
-            if (j0 + j < R.len) {
+            if (j0 + j < len) {
                 c[j] = __ldg(A.ci + R.base + (j0 + j) * 32);
                 v[j] = __ldg(A.va + R.base + (j0 + j) * 32);
+                if (!PBCG_IN(c[j], A.ncols, CHK_COL))
+                    c[j] = 0;
             }
         }
 #pragma unroll
         for (int j = 0; j < UNR; j++) {
-            if (j0 + j < R.len) {
+            if (j0 + j < len) {
                 xs[j] = __ldg(s + c[j]);
                 xr[j] = __ldg(r + c[j]);
             }
         }
 #pragma unroll
         for (int j = 0; j < UNR; j++)
-            if (j0 + j < R.len)
+            if (j0 + j < len)
                 acc = __fma_rn(v[j], __fma_rn(na, xs[j], xr[j]), acc);
     }
     return acc;
@@ -772,6 +820,65 @@ static __global__ void __launch_bounds__(THREADS) k_spmv(Mat A, const double *x,
     }
 }
 
+// Device-side validation of an uploaded SELL-32 layout (every build): slice
+// offsets non-decreasing in whole 32-entry columns, every row no longer than
+// its slice (rows past n empty), every stored column inside the gathered
+// vector, every tile record matching the slice offsets with gather blocks
+// inside the vector, and every staged local index pointing at the entry's
+// column.  *word receives the first failure found (CHK_* << 56 | position),
+// or stays 0.  Reads only inside the arrays' sizes.
+static __global__ void k_mat_check(Mat A, long long padded, unsigned long long *word)
+{
+    auto bad = [&](int kind, long long pos) {
+        atomicCAS(word, 0ull, ((unsigned long long)kind << 56) | ((unsigned long long)pos & ((1ull << 56) - 1)));
+    };
+    const int ntiles = (A.nslices + TILE_SLICES - 1) / TILE_SLICES;
+    const long long nrows = (long long)A.nslices * 32;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nrows; p += stride) {
+        const int s = (int)(p >> 5), lane = (int)(p & 31);
+        const int o0 = A.sl_off[s], o1 = A.sl_off[s + 1];
+        if (o1 < o0 || ((o1 - o0) & 31) || o1 > padded) {
+            bad(CHK_SPAN, s);
+            continue;
+        }
+        const int width = (o1 - o0) >> 5, len = A.rlen[p];
+        if (len < 0 || len > width || (p >= A.n && len != 0)) {
+            bad(CHK_RLEN, p);
+            continue;
+        }
+        for (int j = 0; j < len; j++) {
+            const long long e = o0 + lane + 32ll * j;
+            const int c = A.ci[e];
+            if (c < 0 || c >= A.ncols)
+                bad(CHK_COL, e);
+        }
+    }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; A.tmeta && t < ntiles; t += stride) {
+        const int *r = A.tmeta + t * TMETA;
+        const int sa = (int)t * TILE_SLICES, sb = min(A.nslices, sa + TILE_SLICES);
+        if (r[0] != A.sl_off[sa] || r[1] != A.sl_off[sb]) {
+            bad(CHK_TILE, t);
+            continue;
+        }
+        int nblk = 0;
+        for (int g = 0; g < GMAX; g++) {
+            if (r[2 + g] < 0)
+                continue;
+            nblk++;
+            if (r[2 + g] >= (A.ncols + TILE_ROWS - 1) / TILE_ROWS)
+                bad(CHK_BLOCK, t);
+        }
+        if (nblk == 0 || !A.lci || r[1] - r[0] > MCAP)
+            continue;
+        for (int e = r[0]; e < r[1]; e++) {
+            const int l = A.lci[e], g = l / TILE_ROWS;
+            if (g >= nblk || r[2 + g] * TILE_ROWS + l % TILE_ROWS != A.ci[e])
+                bad(CHK_LOCAL, e);
+        }
+    }
+}
+
 // dst[p] = src[perm[p]] (into solver order)
 static __global__ void k_gather(int n, const int *__restrict__ perm, const double *__restrict__ src, double *dst)
 {
@@ -913,6 +1020,8 @@ struct TilePipe {
         info[k].staged = staged;
         info[k].windowed = windowed;
         info[k].tile = tile;
+        info[k].span = span;
+        info[k].nblk = nblk;
         uint32_t bytes = (uint32_t)nv * TILE_ROWS * 8 + L::RLEN + L::SLOFF + (staged ? (uint32_t)span * (windowed ? 10u : 12u) : 0u) +
                          (uint32_t)nblk * TILE_ROWS * 8 + (tn >= 0 ? TMETA * 4u : 0u);
         fence_async_shared();
@@ -935,9 +1044,12 @@ struct TilePipe {
         if (windowed) {
 #pragma unroll
             for (int g = 0; g < GMAX; g++)
-                if (rec[2 + g] >= 0)
-                    bulk_g2s(stage(k) + L::VEC + (size_t)g * TILE_ROWS * 8, gx + (size_t)rec[2 + g] * TILE_ROWS,
+                if (rec[2 + g] >= 0) {
+                    // (a checked build copies block 0 in place of a block outside the vector)
+                    const int blk = PBCG_IN(rec[2 + g], (A.ncols + TILE_ROWS - 1) / TILE_ROWS, CHK_BLOCK) ? rec[2 + g] : 0;
+                    bulk_g2s(stage(k) + L::VEC + (size_t)g * TILE_ROWS * 8, gx + (size_t)blk * TILE_ROWS,
                              TILE_ROWS * 8, &bar[k]);
+                }
         }
     }
 
@@ -948,9 +1060,16 @@ struct TilePipe {
         const int off = so[warp];
         // the slice's width: explicit for pools (a tile's last slice need not be
         // followed by the same slot's entries), else the distance to the next slice
-        const int width = A.sl_w ? __ldg(A.sl_w + (size_t)(info[k].tile * TILE_SLICES + warp)) : (so[warp + 1] - off) >> 5;
-        const int len = rlen(k)[warp * 32 + lane];
+        int width = A.sl_w ? __ldg(A.sl_w + (size_t)(info[k].tile * TILE_SLICES + warp)) : (so[warp + 1] - off) >> 5;
+        int len = rlen(k)[warp * 32 + lane];
         const bool st = info[k].staged;
+#if PBCG_CHECKS
+        if (!PBCG_IN(len, width + 1, CHK_RLEN))
+            len = width;
+        if (st && !(PBCG_IN(off - info[k].e0, info[k].span + 1, CHK_SPAN) &&
+                    PBCG_IN(off - info[k].e0 + 32 * width, info[k].span + 1, CHK_SPAN)))
+            width = len = 0;
+#endif
         const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
         const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
         double acc = 0.0;
@@ -960,8 +1079,12 @@ struct TilePipe {
             for (int j0 = 0; j0 < width; j0 += UNR) {
 #pragma unroll
                 for (int j = 0; j < UNR; j++)
-                    if (j0 + j < len)
-                        acc = __fma_rn(vp[(j0 + j) * 32], xw[lp[(j0 + j) * 32]], acc);
+                    if (j0 + j < len) {
+                        int l = lp[(j0 + j) * 32];
+                        if (!PBCG_IN(l, info[k].nblk * TILE_ROWS, CHK_LOCAL))
+                            l = 0;
+                        acc = __fma_rn(vp[(j0 + j) * 32], xw[l], acc);
+                    }
             }
             return acc;
         }
@@ -988,6 +1111,10 @@ struct TilePipe {
             }
 #pragma unroll
             for (int j = 0; j < UNR; j++)
+                if (j0 + j < len && !PBCG_IN(c[j], A.ncols, CHK_COL))
+                    c[j] = 0;
+#pragma unroll
+            for (int j = 0; j < UNR; j++)
                 if (j0 + j < len)
                     xv[j] = __ldg(x + c[j]);
 #pragma unroll
@@ -1005,9 +1132,16 @@ struct TilePipe {
     {
         const int *so = sloff(k);
         const int off = so[warp];
-        const int width = A.sl_w ? __ldg(A.sl_w + (size_t)(info[k].tile * TILE_SLICES + warp)) : (so[warp + 1] - off) >> 5;
-        const int len = rlen(k)[warp * 32 + lane];
+        int width = A.sl_w ? __ldg(A.sl_w + (size_t)(info[k].tile * TILE_SLICES + warp)) : (so[warp + 1] - off) >> 5;
+        int len = rlen(k)[warp * 32 + lane];
         const bool st = info[k].staged;
+#if PBCG_CHECKS
+        if (!PBCG_IN(len, width + 1, CHK_RLEN))
+            len = width;
+        if (st && !(PBCG_IN(off - info[k].e0, info[k].span + 1, CHK_SPAN) &&
+                    PBCG_IN(off - info[k].e0 + 32 * width, info[k].span + 1, CHK_SPAN)))
+            width = len = 0;
+#endif
         const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
         const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
         double acc = 0.0;
@@ -1032,6 +1166,10 @@ struct TilePipe {
                     }
                 }
             }
+#pragma unroll
+            for (int j = 0; j < UNR; j++)
+                if (j0 + j < len && !PBCG_IN(c[j], A.ncols, CHK_COL))
+                    c[j] = 0;
 #pragma unroll
             for (int j = 0; j < UNR; j++) {
                 if (j0 + j < len) {

@@ -119,6 +119,8 @@ struct StageInfo {
     int staged;      // 1 if the tile's ci/va are in shared memory
     int windowed;    // 1 if the gathered vector's blocks are in shared memory (ci local)
     int tile;        // the tile held
+    int span;        // SELL entries of the tile (bounds checks)
+    int nblk;        // gather blocks staged (bounds checks)
 };
 
 }  // namespace pbcg

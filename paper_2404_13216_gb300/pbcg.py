@@ -4,6 +4,9 @@ Every step of the solver runs in the library's CUDA kernels; this module moves
 pointers and sizes across the C ABI.  Arrays may be numpy arrays (host) or
 torch tensors (host or CUDA; their data_ptr is passed through).  Loading the
 module raises if the library has not been built -- there is no fallback.
+The environment variable PBCG_LIB, when set, names another build of the
+library to load instead (for example _build/libpbcg_checked.so, the build
+with device-side bounds checks); results do not change.
 """
 from __future__ import annotations
 
@@ -14,7 +17,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libpbcg.so")
+LIB_PATH = os.environ.get("PBCG_LIB") or os.path.join(_HERE, "_build", "libpbcg.so")
 
 OK, MAXIT, BREAKDOWN, NONFINITE = 0, 1, 2, 3
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_COMM = -1, -2, -3, -4, -5
@@ -28,7 +31,8 @@ EXPORTS = ("pbcg_create", "pbcg_destroy", "pbcg_last_error", "pbcg_csr_upload", 
            "pbcg_profile_solve", "pbcg_dot_noalloc", "pbcg_set_option", "pbcg_pool_create", "pbcg_pool_destroy",
            "pbcg_pool_admit", "pbcg_pool_step", "pbcg_pool_poll", "pbcg_pool_result", "pbcg_pool_history",
            "pbcg_pool_room", "pbcg_check_wait", "pbcg_part_plan", "pbcg_part_create", "pbcg_part_solve",
-           "pbcg_part_destroy", "pbcg_set_variant", "pbcg_get_variant", "pbcg_tune")
+           "pbcg_part_destroy", "pbcg_set_variant", "pbcg_get_variant", "pbcg_tune", "pbcg_mat_check",
+           "pbcg_check_word", "pbcg_debug_set_col")
 
 
 class PbcgError(RuntimeError):
@@ -131,6 +135,12 @@ def load_library(path: str = LIB_PATH):
     lib.pbcg_tune.argtypes = [P, P, ctypes.c_int, ctypes.c_int, i32, P, i32, ctypes.c_char_p,
                               ctypes.POINTER(_Variant), P, i32, ctypes.POINTER(i32)]
     lib.pbcg_tune.restype = ctypes.c_int
+    lib.pbcg_mat_check.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.pbcg_mat_check.restype = ctypes.c_int
+    lib.pbcg_check_word.argtypes = [P, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint64)]
+    lib.pbcg_check_word.restype = ctypes.c_int
+    lib.pbcg_debug_set_col.argtypes = [P, P, i64, i32]
+    lib.pbcg_debug_set_col.restype = ctypes.c_int
     return lib
 
 
@@ -366,6 +376,22 @@ class Context:
                                    cache_path.encode() if cache_path else None, ctypes.byref(ch),
                                    ctypes.cast(tried, ctypes.c_void_p), cap, ctypes.byref(nt)))
         return Variant._of(ch), [Variant._of(tried[i]) for i in range(min(nt.value, cap))]
+
+    def mat_check(self, mat: Matrix) -> int:
+        """pbcg_mat_check: 0, or the first layout failure (kind << 56 | position)."""
+        w = ctypes.c_uint64(0)
+        self._check(_lib.pbcg_mat_check(self.handle, mat.handle, ctypes.byref(w)))
+        return w.value
+
+    def check_word(self, reset: bool = False):
+        """pbcg_check_word: (checks compiled in, first failed in-kernel check or 0)."""
+        en, w = ctypes.c_int32(0), ctypes.c_uint64(0)
+        self._check(_lib.pbcg_check_word(self.handle, int(bool(reset)), ctypes.byref(en), ctypes.byref(w)))
+        return bool(en.value), w.value
+
+    def debug_set_col(self, mat: Matrix, entry: int, col: int):
+        """pbcg_debug_set_col (checked build): overwrite one stored column of mat's device layout."""
+        self._check(_lib.pbcg_debug_set_col(self.handle, mat.handle, int(entry), int(col)))
 
     def check_wait(self, probes: int):
         """Run the bounded device wait on a phase nothing completes; returns (expired, seconds)."""
