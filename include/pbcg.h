@@ -364,7 +364,9 @@ int pbcg_profile_solve(pbcg_ctx *ctx, const pbcg_mat *A, const double *b, double
  *                from global memory;
  *   order        tile order of a pass: 0 default (round-robin when staged,
  *                claimed otherwise), 1 round-robin, 2 claimed from a
- *                grid-wide counter in index order;
+ *                grid-wide counter in index order, 3 round-robin except the
+ *                last two tiles of each CTA's share, which are claimed (the
+ *                SMs that run ahead take over the tail);
  *   ctas_per_sm  resident CTAs per SM of the passes of pbcg_solve (0: as
  *                many as fit; else at most that many);
  *   batched_ctas_per_sm  the same for pbcg_solve_batched's passes (fewer

@@ -88,7 +88,7 @@ struct pbcg_mat {
     struct BatchLayout *bl;            // tile-aligned layout of the last batched solve, or NULL
     // launch variant of pbcg_solve's passes (pbcg_set_variant / pbcg_tune); none changes exact results
     int v_staged = 1;                  // stage tiles in shared memory when they fit (narrow matrices)
-    int v_order = 0;                   // tile order: 0 default, 1 round-robin, 2 claimed
+    int v_order = 0;                   // tile order: 0 default, 1 round-robin, 2 claimed, 3 round-robin + claimed tail
     int v_ctas = 0;                    // resident CTAs per SM of the passes (0: as many as fit)
     int b_ctas = 0;                    // same, batched passes
     double v_us = 0.0;                 // time per iteration pbcg_tune measured for it
@@ -1896,7 +1896,7 @@ pbcg_variant variant_of(const pbcg_mat *m)
 
 bool variant_ok(const pbcg_variant &v)
 {
-    return (v.staged == 0 || v.staged == 1) && v.order >= 0 && v.order <= 2 && v.ctas_per_sm >= 0 &&
+    return (v.staged == 0 || v.staged == 1) && v.order >= 0 && v.order <= 3 && v.ctas_per_sm >= 0 &&
            v.ctas_per_sm <= 32 && v.batched_ctas_per_sm >= 0 && v.batched_ctas_per_sm <= 32;
 }
 
@@ -2034,15 +2034,15 @@ int tune_impl(pbcg_ctx *ctx, pbcg_mat *m, int alg, int mode, int32_t nsys, const
         for (int st : {1, 0}) {
             if (st == 0 && (!m->narrow || cluster))
                 continue;           // nothing to stage either way
-            for (int alt : {0, 1}) {
+            for (int alt : {0, 1, 2}) {
                 if (alt && cluster)
                     continue;
                 for (int c : {0, 1}) {
                     if (c && cluster)
                         continue;
                     d.staged = st;
-                    // the order other than this staging's default
-                    d.order = alt ? ((m->narrow && st) ? 2 : 1) : 0;
+                    // this staging's default order, the other pure order, round-robin with a claimed tail
+                    d.order = alt == 0 ? 0 : alt == 1 ? ((m->narrow && st) ? 2 : 1) : 3;
                     d.ctas_per_sm = c;
                     cand.push_back(d);
                 }

@@ -166,7 +166,16 @@ struct Vecs {
 template <bool MATS>
 __device__ __forceinline__ bool claimed_tiles(const Ctl *c)
 {
-    return c->order == 2 || (c->order == 0 && !MATS);
+    return c->order >= 2 || (c->order == 0 && !MATS);
+}
+
+// Ctl::order 3: round-robin, with the last TAIL_CLAIMED tiles of each CTA's
+// share claimed (tile_loop's rounds); other orders claim every tile or none
+constexpr int TAIL_CLAIMED = 2;
+__device__ __forceinline__ int rr_rounds(const Ctl *c, int nslices)
+{
+    const int ntiles = (nslices + TILE_SLICES - 1) / TILE_SLICES;
+    return c->order == 3 ? max(0, ntiles / (int)gridDim.x - TAIL_CLAIMED) : 0;
 }
 
 // residual replacement at the start of iteration it (every rr_period iterations, never at 0)
@@ -1198,7 +1207,10 @@ struct TilePipe {
 //
 // Tiles go to CTAs round-robin (CTA b takes b, b + grid, ...), or, with dyn
 // (a grid-wide counter that the pass's last CTA resets), in claim order: the
-// thread that refills a stage claims the next tile.  A matrix with wide rows
+// thread that refills a stage claims the next tile.  With dyn and rounds > 0
+// the first `rounds` tiles of every CTA are dealt round-robin and only the
+// rest are claimed (tiles rounds * grid, ... in claim order), so that the
+// SMs that run ahead take over the tail without paying a claim per tile.  A matrix with wide rows
 // keeps its rows sorted by length, so claiming hands out the heaviest tiles
 // first and lets the light ones fill in around them (round-robin leaves the
 // CTA holding the heaviest tile of every round with the most work).  When the
@@ -1206,7 +1218,8 @@ struct TilePipe {
 // no data and a tile of -1, which ends every warp's loop at that stage.
 template <int NV, bool MATS, class Body>
 __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&src)[NV], int nv, const double *gx,
-                                          Ctl *c, uint8_t *dsm, Body body, unsigned int *dyn = nullptr)
+                                          Ctl *c, uint8_t *dsm, Body body, unsigned int *dyn = nullptr,
+                                          int rounds = 0)
 {
     __shared__ uint64_t bar[NSTAGE];
     __shared__ StageInfo info[NSTAGE];
@@ -1215,7 +1228,10 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
     __shared__ int tmo;
     TilePipe<NV, MATS> P{dsm, bar, info};
     const int ntiles = (A.nslices + TILE_SLICES - 1) / TILE_SLICES;
-    const int my = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    // round-robin tiles of this CTA (all of its tiles without dyn)
+    const int my = dyn ? min(rounds, ntiles / (int)gridDim.x)
+                       : (ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0);
+    const unsigned int claim0 = dyn ? (unsigned int)my * gridDim.x : 0u;     // first claimed tile
     auto tile_of = [&](int jj) { return jj < my ? (int)blockIdx.x + jj * (int)gridDim.x : -1; };
     const bool recs = A.tmeta != nullptr;     // tile records travel with the stages
     auto record = [&](int t, int (&rec)[TMETA]) {   // from global memory
@@ -1233,7 +1249,7 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
     };
     // dynamic: claim a tile into stage k (or end the stage's sequence)
     auto claim_issue = [&](int k) {
-        const unsigned int t = atomicAdd(dyn, 1u);
+        const unsigned int t = claim0 + atomicAdd(dyn, 1u);
         if (t < (unsigned int)ntiles) {
             int rec[TMETA];
             record((int)t, rec);
@@ -1254,13 +1270,13 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
         fence_mbar_init();
         fence_async_shared();
         for (int k = 0; k < NSTAGE; k++) {
-            if (dyn) {
-                claim_issue(k);
-            } else if (k < my) {
+            if (k < my) {
                 int rec[TMETA];
                 record(tile_of(k), rec);
                 nissued[k] += 1;
                 P.issue(k, tile_of(k), rec, A, src, nv, gx, recs ? tile_of(k + NSTAGE) : -1);
+            } else if (dyn) {
+                claim_issue(k);
             }
         }
     }
@@ -1285,23 +1301,21 @@ __device__ __forceinline__ void tile_loop(const Mat &A, const double *const (&sr
                 // last warp out of this stage: every warp has read it
                 __threadfence_block();
                 done_cnt[k] = 0;
-                if (dyn) {
-                    claim_issue(k);
-                } else {
-                    const int jn = j + NSTAGE;
-                    if (jn < my) {
-                        int rec[TMETA];
-                        if (recs) {
-                            const int *m = P.meta(k);
+                const int jn = j + NSTAGE;
+                if (jn < my) {
+                    int rec[TMETA];
+                    if (recs) {
+                        const int *m = P.meta(k);
 #pragma unroll
-                            for (int q = 0; q < TMETA; q++)
-                                rec[q] = m[q];
-                        } else {
-                            record(tile_of(jn), rec);
-                        }
-                        nissued[k] += 1;
-                        P.issue(k, tile_of(jn), rec, A, src, nv, gx, recs ? tile_of(jn + NSTAGE) : -1);
+                        for (int q = 0; q < TMETA; q++)
+                            rec[q] = m[q];
+                    } else {
+                        record(tile_of(jn), rec);
                     }
+                    nissued[k] += 1;
+                    P.issue(k, tile_of(jn), rec, A, src, nv, gx, recs ? tile_of(jn + NSTAGE) : -1);
+                } else if (dyn) {
+                    claim_issue(k);
                 }
             }
         }
@@ -1483,7 +1497,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         D.template add2<true>(sh, 1, y, y, dy, dy, act);
         D.template add2<false>(sh, 2, r0i, si, dr, ds, act);
         D.template add2<false>(sh, 3, r0i, zi, dr, dz, act);
-    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr);
+    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
     if (!finalize<4, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1528,7 +1542,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
         D.template add_row<3, false, false, true>(sh, act, r0i, rn, dr0, dr, r0i, wn, dr0, dw, rn, rn, &dr, &dr);
-    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr);
+    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
     if (!finalize<3, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1632,7 +1646,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dr = decode(r0i), ds = decode(si);
         D.template add2<false>(sh, 0, r0i, si, dr, ds, act);
-    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr);
+    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
     if (!finalize<1, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)
@@ -1668,7 +1682,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         }
         const Dec dq = decode(qi), dy = decode(yi);
         D.template add_row<2, false, true>(sh, act, qi, yi, dq, dy, yi, yi, dy, dy);
-    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr);
+    }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
     if (!finalize<2, MODE>(D, sh, wk))
         return;
     if (threadIdx.x == 0)

@@ -40,7 +40,7 @@ def _variants(narrow):
     from paper_2404_13216_gb300 import pbcg
     out = []
     for staged in ((1, 0) if narrow else (1,)):
-        for order in (0, 1, 2):
+        for order in (0, 1, 2, 3):
             for ctas in (0, 1):
                 out.append(pbcg.Variant(staged, order, ctas, 0))
     return out
@@ -106,7 +106,7 @@ def test_tune_keeps_the_fastest_and_caches(ctx, tmp_path):
     r0, h0, x0 = _solve(ctx, M, b, 30)
     cache = str(tmp_path / "tune.jsonl")
     chosen, tried = ctx.tune(M, pbcg.PIPELINED, pbcg.EXACT, iters=20, cache_path=cache)
-    assert len(tried) == 8
+    assert len(tried) == 12
     default = tried[0]
     assert (default.staged, default.order, default.ctas_per_sm) == (1, 0, 0)
     assert chosen.us_per_iter == min(t.us_per_iter for t in tried) <= default.us_per_iter
@@ -123,7 +123,7 @@ def test_tune_keeps_the_fastest_and_caches(ctx, tmp_path):
         (chosen.staged, chosen.order, chosen.ctas_per_sm)
     # plain mode is a key of its own
     pc, pt = ctx.tune(M, pbcg.PIPELINED, pbcg.PLAIN, iters=20, cache_path=cache)
-    assert len(pt) == 8 and len(open(cache).readlines()) == 2
+    assert len(pt) == 12 and len(open(cache).readlines()) == 2
     M.free()
 
 
@@ -143,7 +143,7 @@ def test_variant_validation(ctx):
     from paper_2404_13216_gb300 import pbcg
     A = inputs.convdiff2d(20, 5.0)
     M = ctx.upload_csr(A)
-    for bad in (pbcg.Variant(2, 0, 0, 0), pbcg.Variant(1, 3, 0, 0), pbcg.Variant(1, 0, -1, 0)):
+    for bad in (pbcg.Variant(2, 0, 0, 0), pbcg.Variant(1, 4, 0, 0), pbcg.Variant(1, 0, -1, 0)):
         with pytest.raises(pbcg.PbcgError):
             ctx.set_variant(M, bad)
     with pytest.raises(pbcg.PbcgError):
