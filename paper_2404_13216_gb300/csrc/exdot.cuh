@@ -467,8 +467,10 @@ static __device__ double round_digits(const unsigned long long *dig, int k0, int
 // Round the ND global accumulators g[0..ND-1] and reset them; every thread of
 // the CTA calls.  The touched digits are first copied, in parallel, into the
 // CTA accumulator c (free at this point: its contents were merged into g), so
-// that the serial rounding (one thread per dot) reads shared memory only.
-// dv[d] receives the rounded dots.
+// that the serial rounding reads shared memory only.  Every thread issues all
+// of its loads before any of its stores, so the copy costs one round trip to
+// L2 whatever ND is, and the dots are rounded by lane 0 of warps 0 .. ND-1,
+// side by side.  dv[d] receives the rounded dots.
 template <int ND>
 __device__ void gacc_round_reset_cta(GAcc *g, CtaAcc<ND> &c, uint32_t (*scratch)[NDIG], double *dv)
 {
@@ -480,17 +482,36 @@ __device__ void gacc_round_reset_cta(GAcc *g, CtaAcc<ND> &c, uint32_t (*scratch)
         c.nf[d] = *((volatile int *)&g[d].nf);
     }
     __syncthreads();
+    // position i of the flattened (dot, digit) range: dot i / NDIG, digit i % NDIG
+    constexpr int PER = (ND * NDIG + 255) / 256;
+    unsigned long long v[PER];
+    bool hit[PER];
 #pragma unroll
-    for (int d = 0; d < ND; d++) {
-        const int k0 = c.kmin[d], k1 = c.kmax[d];
-        for (int k = k0 + (int)threadIdx.x; k <= k1; k += blockDim.x) {
-            c.dig[d][k] = __ldcg(&g[d].dig[k]);
+    for (int j = 0; j < PER; j++) {
+        const int i = (int)threadIdx.x + j * (int)blockDim.x;
+        const int d = i / NDIG, k = i - d * NDIG;
+        hit[j] = i < ND * NDIG && k >= c.kmin[d] && k <= c.kmax[d];
+        v[j] = hit[j] ? __ldcg(&g[d].dig[k]) : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        if (hit[j]) {
+            const int i = (int)threadIdx.x + j * (int)blockDim.x;
+            const int d = i / NDIG, k = i - d * NDIG;
+            c.dig[d][k] = v[j];
             g[d].dig[k] = 0ull;                      // clear every touched digit, NaN results included
         }
     }
+    for (int i = (int)threadIdx.x + PER * (int)blockDim.x; i < ND * NDIG; i += blockDim.x) {
+        const int d = i / NDIG, k = i - d * NDIG;    // (a CTA of fewer than 256 threads)
+        if (k >= c.kmin[d] && k <= c.kmax[d]) {
+            c.dig[d][k] = __ldcg(&g[d].dig[k]);
+            g[d].dig[k] = 0ull;
+        }
+    }
     __syncthreads();
-    if (threadIdx.x < ND) {
-        const int d = threadIdx.x;
+    if ((threadIdx.x & 31) == 0 && (int)(threadIdx.x >> 5) < ND) {
+        const int d = threadIdx.x >> 5;
         dv[d] = round_digits(c.dig[d], c.kmin[d], c.kmax[d], c.nf[d], scratch[d]);
         g[d].kmin = NDIG;
         g[d].kmax = -1;
