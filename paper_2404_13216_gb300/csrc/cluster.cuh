@@ -257,9 +257,11 @@ __device__ __forceinline__ void cluster_merge(DotSet<ND, MODE> &D, Shm<ND> &sh, 
         return;
     if (MODE == 1) {
         // round, then clear the touched digits for the next merge
-        if (threadIdx.x < ND) {
-            const int d = threadIdx.x;
-            sh.dv[d] = round_digits(hub.dig[d], hub.kmin[d], hub.kmax[d], hub.nf[d], sh.scratch[d]);
+        if (warp < ND) {                                // warp d rounds dot d
+            const double v = round_digits_warp(hub.dig[warp], hub.kmin[warp], hub.kmax[warp], hub.nf[warp],
+                                               sh.scratch[warp]);
+            if ((threadIdx.x & 31) == 0)
+                sh.dv[warp] = v;
         }
         __syncthreads();
         for (int d = 0; d < ND; d++)

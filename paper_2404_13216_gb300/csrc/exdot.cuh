@@ -464,58 +464,187 @@ static __device__ double round_digits(const unsigned long long *dig, int k0, int
     return __longlong_as_double((long long)bits);
 }
 
+// The same rounding as round_digits, by all 32 lanes of one warp (returns the
+// value in every lane).  Carry normalisation runs on 32 digits at a time:
+// each lane holds one digit, the part of it above bit 31 moves one lane up per
+// step (shuffles) until every lane's digit lies in [0, 2^32), and the top
+// lane's part carries into the next 32 digits.  The lowest and highest nonzero
+// words and the sticky bits below the rounding position come from ballots.
+// Every step is exact, so the result is round_digits' bit for bit.
+static __device__ double round_digits_warp(const unsigned long long *dig, int k0, int k1, int nf, uint32_t *scratch)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (nf)
+        return __longlong_as_double(0x7ff8000000000000ll);
+    if (k1 < k0)
+        return 0.0;
+    // 1. scratch[k0 .. top] := the two's complement words of the sum; stop once
+    //    the words above are pure sign extension (carry 0 over a clear top bit,
+    //    or -1 over a set one)
+    long long cin = 0;
+    int top = k0;
+    for (int kc = k0; kc < NDIG; kc += 32) {
+        const int k = kc + lane;
+        long long d = (k <= k1) ? (long long)dig[k] : 0ll;
+        if (lane == 0)
+            d += cin;
+        long long out = 0;
+        while (__any_sync(FULL, (d >> 32) != 0)) {           // at most 33 rounds: the parts shrink to +-1 at once
+            const long long hi = d >> 32;
+            const long long below = __shfl_up_sync(FULL, hi, 1);
+            out += __shfl_sync(FULL, hi, 31);
+            d = (long long)(uint32_t)d + (lane == 0 ? 0ll : below);
+        }
+        if (k < NDIG)
+            scratch[k] = (uint32_t)d;
+        cin = out;
+        top = min(kc + 31, NDIG - 1);
+        const uint32_t tw = __shfl_sync(FULL, (uint32_t)d, 31);
+        if (kc + 31 >= k1 && ((cin == 0 && !(tw >> 31)) || (cin == -1 && (tw >> 31))))
+            break;
+    }
+    __syncwarp();
+    const bool negv = cin < 0;
+    if (negv) {
+        // magnitude: words below the lowest nonzero one stay 0, that one is
+        // negated, every word above it is inverted
+        bool seen = false;
+        for (int c = k0; c <= top; c += 32) {
+            const int k = c + lane;
+            const uint32_t w = (k <= top) ? scratch[k] : 0u;
+            const unsigned nz = __ballot_sync(FULL, k <= top && w != 0u);
+            uint32_t r;
+            if (seen) {
+                r = ~w;
+            } else {
+                const int low = nz ? __ffs(nz) - 1 : 32;
+                r = lane < low ? 0u : (lane == low ? 0u - w : ~w);
+            }
+            seen = seen || nz != 0u;
+            if (k <= top)
+                scratch[k] = r;
+        }
+        __syncwarp();
+    }
+    // 2. the highest nonzero word
+    int hk = -1;
+    for (int c = top; c >= k0 && hk < 0; c -= 32) {
+        const int k = c - lane;
+        const unsigned nz = __ballot_sync(FULL, k >= k0 && scratch[k] != 0u);
+        if (nz)
+            hk = c - (__ffs(nz) - 1);
+    }
+    if (hk < 0)
+        return 0.0;
+    const int h = hk * 32 + 31 - __clz(scratch[hk]);
+    const int lsb = max(h - 52, 1074);
+    auto word = [&](int k) -> unsigned long long { return (k >= k0 && k <= top) ? scratch[k] : 0u; };
+    const int kl = lsb >> 5, sl = lsb & 31;
+    const unsigned long long lo64 = word(kl) | (word(kl + 1) << 32);
+    unsigned long long m = sl ? (lo64 >> sl) | (word(kl + 2) << (64 - sl)) : lo64;
+    const uint32_t rb = bit_at(scratch, k0, top, lsb - 1);
+    // sticky: any bit below lsb - 1
+    const int sk = (lsb - 1) >> 5;
+    bool st = false;
+    for (int c = k0; c < sk && c <= top; c += 32) {
+        const int k = c + lane;
+        st = st || __any_sync(FULL, k < sk && k <= top && scratch[k] != 0u);
+    }
+    if (sk >= k0 && sk <= top)
+        st = st || (scratch[sk] & ((1u << ((lsb - 1) & 31)) - 1u)) != 0u;
+    if (rb && (st || (m & 1ull)))
+        m += 1ull;
+    long long ef = (long long)(lsb - 1074);
+    unsigned long long bits = ((unsigned long long)ef << 52) + m;
+    if (bits >= 0x7ff0000000000000ull)
+        bits = 0x7ff0000000000000ull;
+    if (negv)
+        bits |= 0x8000000000000000ull;
+    return __longlong_as_double((long long)bits);
+}
+
 // Round the ND global accumulators g[0..ND-1] and reset them; every thread of
-// the CTA calls.  The touched digits are first copied, in parallel, into the
-// CTA accumulator c (free at this point: its contents were merged into g), so
-// that the serial rounding reads shared memory only.  Every thread issues all
-// of its loads before any of its stores, so the copy costs one round trip to
-// L2 whatever ND is, and the dots are rounded by lane 0 of warps 0 .. ND-1,
+// the CTA calls.  All ND * NDIG digits (the untouched ones are 0) and the
+// non-finite flags are loaded in one round trip to L2 -- every thread issues
+// its loads before any store -- into the CTA accumulator c (free at this
+// point: its contents were merged into g); the range each dot's rounding
+// scans is that of its nonzero digits.  Warp d rounds dot d, the ND warps
 // side by side.  dv[d] receives the rounded dots.
 template <int ND>
 __device__ void gacc_round_reset_cta(GAcc *g, CtaAcc<ND> &c, uint32_t (*scratch)[NDIG], double *dv)
 {
     __syncthreads();
     if (threadIdx.x < ND) {
-        const int d = threadIdx.x;
-        c.kmin[d] = *((volatile int *)&g[d].kmin);
-        c.kmax[d] = *((volatile int *)&g[d].kmax);
-        c.nf[d] = *((volatile int *)&g[d].nf);
+        c.kmin[threadIdx.x] = NDIG;
+        c.kmax[threadIdx.x] = -1;
     }
-    __syncthreads();
+    int nf = 0;
+    if (threadIdx.x < ND)
+        nf = *((volatile int *)&g[threadIdx.x].nf);
     // position i of the flattened (dot, digit) range: dot i / NDIG, digit i % NDIG
     constexpr int PER = (ND * NDIG + 255) / 256;
     unsigned long long v[PER];
-    bool hit[PER];
 #pragma unroll
     for (int j = 0; j < PER; j++) {
         const int i = (int)threadIdx.x + j * (int)blockDim.x;
         const int d = i / NDIG, k = i - d * NDIG;
-        hit[j] = i < ND * NDIG && k >= c.kmin[d] && k <= c.kmax[d];
-        v[j] = hit[j] ? __ldcg(&g[d].dig[k]) : 0ull;
+        v[j] = i < ND * NDIG ? __ldcg(&g[d].dig[k]) : 0ull;
     }
+    __syncthreads();                                 // (c.kmin / c.kmax initialised)
+    if (threadIdx.x < ND)
+        c.nf[threadIdx.x] = nf;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < PER; j++) {
-        if (hit[j]) {
-            const int i = (int)threadIdx.x + j * (int)blockDim.x;
-            const int d = i / NDIG, k = i - d * NDIG;
+        const int i = (int)threadIdx.x + j * (int)blockDim.x;
+        const int d = i / NDIG, k = i - d * NDIG;
+        const bool nz = i < ND * NDIG && v[j] != 0ull;
+        if (i < ND * NDIG) {
             c.dig[d][k] = v[j];
-            g[d].dig[k] = 0ull;                      // clear every touched digit, NaN results included
+            if (nz)
+                g[d].dig[k] = 0ull;                  // every nonzero digit cleared, NaN results included
+        }
+        // the warp's lowest and highest nonzero digit of each dot it covers: its
+        // lanes hold consecutive positions, so at most two dots (those of dot d0
+        // form a prefix, the next dot starts at digit 0); one shared atomic per
+        // bound instead of one per digit
+        const unsigned mall = __ballot_sync(0xffffffffu, nz);
+        const unsigned pre = __ballot_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0));
+        const int d0 = __shfl_sync(0xffffffffu, d, 0), kl0 = __shfl_sync(0xffffffffu, k, 0);
+        const unsigned m0 = mall & pre, m1 = mall & ~pre;
+        if (lane == 0) {
+            if (m0) {
+                atomicMin(&c.kmin[d0], kl0 + (__ffs(m0) - 1));
+                atomicMax(&c.kmax[d0], kl0 + (31 - __clz(m0)));
+            }
+            if (m1) {
+                const int L = __popc(pre);           // the lane holding digit 0 of dot d0 + 1
+                atomicMin(&c.kmin[d0 + 1], (__ffs(m1) - 1) - L);
+                atomicMax(&c.kmax[d0 + 1], (31 - __clz(m1)) - L);
+            }
         }
     }
     for (int i = (int)threadIdx.x + PER * (int)blockDim.x; i < ND * NDIG; i += blockDim.x) {
         const int d = i / NDIG, k = i - d * NDIG;    // (a CTA of fewer than 256 threads)
-        if (k >= c.kmin[d] && k <= c.kmax[d]) {
-            c.dig[d][k] = __ldcg(&g[d].dig[k]);
+        const unsigned long long w = __ldcg(&g[d].dig[k]);
+        c.dig[d][k] = w;
+        if (w != 0ull) {
             g[d].dig[k] = 0ull;
+            atomicMin(&c.kmin[d], k);
+            atomicMax(&c.kmax[d], k);
         }
     }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0 && (int)(threadIdx.x >> 5) < ND) {
+    if ((int)(threadIdx.x >> 5) < ND) {
         const int d = threadIdx.x >> 5;
-        dv[d] = round_digits(c.dig[d], c.kmin[d], c.kmax[d], c.nf[d], scratch[d]);
-        g[d].kmin = NDIG;
-        g[d].kmax = -1;
-        g[d].nf = 0;
+        const double r = round_digits_warp(c.dig[d], c.kmin[d], c.kmax[d], c.nf[d], scratch[d]);
+        if ((threadIdx.x & 31) == 0) {
+            dv[d] = r;
+            g[d].kmin = NDIG;
+            g[d].kmax = -1;
+            g[d].nf = 0;
+        }
     }
     __syncthreads();
 }

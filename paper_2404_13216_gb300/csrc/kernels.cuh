@@ -470,10 +470,15 @@ __device__ __forceinline__ void merge_publish(DotSet<ND, MODE> &D, Shm<ND> &sh, 
 // accumulators (and reset them) or sum the plain partials in CTA order, into
 // sh.dv.  Called by every thread of that CTA.
 template <int ND, int MODE>
-__device__ __forceinline__ void merge_finish(Shm<ND> &sh, Work *wk)
+__device__ __forceinline__ void merge_finish(Shm<ND> &sh, Work *wk, const void *pre = nullptr)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __threadfence();
+    if (pre && threadIdx.x == THREADS - 1) {
+        // the control block the scalar step reads next, into L1 while the merge runs
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(pre));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"((const char *)pre + 128));
+    }
     if (MODE == 1) {
         gacc_round_reset_cta<ND>(wk->g, sh.acc, sh.scratch, sh.dv);
     } else if (warp < ND) {
@@ -490,10 +495,12 @@ __device__ __forceinline__ void merge_finish(Shm<ND> &sh, Work *wk)
 }
 
 // Merge the CTA's dots grid-wide.  Returns true in the last CTA, whose
-// sh.dv[] then holds the finished dot values.  Called by every thread.
+// sh.dv[] then holds the finished dot values.  Called by every thread.  pre:
+// the control block the last CTA's scalar step reads (prefetched), or NULL.
 template <int ND, int MODE>
-__device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
+__device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk, const void *pre = nullptr)
 {
+    const int dist = wk->dist;       // loaded here, used by the last CTA: off the path after the ticket
     merge_publish<ND, MODE>(D, sh, wk);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -503,7 +510,7 @@ __device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
     __syncthreads();
     if (!sh.last)
         return false;
-    if (wk->dist) {
+    if (dist) {
         // one rank of a row-partitioned solve: the exact digits stay in wk->g
         // and the plain partials are summed into wk->loc; the host adds them
         // over the ranks and k_dist_finish rounds and takes the scalar step
@@ -520,7 +527,7 @@ __device__ bool finalize(DotSet<ND, MODE> &D, Shm<ND> &sh, Work *wk)
         __syncthreads();
         return false;
     }
-    merge_finish<ND, MODE>(sh, wk);
+    merge_finish<ND, MODE>(sh, wk, pre);
     if (threadIdx.x == 0) {
         wk->ticket = 0u;
         wk->tile_next = 0u;          // every CTA has left its tile loop
@@ -1498,7 +1505,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         D.template add2<false>(sh, 2, r0i, si, dr, ds, act);
         D.template add2<false>(sh, 3, r0i, zi, dr, dz, act);
     }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
-    if (!finalize<4, MODE>(D, sh, wk))
+    if (!finalize<4, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
         pipe_x_tail(c, sh.dv);
@@ -1543,7 +1550,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
         D.template add_row<3, false, false, true>(sh, act, r0i, rn, dr0, dr, r0i, wn, dr0, dw, rn, rn, &dr, &dr);
     }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
-    if (!finalize<3, MODE>(D, sh, wk))
+    if (!finalize<3, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
         pipe_y_tail(c, sh.dv);
@@ -1647,7 +1654,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         const Dec dr = decode(r0i), ds = decode(si);
         D.template add2<false>(sh, 0, r0i, si, dr, ds, act);
     }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
-    if (!finalize<1, MODE>(D, sh, wk))
+    if (!finalize<1, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
         bicg_a_scalar(c, sh.dv[0]);
@@ -1683,7 +1690,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         const Dec dq = decode(qi), dy = decode(yi);
         D.template add_row<2, false, true>(sh, act, qi, yi, dq, dy, yi, yi, dy, dy);
     }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
-    if (!finalize<2, MODE>(D, sh, wk))
+    if (!finalize<2, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
         bicg_b_scalar(c, sh.dv[0], sh.dv[1]);
@@ -1721,7 +1728,7 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
         const Dec dr0 = decode(r0i), dr = decode(rn);
         D.template add_row<2, false, true>(sh, act, r0i, rn, dr0, dr, rn, rn, dr, dr);
     });
-    if (!finalize<2, MODE>(D, sh, wk))
+    if (!finalize<2, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
         bicg_c_scalar(c, sh.dv[0], sh.dv[1]);
