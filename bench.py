@@ -487,6 +487,9 @@ def summary_block(line):
         if k in cf:
             out[k] = {"us_per_iter": g(cf, k, "us_per_iter"), "frac": g(cf, k, "frac_of_measured_hbm"),
                       "iters": g(cf, k, "iters"), "status": g(cf, k, "status")}
+    tn = cf.get("tuning") or {}
+    for k, v in tn.items():
+        out["tuned_" + k] = {"chosen": v.get("chosen"), "default_us_per_iter": v.get("default_us_per_iter")}
     return out
 
 
@@ -659,9 +662,27 @@ def run_config_legs(ctx, pbcg, torch, dev, peak):
     ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_JACOBI)
     out["powerlaw_pbicgstab_jacobi_exact_to_tol"] = leg(A, pbcg.PIPELINED, pbcg.EXACT, TOL, 400, 1, 23)
     ctx.set_option(pbcg.OPT_PRECOND, pbcg.PRECOND_NONE)
+    out["tuning"] = run_tuning_leg(ctx, pbcg, inputs)
     out["notes"] = ("us_per_iter = solve time / iterations (setup and the true-residual check included); "
                     "bytes_per_iter = 2M + 23V (p-BiCGStab) or 2M + 17V (BiCGStab); the 64^2 system is "
                     "L2-resident, so its GB/s is not an HBM figure; tol 1e-300 runs exactly maxit iterations")
+    return out
+
+
+def run_tuning_leg(ctx, pbcg, inputs):
+    """pbcg_tune on the 128^3 system and the power-law matrix (exact p-BiCGStab):
+    every candidate launch variant's measured time per iteration, and the one
+    kept (the default is always a candidate; every variant gives the same
+    exact results)."""
+    out = {}
+    for name, A in (("convdiff128", inputs.convdiff3d(N_SIDE, PECLET, WIND)), ("powerlaw", inputs.powerlaw())):
+        M = ctx.upload_csr(A)
+        chosen, tried = ctx.tune(M, pbcg.PIPELINED, pbcg.EXACT, iters=30)
+        M.free()
+        fmt = lambda v: {"staged": v.staged, "order": v.order, "ctas_per_sm": v.ctas_per_sm,
+                         "us_per_iter": round(v.us_per_iter, 2)}
+        out[name] = {"chosen": fmt(chosen), "default_us_per_iter": round(tried[0].us_per_iter, 2),
+                     "candidates": [fmt(t) for t in tried]}
     return out
 
 
