@@ -671,13 +671,14 @@ def run_config_legs(ctx, pbcg, torch, dev, peak):
 
 def run_tuning_leg(ctx, pbcg, inputs):
     """pbcg_tune on the 128^3 system and the power-law matrix (exact p-BiCGStab):
-    every candidate launch variant's measured time per iteration, and the one
-    kept (the default is always a candidate; every variant gives the same
-    exact results)."""
+    every candidate launch variant's measured time per iteration (iterations
+    101-300 of the 128^3 solve, 31-90 of the power-law one), and the one kept
+    (the default is always a candidate; every variant gives the same exact
+    results)."""
     out = {}
     for name, A in (("convdiff128", inputs.convdiff3d(N_SIDE, PECLET, WIND)), ("powerlaw", inputs.powerlaw())):
         M = ctx.upload_csr(A)
-        chosen, tried = ctx.tune(M, pbcg.PIPELINED, pbcg.EXACT, iters=30)
+        chosen, tried = ctx.tune(M, pbcg.PIPELINED, pbcg.EXACT, iters=100 if name == "convdiff128" else 30)
         M.free()
         fmt = lambda v: {"staged": v.staged, "order": v.order, "ctas_per_sm": v.ctas_per_sm,
                          "us_per_iter": round(v.us_per_iter, 2)}

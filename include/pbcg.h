@@ -392,11 +392,13 @@ int pbcg_get_variant(pbcg_ctx *ctx, const pbcg_mat *A, pbcg_variant *out);
 
 /*
  * Autotune A's launch variant for algorithm alg and dot_mode: every
- * candidate variant runs a trial solve of `iters` iterations (b = A * ones,
- * x0 = 0, no stop) and the fastest per iteration (CUDA events on the
- * context's stream, after one untimed trial) becomes A's variant; the
+ * candidate variant runs trial solves (b = A * ones, x0 = 0, no stop) of
+ * `iters` and 3 * iters iterations after an untimed one; its time per
+ * iteration is the difference of the two (CUDA events on the context's
+ * stream) over 2 * iters, so setup, the first iterations and the
+ * true-residual check drop out.  The fastest becomes A's variant; the
  * default is always a candidate, so the choice is never slower than it as
- * measured.  nsys = 0 tunes pbcg_solve's passes; nsys >= 1 with
+ * measured.  1 <= iters <= 30000.  nsys = 0 tunes pbcg_solve's passes; nsys >= 1 with
  * sys_row_ptr[nsys+1] tunes pbcg_solve_batched's passes for that block
  * structure.  A system small enough for the one-cluster loop keeps the
  * default (its launch is fixed).
@@ -408,7 +410,8 @@ int pbcg_get_variant(pbcg_ctx *ctx, const pbcg_mat *A, pbcg_variant *out);
  * appended.  chosen (may be NULL) receives the variant applied; tried (cap
  * entries, may be NULL) the candidates with their times, *ntried (may be
  * NULL) how many ran (0 when the cache answered).
- * Errors: INVALID (bad arguments, iters < 1), OOM, CUDA, or a trial's error.
+ * Errors: INVALID (bad arguments, iters outside 1 .. 30000), OOM, CUDA, or
+ * a trial's error.
  */
 int pbcg_tune(pbcg_ctx *ctx, pbcg_mat *A, int alg, int dot_mode, int32_t nsys, const int32_t *sys_row_ptr,
               int32_t iters, const char *cache_path, pbcg_variant *chosen, pbcg_variant *tried, int32_t cap,

@@ -1989,7 +1989,7 @@ int tune_impl(pbcg_ctx *ctx, pbcg_mat *m, int alg, int mode, int32_t nsys, const
         return fail(ctx, PBCG_ERR_INVALID, "unknown algorithm %d", alg);
     if (mode != PBCG_DOT_PLAIN && mode != PBCG_DOT_EXACT)
         return fail(ctx, PBCG_ERR_INVALID, "unknown dot mode %d", mode);
-    if (iters < 1 || iters > 100000 || nsys < 0 || (nsys > 0 && !srp) || cap < 0 || (cap > 0 && !tried))
+    if (iters < 1 || iters > 30000 || nsys < 0 || (nsys > 0 && !srp) || cap < 0 || (cap > 0 && !tried))
         return fail(ctx, PBCG_ERR_INVALID, "bad tuning arguments");
     if (nsys > 0) {
         if (srp[0] != 0 || srp[nsys] != m->n)
@@ -2074,23 +2074,19 @@ int tune_impl(pbcg_ctx *ctx, pbcg_mat *m, int alg, int mode, int32_t nsys, const
         cudaEvent_t a, b;
         ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } ev{e0, e1};
-    auto trial = [&](bool timed, double *us) -> int {
+    // one trial solve of `its` iterations; *ms its CUDA-event time (NULL: untimed)
+    auto trial = [&](int its, float *ms) -> int {
         CK(cudaMemsetAsync(xx.p, 0, sizeof(double) * n, ctx->stream));
-        if (timed)
+        if (ms)
             CK(cudaEventRecord(e0, ctx->stream));
-        int r = nsys > 0 ? solve_batched_impl(ctx, m, nsys, srp, bb.p, xx.p, tols.data(), iters, alg, mode, res.data())
-                         : solve_impl(ctx, m, bb.p, xx.p, 1e-300, iters, alg, mode, res.data(), nullptr);
+        int r = nsys > 0 ? solve_batched_impl(ctx, m, nsys, srp, bb.p, xx.p, tols.data(), its, alg, mode, res.data())
+                         : solve_impl(ctx, m, bb.p, xx.p, 1e-300, its, alg, mode, res.data(), nullptr);
         if (r < 0)
             return r;
-        if (timed) {
+        if (ms) {
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            int its = 0;
-            for (auto &q : res)
-                its = std::max(its, q.iters);
-            *us = 1e3 * ms / std::max(its, 1);
+            CK(cudaEventElapsedTime(ms, e0, e1));
         }
         return 0;
     };
@@ -2099,11 +2095,14 @@ int tune_impl(pbcg_ctx *ctx, pbcg_mat *m, int alg, int mode, int32_t nsys, const
     int k = 0;
     for (auto &c : cand) {
         apply_variant(m, c);
-        double us = 0.0;
-        if ((rc = trial(false, &us)) || (rc = trial(true, &us))) {
+        // iterations iters+1 .. 3 iters: the difference of two timed trials
+        // (setup, the first iterations and the true-residual check drop out)
+        float t1 = 0.f, t3 = 0.f;
+        if ((rc = trial(iters, nullptr)) || (rc = trial(iters, &t1)) || (rc = trial(3 * iters, &t3))) {
             apply_variant(m, base);
             return rc;
         }
+        const double us = 1e3 * (double)(t3 - t1) / (2.0 * iters);
         c.us_per_iter = us;
         if (tried && k < cap)
             tried[k] = c;
