@@ -216,6 +216,12 @@ def run_cpu_table(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands (there is no other
+    implementation of this method to run), exact p-BiCGStab on the 128^3
+    system.  Each step is a solve of 1 + PER_STEP iterations; the time of a
+    1-iteration solve (setup, one iteration, the true-residual check),
+    measured during the warm-up, is subtracted, so the value counts
+    iterations only, like the GPU arm's steady iterations."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
@@ -225,19 +231,26 @@ def run_reference(args):
     A = inputs.convdiff3d(N_SIDE, PECLET, WIND)
     b = inputs.rhs_ones(A)
     cores = os.cpu_count() or 1
-    per_step = 2
-    for _ in range(args.warmup):
-        oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=per_step, alg=1, mode=1, nthreads=cores)
-    t0 = time.perf_counter()
-    its = 0
+    per_step = 3
+
+    def solve(its):
+        t = time.perf_counter()
+        r = oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=its, alg=1, mode=1, nthreads=cores)
+        return time.perf_counter() - t, r.iters
+
+    base = []
+    for _ in range(max(args.warmup, 1)):
+        base.append(solve(1)[0])
+    t_base = min(base)
+    dt, its = 0.0, 0
     for _ in range(args.steps):
-        r = oracle.solve(A.row_ptr, A.col_idx, A.vals, b, tol=1e-300, maxit=per_step, alg=1, mode=1,
-                         nthreads=cores)
-        its += r.iters
-    dt = time.perf_counter() - t0
+        t, n = solve(1 + per_step)
+        dt += max(t - t_base, 1e-9)
+        its += n - 1
     v = its / dt
-    sample = (f"{per_step} exact p-BiCGStab iterations (setup included) per step on the 128^3 system, "
-              f"{cores} threads for exact dots, CPU {cpu_model()}")
+    sample = (f"{per_step} exact p-BiCGStab iterations per step on the 128^3 system (a {1 + per_step}-iteration solve "
+              f"less a 1-iteration solve, {t_base:.2f} s, timed in the warm-up), {cores} threads for exact dots, "
+              f"CPU {cpu_model()}")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
