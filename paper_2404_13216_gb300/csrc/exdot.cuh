@@ -466,11 +466,13 @@ static __device__ double round_digits(const unsigned long long *dig, int k0, int
 
 // The same rounding as round_digits, by all 32 lanes of one warp (returns the
 // value in every lane).  Carry normalisation runs on 32 digits at a time:
-// each lane holds one digit, the part of it above bit 31 moves one lane up per
-// step (shuffles) until every lane's digit lies in [0, 2^32), and the top
-// lane's part carries into the next 32 digits.  The lowest and highest nonzero
-// words and the sticky bits below the rounding position come from ballots.
-// Every step is exact, so the result is round_digits' bit for bit.
+// each lane holds one digit; the part of it above bit 31 moves one lane up
+// (shuffles), after which every remaining carry is -1, 0 or +1, and those are
+// settled at once by a carry-lookahead over the warp (ballots) -- no carry
+// ripples lane by lane; the top lane's part carries into the next 32 digits.
+// The lowest and highest nonzero words and the sticky bits below the
+// rounding position come from ballots.  Every step is exact, so the result is
+// round_digits' bit for bit.
 static __device__ double round_digits_warp(const unsigned long long *dig, int k0, int k1, int nf, uint32_t *scratch)
 {
     constexpr unsigned FULL = 0xffffffffu;
@@ -489,18 +491,45 @@ static __device__ double round_digits_warp(const unsigned long long *dig, int k0
         long long d = (k <= k1) ? (long long)dig[k] : 0ll;
         if (lane == 0)
             d += cin;
-        long long out = 0;
-        while (__any_sync(FULL, (d >> 32) != 0)) {           // at most 33 rounds: the parts shrink to +-1 at once
-            const long long hi = d >> 32;
-            const long long below = __shfl_up_sync(FULL, hi, 1);
-            out += __shfl_sync(FULL, hi, 31);
-            d = (long long)(uint32_t)d + (lane == 0 ? 0ll : below);
+        // move each digit's part above bit 31 one lane up (the top lane's out
+        // of the chunk): |digit| < 2^62, so what a lane then holds lies in
+        // (-2^30, 2^32 + 2^30) and its own carry is -1, 0 or +1
+        const long long hi = d >> 32;
+        const long long below = __shfl_up_sync(FULL, hi, 1);    // (every lane shuffles; lane 0 ignores it)
+        long long out = __shfl_sync(FULL, hi, 31);
+        d = (long long)(uint32_t)d + (lane == 0 ? 0ll : below);
+        const int c1 = (int)(d >> 32);                       // -1, 0 or 1, into the next lane
+        out += __shfl_sync(FULL, c1, 31);
+        const int c1_below = __shfl_up_sync(FULL, c1, 1);
+        const int inc = lane == 0 ? 0 : c1_below;
+        uint32_t w = (uint32_t)d;
+        // add the +1 carries, then the -1 borrows, each with a lookahead over
+        // the warp: lane i is bit i; g generates (overflows by itself), p
+        // propagates (overflows with one more); the carries into the lanes are
+        // the carries of the integer addition g + (g | p)
+        {
+            const unsigned g = __ballot_sync(FULL, inc == 1 && w == 0xffffffffu);
+            w += inc == 1 ? 1u : 0u;
+            const unsigned p = __ballot_sync(FULL, w == 0xffffffffu);
+            const unsigned long long sum = (unsigned long long)g + (unsigned long long)(g | p);
+            const unsigned into = (unsigned)sum ^ (p & ~g);
+            w += (into >> lane) & 1u;
+            out += (long long)(sum >> 32);
+        }
+        {
+            const unsigned g = __ballot_sync(FULL, inc == -1 && w == 0u);
+            w -= inc == -1 ? 1u : 0u;
+            const unsigned p = __ballot_sync(FULL, w == 0u);
+            const unsigned long long sum = (unsigned long long)g + (unsigned long long)(g | p);
+            const unsigned into = (unsigned)sum ^ (p & ~g);
+            w -= (into >> lane) & 1u;
+            out -= (long long)(sum >> 32);
         }
         if (k < NDIG)
-            scratch[k] = (uint32_t)d;
+            scratch[k] = w;
         cin = out;
         top = min(kc + 31, NDIG - 1);
-        const uint32_t tw = __shfl_sync(FULL, (uint32_t)d, 31);
+        const uint32_t tw = __shfl_sync(FULL, w, 31);
         if (kc + 31 >= k1 && ((cin == 0 && !(tw >> 31)) || (cin == -1 && (tw >> 31))))
             break;
     }
