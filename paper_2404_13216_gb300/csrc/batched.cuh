@@ -83,8 +83,16 @@ __device__ __forceinline__ void b_flush(DotSet<ND, MODE> &D, Shm<ND> &sh, const 
             // partials of the system's flush groups, in tile order (non-first tiles hold +0)
             const int t0 = B.sys_t0[sys], t1 = B.sys_t1[sys];
             double v = 0.0;
-            for (int t = t0 + lane; t < t1; t += 32)
-                v = __dadd_rn(v, __ldcg(B.part + (size_t)t * MAXD + warp));
+            for (int ta = t0 + lane; ta < t1; ta += 32 * 8) {     // eight loads per round trip, same order
+                double u[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    u[j] = ta + 32 * j < t1 ? __ldcg(B.part + (size_t)(ta + 32 * j) * MAXD + warp) : 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (ta + 32 * j < t1)
+                        v = __dadd_rn(v, u[j]);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));

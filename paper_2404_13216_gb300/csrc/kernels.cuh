@@ -484,8 +484,19 @@ __device__ __forceinline__ void merge_finish(Shm<ND> &sh, Work *wk, const void *
     } else if (warp < ND) {
         const double *pp = wk->part + warp * wk->maxgrid;
         double v = 0.0;
-        for (int c = lane; c < (int)gridDim.x; c += 32)
-            v = __dadd_rn(v, __ldcg(pp + c));
+        // lane l adds partials l, l + 32, ... in that order; they are loaded
+        // eight at a time, so the sum waits on one round trip per eight
+        const int grid = (int)gridDim.x;
+        for (int c0 = lane; c0 < grid; c0 += 32 * 8) {
+            double t[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                t[j] = c0 + 32 * j < grid ? __ldcg(pp + c0 + 32 * j) : 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (c0 + 32 * j < grid)
+                    v = __dadd_rn(v, t[j]);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
