@@ -527,6 +527,8 @@ struct BodyKernel {
     const char *name;
     int has_work;    // kernel takes (Mat, Vecs, Ctl*, Work*) rather than (Mat, Vecs, const Ctl*)
     size_t smem;     // dynamic shared memory
+    int prog = 0;    // follows the kernel before it over a programmatic edge (it waits in
+                     // grid_dep_wait; the one before triggers after its tile loop)
 };
 
 // narrow: the passes stage tiles in shared memory (the matrix's tiles fit and
@@ -546,17 +548,17 @@ std::vector<BodyKernel> body_kernels(int alg, int mode, bool narrow)
         k.push_back({mode ? Kern<1>::pipe_x_tma(narrow) : Kern<0>::pipe_x_tma(narrow),
                      mode ? "pipe_x_exact" : "pipe_x_plain", 1, sx});
         k.push_back({mode ? Kern<1>::pipe_y_tma(narrow) : Kern<0>::pipe_y_tma(narrow),
-                     mode ? "pipe_y_exact" : "pipe_y_plain", 1, sy});
+                     mode ? "pipe_y_exact" : "pipe_y_plain", 1, sy, 1});
     } else {
         const size_t sa = narrow ? stage_bytes<1, true>() : stage_bytes<1, false>();
         const size_t sb = narrow ? stage_bytes<2, true>() : stage_bytes<2, false>();
         k.push_back({(void *)k_bicg_p_tma, "bicg_p", 1, stage_bytes<3, false>()});
         k.push_back({mode ? Kern<1>::bicg_a(narrow) : Kern<0>::bicg_a(narrow), mode ? "bicg_a_exact" : "bicg_a_plain", 1,
-                     sa});
+                     sa, 1});
         k.push_back({mode ? Kern<1>::bicg_b(narrow) : Kern<0>::bicg_b(narrow), mode ? "bicg_b_exact" : "bicg_b_plain", 1,
-                     sb});
+                     sb, 1});
         k.push_back({mode ? Kern<1>::bicg_c() : Kern<0>::bicg_c(), mode ? "bicg_c_exact" : "bicg_c_plain", 1,
-                     stage_bytes<6, false>()});
+                     stage_bytes<6, false>(), 1});
     }
     return k;
 }
@@ -601,14 +603,24 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, Loop
     for (auto &bk : body_kernels(alg, mode, m->narrow && m->v_staged)) {
         void *args4[4] = {&A, &V, &c, &wk};
         void *args3[3] = {&A, &V, &c};
-        cudaKernelNodeParams kp{};
-        kp.func = bk.fn;
-        kp.gridDim = dim3(grid_for(ctx, bk.fn, A.nslices, bk.smem, bk.has_work ? m->v_ctas : 0));
-        kp.blockDim = dim3(THREADS);
-        kp.sharedMemBytes = (unsigned)bk.smem;
-        kp.kernelParams = bk.has_work ? args4 : args3;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeKernel;
+        np.kernel.func = bk.fn;
+        np.kernel.gridDim = dim3(grid_for(ctx, bk.fn, A.nslices, bk.smem, bk.has_work ? m->v_ctas : 0));
+        np.kernel.blockDim = dim3(THREADS);
+        np.kernel.sharedMemBytes = (unsigned)bk.smem;
+        np.kernel.kernelParams = bk.has_work ? args4 : args3;
+        // a pass behind a programmatic edge takes the SMs the CTAs of the pass
+        // before it leave while that pass's last CTA merges (it waits in
+        // grid_dep_wait before its first global read)
+        cudaGraphEdgeData ed = {};
+        const bool prog = prev && bk.prog;
+        if (prog) {
+            ed.from_port = cudaGraphKernelNodePortProgrammatic;
+            ed.type = cudaGraphDependencyTypeProgrammatic;
+        }
         cudaGraphNode_t node;
-        CK(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        CK(cudaGraphAddNode(&node, body, prev ? &prev : nullptr, prog ? &ed : nullptr, prev ? 1 : 0, &np));
         prev = node;
     }
     CK(cudaGraphInstantiate(&L.exec, L.graph, 0));

@@ -178,6 +178,22 @@ __device__ __forceinline__ int rr_rounds(const Ctl *c, int nslices)
     return c->order == 3 ? max(0, ntiles / (int)gridDim.x - TAIL_CLAIMED) : 0;
 }
 
+// Programmatic dependent launch.  A pass launched behind a programmatic graph
+// edge (pass Y after pass X; BiCGStab's A after P, B after A, C after B) may
+// become resident once every CTA of the pass before it has left its tile
+// loop (grid_dep_launch), while that pass's last CTA still merges; it runs
+// grid_dep_wait -- which returns once the earlier grid has completed and its
+// stores are visible -- before its first global read.  Launched otherwise,
+// both are no-ops.
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // residual replacement at the start of iteration it (every rr_period iterations, never at 0)
 __device__ __forceinline__ bool rr_now(const Ctl *c)
 {
@@ -1461,11 +1477,12 @@ template <int MODE, bool MATS>
 __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_pipe_x_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
-    if (c->status != ST_RUNNING)
-        return;
     extern __shared__ __align__(128) uint8_t dsm[];
     __shared__ Shm<4> sh;
     shm_init<4, MODE>(sh);
+    grid_dep_wait();
+    if (c->status != ST_RUNNING)
+        return;
     const bool first = (c->it == 0);
     const bool rr = rr_now(c);       // p, s, z were just recomputed: no recurrence this iteration
     const double alpha = c->alpha, beta = c->beta, omega = c->omega;
@@ -1516,6 +1533,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         D.template add2<false>(sh, 2, r0i, si, dr, ds, act);
         D.template add2<false>(sh, 3, r0i, zi, dr, dz, act);
     }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
+    grid_dep_launch();               // pass Y may take the SMs this CTA leaves
     if (!finalize<4, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
@@ -1527,11 +1545,12 @@ template <int MODE, bool MATS>
 __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_pipe_y_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
-    if (c->status != ST_RUNNING)
-        return;
     extern __shared__ __align__(128) uint8_t dsm[];
     __shared__ Shm<3> sh;
     shm_init<3, MODE>(sh);
+    grid_dep_wait();                 // pass X's merge and omega_i complete
+    if (c->status != ST_RUNNING)
+        return;
     const double alpha = c->alpha, omega = c->omega;
     const double nalpha = -alpha, nomega = -omega;
     DotSet<3, MODE> D;
@@ -1635,6 +1654,7 @@ static __global__ void __launch_bounds__(THREADS) k_bicg_p_tma(Mat A, Vecs V, Ct
         if (sl < A.nslices && i < A.n)
             V.p[i] = __fma_rn(beta, __fma_rn(nomega, P.vec(k, 0)[o], P.vec(k, 1)[o]), P.vec(k, 2)[o]);
     });
+    grid_dep_launch();
 }
 
 // A(i): s = A p; dot (r0, s); alpha_i
@@ -1642,11 +1662,12 @@ template <int MODE, bool MATS>
 __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_bicg_a_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
-    if (c->status != ST_RUNNING)
-        return;
     extern __shared__ __align__(128) uint8_t dsm[];
     __shared__ Shm<1> sh;
     shm_init<1, MODE>(sh);
+    grid_dep_wait();
+    if (c->status != ST_RUNNING)
+        return;
     DotSet<1, MODE> D;
     D.init();
     const double *const src[1] = {V.r0};
@@ -1665,6 +1686,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         const Dec dr = decode(r0i), ds = decode(si);
         D.template add2<false>(sh, 0, r0i, si, dr, ds, act);
     }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
+    grid_dep_launch();
     if (!finalize<1, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
@@ -1677,11 +1699,12 @@ template <int MODE, bool MATS>
 __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_bicg_b_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
-    if (c->status != ST_RUNNING)
-        return;
     extern __shared__ __align__(128) uint8_t dsm[];
     __shared__ Shm<2> sh;
     shm_init<2, MODE>(sh);
+    grid_dep_wait();
+    if (c->status != ST_RUNNING)
+        return;
     const double nalpha = -c->alpha;
     DotSet<2, MODE> D;
     D.init();
@@ -1701,6 +1724,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         const Dec dq = decode(qi), dy = decode(yi);
         D.template add_row<2, false, true>(sh, act, qi, yi, dq, dy, yi, yi, dy, dy);
     }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
+    grid_dep_launch();
     if (!finalize<2, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
@@ -1712,11 +1736,12 @@ template <int MODE>
 __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PLAIN)
     k_bicg_c_tma(Mat A, Vecs V, Ctl *c, Work *wk)
 {
-    if (c->status != ST_RUNNING)
-        return;
     extern __shared__ __align__(128) uint8_t dsm[];
     __shared__ Shm<2> sh;
     shm_init<2, MODE>(sh);
+    grid_dep_wait();
+    if (c->status != ST_RUNNING)
+        return;
     const double alpha = c->alpha, omega = c->omega;
     const double nalpha = -alpha, nomega = -omega;
     DotSet<2, MODE> D;
