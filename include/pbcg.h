@@ -62,7 +62,8 @@ typedef struct {
     double relres_recursive;  /* sqrt((r,r)) / sqrt((b,b)) of the last iterate, solve's dot mode */
     double relres_true;       /* ||b - A x||_2 / ||b||_2 with the fixed SpMV and exact dots */
     double seconds;           /* wall time of the call on the host */
-    int32_t launches;         /* kernel launches the call issued (graph-body kernels counted per iteration) */
+    int32_t launches;         /* kernel launches the call issued (graph-body kernels counted per body execution:
+                                 a body holds 16 iterations, whose passes after a stop return at once) */
     int32_t reserved;
 } pbcg_result;
 

@@ -40,6 +40,7 @@ struct LoopGraph {
     bool jac = false;                  // built on the Jacobi-scaled entries
     const void *mat = nullptr;
     int var = -1;                      // launch variant it was built for (staged, order, CTAs per SM)
+    int unroll = 1;                    // iterations per execution of the WHILE body
 };
 
 struct Workspace {
@@ -546,13 +547,13 @@ std::vector<BodyKernel> body_kernels(int alg, int mode, bool narrow)
         size_t sx = narrow ? stage_bytes<7, true>() : stage_bytes<7, false>();
         size_t sy = narrow ? stage_bytes<6, true>() : stage_bytes<6, false>();
         k.push_back({mode ? Kern<1>::pipe_x_tma(narrow) : Kern<0>::pipe_x_tma(narrow),
-                     mode ? "pipe_x_exact" : "pipe_x_plain", 1, sx});
+                     mode ? "pipe_x_exact" : "pipe_x_plain", 1, sx, 1});
         k.push_back({mode ? Kern<1>::pipe_y_tma(narrow) : Kern<0>::pipe_y_tma(narrow),
                      mode ? "pipe_y_exact" : "pipe_y_plain", 1, sy, 1});
     } else {
         const size_t sa = narrow ? stage_bytes<1, true>() : stage_bytes<1, false>();
         const size_t sb = narrow ? stage_bytes<2, true>() : stage_bytes<2, false>();
-        k.push_back({(void *)k_bicg_p_tma, "bicg_p", 1, stage_bytes<3, false>()});
+        k.push_back({(void *)k_bicg_p_tma, "bicg_p", 1, stage_bytes<3, false>(), 1});
         k.push_back({mode ? Kern<1>::bicg_a(narrow) : Kern<0>::bicg_a(narrow), mode ? "bicg_a_exact" : "bicg_a_plain", 1,
                      sa, 1});
         k.push_back({mode ? Kern<1>::bicg_b(narrow) : Kern<0>::bicg_b(narrow), mode ? "bicg_b_exact" : "bicg_b_plain", 1,
@@ -572,10 +573,18 @@ int launch_kernel(pbcg_ctx *ctx, void *fn, Mat &A, Vecs &V, Ctl *c, Work *wk, in
     return 0;
 }
 
+// Iterations per execution of the loop graph's WHILE body.  Each execution of
+// the body costs about 6.5 us of conditional-node overhead at 128^3, and the
+// passes inside one body follow each other over programmatic edges; after a
+// stop every later pass of the body returns at its first check of the
+// status, so a stop costs at most LOOP_UNROLL - 1 such empty iterations.
+constexpr int LOOP_UNROLL = 16;
+
 // build (or reuse) the WHILE-node loop graph for this matrix / algorithm / mode
 int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, LoopGraph **out)
 {
     LoopGraph &L = ctx->ws.loop;
+    const int unroll = LOOP_UNROLL;
     const int var = m->v_staged | (m->v_order << 1) | (m->v_ctas << 4);
     if (L.exec && L.mat == m && L.alg == alg && L.mode == mode && L.n == m->n && L.jac == jac && L.var == var) {
         *out = &L;
@@ -600,7 +609,9 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, Loop
     Ctl *c = ctx->ws.ctl;
     Work *wk = ctx->ws.wk;
     cudaGraphNode_t prev = nullptr;
-    for (auto &bk : body_kernels(alg, mode, m->narrow && m->v_staged)) {
+    const auto bks = body_kernels(alg, mode, m->narrow && m->v_staged);
+    for (int u = 0; u < unroll; u++)
+    for (auto &bk : bks) {
         void *args4[4] = {&A, &V, &c, &wk};
         void *args3[3] = {&A, &V, &c};
         cudaGraphNodeParams np = {};
@@ -628,6 +639,7 @@ int get_loop(pbcg_ctx *ctx, const pbcg_mat *m, int alg, int mode, bool jac, Loop
     L.mode = mode;
     L.jac = jac;
     L.var = var;
+    L.unroll = unroll;
     L.mat = m;
     L.n = m->n;
     *out = &L;
@@ -1032,7 +1044,8 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
             int s2 = ctx->h_ctl->status;
             if (s2 == 2 || s2 == 3)
                 bodies += 1;
-            L.launches += bodies * (long long)body.size();
+            bodies = (bodies + G->unroll - 1) / G->unroll;
+            L.launches += bodies * (long long)G->unroll * (long long)body.size();
             fresh = true;
             continue;
         }

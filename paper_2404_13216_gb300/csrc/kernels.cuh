@@ -1580,6 +1580,7 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         const Dec dr0 = decode(r0i), dr = decode(rn), dw = decode(wn);
         D.template add_row<3, false, false, true>(sh, act, r0i, rn, dr0, dr, r0i, wn, dr0, dw, rn, rn, &dr, &dr);
     }, claimed_tiles<MATS>(c) ? &wk->tile_next : nullptr, rr_rounds(c, A.nslices));
+    grid_dep_launch();
     if (!finalize<3, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
@@ -1642,6 +1643,7 @@ __device__ __forceinline__ void bicg_c_scalar(Ctl *c, double rho_new, double rr)
 // P(i), i >= 1: p = fma(beta, fma(-omega, s, p), r)
 static __global__ void __launch_bounds__(THREADS) k_bicg_p_tma(Mat A, Vecs V, Ctl *c, Work *)
 {
+    grid_dep_wait();
     if (c->status != ST_RUNNING || c->it == 0)
         return;
     extern __shared__ __align__(128) uint8_t dsm[];
@@ -1764,6 +1766,7 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
         const Dec dr0 = decode(r0i), dr = decode(rn);
         D.template add_row<2, false, true>(sh, act, r0i, rn, dr0, dr, rn, rn, dr, dr);
     });
+    grid_dep_launch();
     if (!finalize<2, MODE>(D, sh, wk, c))
         return;
     if (threadIdx.x == 0)
