@@ -1,9 +1,10 @@
 // api.cu -- host driver and C ABI of libpbcg (declared in include/pbcg.h).
 //
 // A solve is: setup passes (r_0, w_0, t_0 and their dots), then the loop of
-// Algorithm 1 or 2 as a CUDA graph whose body is the fused passes inside a
-// conditional WHILE node; the last CTA of each pass sets the node's condition,
-// so the device iterates without host round trips.  The host wakes up only
+// Algorithm 1 or 2 as a CUDA graph whose body, inside a conditional WHILE
+// node, is LOOP_UNROLL iterations of the fused passes; the last CTA of each
+// iteration sets the node's condition, so the device iterates without host
+// round trips.  The host wakes up only
 // when the device proposes to stop (residual below target), runs the
 // true-residual pass, and either finishes or relaunches the loop.
 #include <cuda_runtime.h>
@@ -1038,8 +1039,10 @@ int solve_impl(pbcg_ctx *ctx, const pbcg_mat *m, const double *b, double *x, dou
             CK(cudaGraphLaunch(G->exec, ctx->stream));
             if ((rc = read_ctl(ctx)))
                 return rc;
-            // every body execution launches all body kernels; a stop inside an
-            // iteration (non-finite dot, breakdown) still ran that iteration's body
+            // every body execution launches all body kernels (LOOP_UNROLL
+            // iterations of them, those after a stop returning at once); a stop
+            // inside an iteration (non-finite dot, breakdown) still ran that
+            // iteration's kernels
             long long bodies = ctx->h_ctl->it - it_before;
             int s2 = ctx->h_ctl->status;
             if (s2 == 2 || s2 == 3)
