@@ -553,14 +553,15 @@ std::vector<BodyKernel> body_kernels(int alg, int mode, bool narrow)
                      mode ? "pipe_y_exact" : "pipe_y_plain", 1, sy, 1});
     } else {
         const size_t sa = narrow ? stage_bytes<1, true>() : stage_bytes<1, false>();
-        const size_t sb = narrow ? stage_bytes<2, true>() : stage_bytes<2, false>();
+        const size_t sb = narrow ? stage_bytes<1, true>() : stage_bytes<1, false>();
         k.push_back({(void *)k_bicg_p_tma, "bicg_p", 1, stage_bytes<3, false>(), 1});
         k.push_back({mode ? Kern<1>::bicg_a(narrow) : Kern<0>::bicg_a(narrow), mode ? "bicg_a_exact" : "bicg_a_plain", 1,
                      sa, 1});
+        k.push_back({(void *)k_bicg_q, "bicg_q", 0, 0, 1});
         k.push_back({mode ? Kern<1>::bicg_b(narrow) : Kern<0>::bicg_b(narrow), mode ? "bicg_b_exact" : "bicg_b_plain", 1,
                      sb, 1});
         k.push_back({mode ? Kern<1>::bicg_c() : Kern<0>::bicg_c(), mode ? "bicg_c_exact" : "bicg_c_plain", 1,
-                     stage_bytes<6, false>(), 1});
+                     stage_bytes<5, false>(), 1});
     }
     return k;
 }
@@ -2451,14 +2452,14 @@ int part_solve_impl(pbcg_part *P, const double *b, double *x, double tol, int32_
                 (rc = part_reduce(P, 3, mode, FIN_Y)))
                 return rc;
         } else {
-            const BodyKernel &kp = body[0], &ka = body[1], &kb = body[2], &kc = body[3];
+            const BodyKernel &kp = body[0], &ka = body[1], &kq = body[2], &kb = body[3], &kc = body[4];
             if ((rc = L.go(kp.name, kp.fn, A, V, c, wk, 1, kp.smem)) || (rc = part_halo(P, V.p)) ||
                 (rc = L.go(ka.name, ka.fn, A, V, c, wk, 1, ka.smem)) || (rc = part_reduce(P, 1, mode, FIN_BA)) ||
                 (rc = status(&st)))
                 return rc;
             if (st != ST_RUNNING)
                 continue;
-            if ((rc = part_halo(P, V.s)) || (rc = part_halo(P, V.r)) ||
+            if ((rc = L.go(kq.name, kq.fn, A, V, c, wk, 0)) || (rc = part_halo(P, V.q)) ||
                 (rc = L.go(kb.name, kb.fn, A, V, c, wk, 1, kb.smem)) || (rc = part_reduce(P, 2, mode, FIN_BB)) ||
                 (rc = status(&st)))
                 return rc;

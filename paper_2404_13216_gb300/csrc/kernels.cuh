@@ -1695,8 +1695,31 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
         bicg_a_scalar(c, sh.dv[0]);
 }
 
-// B(i): y = A q with q_j = fma(-alpha, s_j, r_j) formed for each gathered
-// entry (alpha is known only after pass A); dots (q,y), (y,y); omega_i
+// Q(i): q = r - alpha s, formed once per row as fma(-alpha, s_j, r_j), for
+// pass B to gather and for passes B and C to read (alpha is known only after
+// pass A).  Elementwise, two rows per thread per step.
+static __global__ void __launch_bounds__(THREADS) k_bicg_q(Mat A, Vecs V, const Ctl *c)
+{
+    grid_dep_wait();
+    grid_dep_launch();               // pass B's CTAs may become resident as these leave
+    if (c->status != ST_RUNNING)
+        return;
+    const double nalpha = -c->alpha;
+    const int n = A.n;
+    const int stride = 2 * (int)(gridDim.x * blockDim.x);
+    for (int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x); i < n; i += stride) {
+        // (vectors are 16-byte aligned and padded to whole tiles: i + 1 is in the allocation)
+        const double2 sv = *reinterpret_cast<const double2 *>(V.s + i);
+        const double2 rv = *reinterpret_cast<const double2 *>(V.r + i);
+        if (i + 1 < n) {
+            *reinterpret_cast<double2 *>(V.q + i) = make_double2(__fma_rn(nalpha, sv.x, rv.x), __fma_rn(nalpha, sv.y, rv.y));
+        } else {
+            V.q[i] = __fma_rn(nalpha, sv.x, rv.x);
+        }
+    }
+}
+
+// B(i): y = A q (q from pass Q); dots (q,y), (y,y); omega_i
 template <int MODE, bool MATS>
 __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     k_bicg_b_tma(Mat A, Vecs V, Ctl *c, Work *wk)
@@ -1707,19 +1730,18 @@ __global__ void __launch_bounds__(THREADS, PBCG_MINB(MODE, MATS))
     grid_dep_wait();
     if (c->status != ST_RUNNING)
         return;
-    const double nalpha = -c->alpha;
     DotSet<2, MODE> D;
     D.init();
-    const double *const src[2] = {V.s, V.r};
-    tile_loop<2, MATS>(A, src, 2, nullptr, c, dsm, [&](const TilePipe<2, MATS> &P, int k, int tile, int warp, int lane) {
+    const double *const src[1] = {V.q};
+    tile_loop<1, MATS>(A, src, 1, V.q, c, dsm, [&](const TilePipe<1, MATS> &P, int k, int tile, int warp, int lane) {
         const int sl = tile * TILE_SLICES + warp;
         const int i = sl * 32 + lane;
         const bool act = sl < A.nslices && i < A.n;
         const int o = warp * 32 + lane;
         double qi = 0.0, yi = 0.0;
         if (sl < A.nslices) {
-            yi = P.spmv_axpy(k, A, warp, lane, nalpha, V.s, V.r);
-            qi = __fma_rn(nalpha, P.vec(k, 0)[o], P.vec(k, 1)[o]);
+            yi = P.spmv(k, A, warp, lane, V.q);
+            qi = P.vec(k, 0)[o];
             if (act)
                 V.y[i] = yi;
         }
@@ -1745,23 +1767,23 @@ __global__ void __launch_bounds__(THREADS, MODE ? PBCG_MINB_EXACT : PBCG_MINB_PL
     if (c->status != ST_RUNNING)
         return;
     const double alpha = c->alpha, omega = c->omega;
-    const double nalpha = -alpha, nomega = -omega;
+    const double nomega = -omega;
     DotSet<2, MODE> D;
     D.init();
-    // stage slots: 0 s, 1 r, 2 p, 3 x, 4 y, 5 r0
-    const double *const src[6] = {V.s, V.r, V.p, V.x, V.y, V.r0};
-    tile_loop<6, false>(A, src, 6, nullptr, c, dsm, [&](const TilePipe<6, false> &P, int k, int tile, int warp, int lane) {
+    // stage slots: 0 q, 1 p, 2 x, 3 y, 4 r0
+    const double *const src[5] = {V.q, V.p, V.x, V.y, V.r0};
+    tile_loop<5, false>(A, src, 5, nullptr, c, dsm, [&](const TilePipe<5, false> &P, int k, int tile, int warp, int lane) {
         const int sl = tile * TILE_SLICES + warp;
         const int i = sl * 32 + lane;
         const bool act = sl < A.nslices && i < A.n;
         const int o = warp * 32 + lane;
         double rn = 0.0, r0i = 0.0;
         if (act) {
-            const double q = __fma_rn(nalpha, P.vec(k, 0)[o], P.vec(k, 1)[o]);
-            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, P.vec(k, 2)[o], P.vec(k, 3)[o]));
-            rn = __fma_rn(nomega, P.vec(k, 4)[o], q);
+            const double q = P.vec(k, 0)[o];
+            V.x[i] = __fma_rn(omega, q, __fma_rn(alpha, P.vec(k, 1)[o], P.vec(k, 2)[o]));
+            rn = __fma_rn(nomega, P.vec(k, 3)[o], q);
             V.r[i] = rn;
-            r0i = P.vec(k, 5)[o];
+            r0i = P.vec(k, 4)[o];
         }
         const Dec dr0 = decode(r0i), dr = decode(rn);
         D.template add_row<2, false, true>(sh, act, r0i, rn, dr0, dr, rn, rn, dr, dr);
