@@ -1167,66 +1167,6 @@ struct TilePipe {
         }
         return acc;
     }
-
-    // SpMV row of (r - alpha s) with alpha = -na: each gathered entry forms
-    // fma(na, s_j, r_j) first (one rounding), then the row's fma chain
-    __device__ __forceinline__ double spmv_axpy(int k, const Mat &A, int warp, int lane, double na,
-                                                const double *__restrict__ s, const double *__restrict__ r) const
-    {
-        const int *so = sloff(k);
-        const int off = so[warp];
-        int width = A.sl_w ? __ldg(A.sl_w + (size_t)(info[k].tile * TILE_SLICES + warp)) : (so[warp + 1] - off) >> 5;
-        int len = rlen(k)[warp * 32 + lane];
-        const bool st = info[k].staged;
-#if PBCG_CHECKS
-        if (!PBCG_IN(len, width + 1, CHK_RLEN))
-            len = width;
-        if (st && !(PBCG_IN(off - info[k].e0, info[k].span + 1, CHK_SPAN) &&
-                    PBCG_IN(off - info[k].e0 + 32 * width, info[k].span + 1, CHK_SPAN)))
-            width = len = 0;
-#endif
-        const int *cp = st ? ci(k) + (off - info[k].e0) + lane : A.ci + off + lane;
-        const double *vp = st ? va(k) + (off - info[k].e0) + lane : A.va + off + lane;
-        double acc = 0.0;
-        const unsigned long long pol = l2_evict_first_policy();
-        for (int j0 = 0; j0 < width; j0 += UNR) {
-            int c[UNR];
-            double v[UNR], xs[UNR], xr[UNR];
-            if (st) {                                  // warp-uniform: entries in shared memory
-#pragma unroll
-                for (int j = 0; j < UNR; j++) {
-                    if (j0 + j < len) {
-                        c[j] = cp[(j0 + j) * 32];
-                        v[j] = vp[(j0 + j) * 32];
-                    }
-                }
-            } else {                                   // entries in global memory, streamed
-#pragma unroll
-                for (int j = 0; j < UNR; j++) {
-                    if (j0 + j < len) {
-                        c[j] = ld_stream(cp + (j0 + j) * 32, pol);
-                        v[j] = ld_stream(vp + (j0 + j) * 32, pol);
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < UNR; j++)
-                if (j0 + j < len && !PBCG_IN(c[j], A.ncols, CHK_COL))
-                    c[j] = 0;
-#pragma unroll
-            for (int j = 0; j < UNR; j++) {
-                if (j0 + j < len) {
-                    xs[j] = __ldg(s + c[j]);
-                    xr[j] = __ldg(r + c[j]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < UNR; j++)
-                if (j0 + j < len)
-                    acc = __fma_rn(v[j], __fma_rn(na, xs[j], xr[j]), acc);
-        }
-        return acc;
-    }
 };
 
 // Common tile loop.  No CTA-wide barrier per tile: each warp waits on the
