@@ -16,15 +16,15 @@
 //     accumulator digits (or writes its plain partial) into CTA 0's shared
 //     memory, the cluster syncs (a hardware barrier), CTA 0 rounds (exact) or
 //     sums in CTA order (plain) and takes the pass's scalar step on its shared
-//     copy of the control block, and the cluster syncs again before the
-//     other CTAs read the scalars from it.
+//     copy of the control block, pushes the scalars the next step reads into
+//     every CTA's shared memory, and the cluster syncs again.
 // The row arithmetic, the SpMV's fma order, the exact rounding and the
 // scalar steps are the functions the passes use, so exact mode is
 // bit-identical to the multi-pass path and to the oracle.  The vectors and
 // the control block go back to global memory when the status leaves RUNNING.
 //
 // There is no spin-wait: every CTA executes the same sequence of cluster
-// barriers (the exit test reads a status that CTA 0 wrote before the last
+// barriers (the exit test reads a status that CTA 0 pushed before the last
 // barrier), and the final barrier keeps every CTA's shared memory alive
 // until no other CTA reads it.
 #pragma once
@@ -129,9 +129,36 @@ struct ClusterRows {
     __device__ __forceinline__ int width(int ls) const { return (msoff[ls + 1] - msoff[ls]) >> 5; }
 };
 
+// The scalars every CTA reads after a merge.  CTA 0 pushes them into each
+// CTA's own copy (one distributed-shared-memory store per CTA) before the
+// barrier that ends the merge, so that after it every thread reads local
+// shared memory instead of loading them from CTA 0.
+struct ClusterScal {
+    double alpha, beta, omega;
+    int status, it;
+};
+
 struct ClusterGather {
     const double *gv[CL_NV][CLUSTER_MAX_CTAS];
+    ClusterScal *scp[CLUSTER_MAX_CTAS];      // every CTA's sc
+    ClusterScal sc;                          // this CTA's copy of the scalars
 };
+
+// CTA 0, every thread: after its scalar step (thread 0), push the scalars to
+// every CTA of the cluster (the caller's cluster barrier publishes them)
+__device__ __forceinline__ void push_scal(const ClusterHub &hub, const ClusterGather &G)
+{
+    __syncthreads();
+    if (threadIdx.x < gridDim.x) {
+        ClusterScal s;
+        s.alpha = hub.ctl.alpha;
+        s.beta = hub.ctl.beta;
+        s.omega = hub.ctl.omega;
+        s.status = hub.ctl.status;
+        s.it = hub.ctl.it;
+        *G.scp[threadIdx.x] = s;
+    }
+}
 
 // Fill this CTA's rows from global memory, CTA 0's hub from the control
 // block, the gather tables; ends with a cluster barrier.
@@ -182,6 +209,12 @@ __device__ __forceinline__ ClusterRows cluster_load(const Mat &A, const Vecs &V,
     }
     for (int t = threadIdx.x; t < CL_NV * (int)gridDim.x; t += THREADS)
         G.gv[t / gridDim.x][t % gridDim.x] = cl.map_shared_rank(R.v(t / gridDim.x), t % gridDim.x);
+    for (int t = threadIdx.x; t < (int)gridDim.x; t += THREADS)
+        G.scp[t] = cl.map_shared_rank(&G.sc, t);
+    cl.sync();
+    // (every CTA is running from here on) the scalars of the first step
+    if (blockIdx.x == 0)
+        push_scal(hub, G);
     cl.sync();
     return R;
 }
@@ -305,7 +338,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __shared__ ClusterGather G;
     const ClusterRows R = cluster_load(A, V, c, rpt, lg, emax, dsm, hub, G, cl);
     ClusterHub *const hub0 = cl.map_shared_rank(&hub, 0);
-    const volatile Ctl *const c0 = &hub0->ctl;     // read after each cluster barrier
+    const volatile ClusterScal *const c0 = &G.sc;  // pushed by CTA 0 before each cluster barrier
     const int me = (int)blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *const Vx = R.v(CV_X), *const Vr = R.v(CV_R), *const Vw = R.v(CV_W), *const Vt = R.v(CV_T);
     double *const Vp = R.v(CV_P), *const Vs = R.v(CV_S), *const Vz = R.v(CV_Z), *const Vv = R.v(CV_V);
@@ -357,8 +390,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 D.template add2<false>(sx, 3, r0i, zi, dr, dz, act);
             }
             cluster_merge<4, MODE>(D, sx, hub, hub0, cl);
-            if (me == 0 && threadIdx.x == 0)
-                pipe_x_tail(&hub.ctl, sx.dv);
+            if (me == 0) {
+                if (threadIdx.x == 0)
+                    pipe_x_tail(&hub.ctl, sx.dv);
+                push_scal(hub, G);
+            }
             cl.sync();
         }
         if (c0->status != ST_RUNNING)
@@ -391,8 +427,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                                                           &dr);
             }
             cluster_merge<3, MODE>(D, sy, hub, hub0, cl);
-            if (me == 0 && threadIdx.x == 0)
-                pipe_y_tail(&hub.ctl, sy.dv);
+            if (me == 0) {
+                if (threadIdx.x == 0)
+                    pipe_y_tail(&hub.ctl, sy.dv);
+                push_scal(hub, G);
+            }
             cl.sync();
         }
     }
@@ -415,7 +454,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __shared__ ClusterGather G;
     const ClusterRows R = cluster_load(A, V, c, rpt, lg, emax, dsm, hub, G, cl);
     ClusterHub *const hub0 = cl.map_shared_rank(&hub, 0);
-    const volatile Ctl *const c0 = &hub0->ctl;
+    const volatile ClusterScal *const c0 = &G.sc;  // pushed by CTA 0 before each cluster barrier
     const int me = (int)blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *const Vx = R.v(CV_X), *const Vr = R.v(CV_R), *const Vp = R.v(CV_P), *const Vs = R.v(CV_S);
     double *const Vy = R.v(CV_Y), *const Vr0 = R.v(CV_R0);
@@ -451,8 +490,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 D.template add2<false>(sa, 0, r0i, si, dr, ds, act);
             }
             cluster_merge<1, MODE>(D, sa, hub, hub0, cl);
-            if (me == 0 && threadIdx.x == 0)
-                bicg_a_scalar(&hub.ctl, sa.dv[0]);
+            if (me == 0) {
+                if (threadIdx.x == 0)
+                    bicg_a_scalar(&hub.ctl, sa.dv[0]);
+                push_scal(hub, G);
+            }
             cl.sync();
         }
         if (c0->status != ST_RUNNING)
@@ -478,8 +520,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 D.template add_row<2, false, true>(sb, act, qi, yi, dq, dy, yi, yi, dy, dy);
             }
             cluster_merge<2, MODE>(D, sb, hub, hub0, cl);
-            if (me == 0 && threadIdx.x == 0)
-                bicg_b_scalar(&hub.ctl, sb.dv[0], sb.dv[1]);
+            if (me == 0) {
+                if (threadIdx.x == 0)
+                    bicg_b_scalar(&hub.ctl, sb.dv[0], sb.dv[1]);
+                push_scal(hub, G);
+            }
             cl.sync();
         }
         if (c0->status != ST_RUNNING)
@@ -507,8 +552,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 D.template add_row<2, false, true>(sb, act, r0i, rn, dr0, dr, rn, rn, dr, dr);
             }
             cluster_merge<2, MODE>(D, sb, hub, hub0, cl);
-            if (me == 0 && threadIdx.x == 0)
-                bicg_c_scalar(&hub.ctl, sb.dv[0], sb.dv[1]);
+            if (me == 0) {
+                if (threadIdx.x == 0)
+                    bicg_c_scalar(&hub.ctl, sb.dv[0], sb.dv[1]);
+                push_scal(hub, G);
+            }
             cl.sync();
         }
     }
